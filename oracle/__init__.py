@@ -1,0 +1,33 @@
+"""Independent FP64 CPU oracle for the SIP Helmholtz operator.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the library path may import, call or
+execute this package: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` use it.
+
+It assembles the symmetric-interior-penalty matrix element by element and face
+by face, straight from the primal bilinear form (Sec. 2.2, Eq. primal, with the
+element view of Eq. IP and the block structure of Appendix A), with dense basis
+matrices at the quadrature points and no sum factorisation, blocking or fusion.
+It shares no code with the CUDA path; the only common module is ``sip_inputs``
+(seeded meshes, orders and random vectors, which hold none of the method's
+arithmetic).
+
+Parity status of each part (what pins it is in ``tests/test_oracle_*.py``):
+
+* quadrature / Lagrange tables: pinned (library Gauss rule, closed forms,
+  polynomial exactness);
+* volume + interior-face + boundary-face blocks: pinned (symmetry, the
+  penalty closed form for an element indicator, Galerkin consistency for
+  polynomials vanishing on the boundary, constant null space of the
+  pure-Neumann stiffness, manufactured-solution convergence order P+1);
+* penalty length h_f on jittered (non-affine) faces: parity unpinned (the
+  paper does not define h_f; the reading min(|K-|,|K+|)/|F| is checked only
+  through the invariants above, which hold for any positive h_f);
+* diffusivity placement (kappa multiplies the volume diffusion term only):
+  parity unpinned beyond finite differences of the oracle's own assembly,
+  because the paper has no kappa.
+"""
+from .quadrature import gauss_legendre, gauss_lobatto, lagrange_matrix, lagrange_deriv_matrix
+from .assembly import SipOracle
+
+__all__ = ["gauss_legendre", "gauss_lobatto", "lagrange_matrix", "lagrange_deriv_matrix", "SipOracle"]

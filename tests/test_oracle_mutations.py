@@ -1,0 +1,79 @@
+"""Planted mistakes: each plausible error in the face terms of the oracle must
+break at least one of the invariants that pin it (symmetry, Galerkin
+consistency, penalty closed form).  Mistakes are planted in a subclass of the
+oracle, on the CPU only."""
+import numpy as np
+import pytest
+
+import sip_inputs as si
+from oracle import SipOracle
+from test_oracle_operator import _bubble, _rel_asym
+
+
+class Mutant(SipOracle):
+    def __init__(self, mesh, mutation, **kw):
+        self.mutation = mutation
+        super().__init__(mesh, **kw)
+
+    def interior_face_blocks(self, pair):
+        W, _, tau, (phim, dnm), (phip, dnp) = self.face_data(pair)
+        mu = self.mutation
+        if mu == "plus_normal_flipped":
+            dnp = -dnp
+        sides = [(phim, dnm, 1.0), (phip, dnp, -1.0)]
+        half_sym = 1.0 if mu == "no_half_in_symmetry_term" else 0.5
+        cons_sign = 1.0 if mu == "consistency_sign" else -1.0
+        tau_f = 2.0 * tau if mu == "double_tau" else tau
+        out = {}
+        for v in range(2):
+            for w in range(2):
+                pv, dv, sv = sides[v]
+                pw, dw, sw = sides[w]
+                out[(v, w)] = (-half_sym * sw * np.einsum("z,zi,zj->ij", W, dv, pw)
+                               + cons_sign * 0.5 * sv * np.einsum("z,zi,zj->ij", W, pv, dw)
+                               + tau_f * sv * sw * np.einsum("z,zi,zj->ij", W, pv, pw))
+        return out
+
+
+def _checks(orc, m, amat, bvec, lam):
+    A = orc.assemble()
+    u, neg_lap = _bubble(amat, bvec, m.dim)
+    lhs = A @ orc.interpolate(u)
+    rhs = orc.rhs(lambda x: neg_lap(x) + lam * u(x))
+    consistent = np.max(np.abs(lhs - rhs)) <= 1e-12 * np.max(np.abs(rhs))
+    symmetric = _rel_asym(A) <= 1e-13
+    # penalty closed form on a uniform grid (amat = identity here)
+    n = int(round(np.sqrt(m.n_elem)))
+    h = 1.0 / n
+    pen_ok = True
+    for e in range(m.n_elem):
+        ex, ey = e % n, e // n
+        expect = lam * h * h
+        for ax, idx in enumerate((ex, ey)):
+            for d in (-1, 1):
+                j = idx + d
+                nb = e + d * n ** ax
+                pmax = max(m.orders[e], m.orders[nb]) if 0 <= j < n else m.orders[e]
+                expect += 2.0 * (pmax + 1) ** 2
+        ind = np.zeros(orc.ndof)
+        ind[orc.off[e]:orc.off[e + 1]] = 1.0
+        pen_ok &= abs(ind @ (A @ ind) - expect) <= 1e-12 * expect
+    return consistent, symmetric, pen_ok
+
+
+MESH = dict(dim=2, n=3, seed=8, order_range=(2, 4))
+
+
+def test_unmutated_passes_all():
+    m = si.rotate_elements(si.structured_mesh(**MESH), 2)
+    lam = 1.1
+    assert all(_checks(Mutant(m, "none", lam=lam), m, np.eye(2), np.zeros(2), lam))
+
+
+@pytest.mark.parametrize("mutation", ["plus_normal_flipped", "no_half_in_symmetry_term",
+                                      "consistency_sign", "double_tau"])
+def test_planted_mistake_is_caught(mutation):
+    m = si.rotate_elements(si.structured_mesh(**MESH), 2)
+    lam = 1.1
+    res = _checks(Mutant(m, mutation, lam=lam), m, np.eye(2), np.zeros(2), lam)
+    assert not all(res), (mutation, res)
