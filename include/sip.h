@@ -1,0 +1,223 @@
+/*
+ * sip.h — C ABI of the GB300 library for the matrix-free symmetric interior
+ * penalty (SIP) Helmholtz operator on quad/hex meshes with per-element order.
+ *
+ * Operator (Sec. 2.2, Eq. IP and Eq. primal; shared trace space of Sec. 3.3):
+ *
+ *   a(v,u) = sum_K (kappa grad v, grad u)_K + lambda (v,u)_K
+ *          - ({grad v},[[u]])_Gamma - ([[v]],{grad u})_Gamma + tau_F ([[u]],[[v]])_Gamma
+ *
+ * discretised with tensor Lagrange polynomials on P+1 Gauss-Lobatto-Legendre
+ * nodes per direction (Table 1, Lagrange-GLL; Eq. expansion), a (P+2)-point
+ * Gauss rule per direction in the volume (Eq. iproduct) and ONE Gauss rule
+ * with max(P-,P+)+2 points per direction on each face, shared by both sides
+ * (Sec. 3.3, "shared trace space"; the mortar-equivalent point evaluation of
+ * Sec. 3.3).  Boundary faces use Nitsche's weak Dirichlet condition with g = 0
+ * ([[u]] = u n, {grad u} = grad u).  Penalty:
+ *   tau_F = tau_scale (max(P-,P+)+1)^2 / h_F,  h_F = min(|K-|,|K+|) / |F|.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - DOF vectors are element major: element e owns entries
+ *   [dof_off[e], dof_off[e+1]) with (P_e+1)^dim values, node index
+ *   i0 + N i1 (+ N^2 i2), N = P_e+1, i0 along the element's first reference
+ *   axis (local vertex bit 0).  Multi-RHS arrays are [nrhs][ndof], contiguous.
+ * - Quadrature-point arrays (kappa, its gradient, iproduct input) are element
+ *   major with (P_e+2)^dim Gauss points per element, lexicographic, first
+ *   reference axis fastest; offsets from sip_quad_offsets.
+ * - Pointers named *_dev are CUDA device pointers owned by the caller; *_host
+ *   are host pointers.  `stream` is a cudaStream_t passed as void* (NULL =
+ *   legacy default stream).  Work is enqueued on that stream; the library does
+ *   not synchronise the device except where a function says so.
+ * - Every function returns SIP_OK (0) or a SIP_ERR_* code; nothing aborts and
+ *   no device trap is used.  sip_last_error() returns a thread-local message
+ *   describing the most recent failure on the calling thread.
+ * - A handle is not thread safe: calls on one handle must be serialised by the
+ *   caller (they share internal scratch buffers).
+ */
+#ifndef SIP_H
+#define SIP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SIP_OK                0
+#define SIP_ERR_ARG           1  /* invalid argument (null pointer, bad size, order outside 1..8) */
+#define SIP_ERR_MESH          2  /* non-manifold face, element glued to itself, non-positive Jacobian */
+#define SIP_ERR_CUDA          3  /* a CUDA runtime call failed (message has the CUDA error string) */
+#define SIP_ERR_OOM           4  /* device allocation failed */
+#define SIP_ERR_NONFINITE     5  /* NaN/Inf in an input or in a CG scalar */
+#define SIP_ERR_NOT_CONVERGED 6  /* CG reached max_iter; stats hold the last residual */
+#define SIP_ERR_BREAKDOWN     7  /* p^T A p <= 0 in CG (operator not positive definite) */
+#define SIP_ERR_NO_DEVICE     8  /* no CUDA device, or the library was built without it */
+
+#define SIP_FP64 0              /* apply in double precision */
+#define SIP_FP32 1              /* apply in single precision with single accumulation */
+
+#define SIP_CG_FP64         0   /* plain CG, FP64 apply */
+#define SIP_CG_FP32_REFINED 1   /* FP64 iterative refinement around an FP32-apply CG */
+
+#define SIP_MAX_ORDER 8
+
+/* Mesh: vertex coordinates and element connectivity (read only, copied). */
+typedef struct sip_mesh {
+    int32_t dim;              /* 2 (quadrilaterals) or 3 (hexahedra) */
+    int64_t n_vert;
+    const double* vert;       /* host [n_vert][dim] */
+    int64_t n_elem;
+    const int64_t* elem_vert; /* host [n_elem][2^dim]; local vertex c sits at reference
+                                 corner xi_k = (bit k of c) ? +1 : -1 (multilinear map) */
+} sip_mesh;
+
+typedef struct sip_options {
+    double  tau_scale;        /* penalty factor in tau_F, default 2 */
+    int32_t qvol_extra;       /* Q = P + qvol_extra volume Gauss points; only 2 is supported */
+    int32_t boundary;         /* 1: Nitsche faces on the boundary (default); 0: drop them
+                                 (pure Neumann operator) */
+    double  inner_rtol;       /* FP32 inner CG tolerance in SIP_CG_FP32_REFINED, default 1e-5 */
+    int32_t max_iter;         /* CG iteration cap (total inner iterations), default 20000 */
+    int32_t check_every;      /* CG iterations per captured graph launch, default 16 */
+    int32_t max_refine;       /* outer refinement steps cap, default 30 */
+    int32_t checkpoint_every; /* save (x, r, p, r.r, k) every k CG iterations; 0 = off */
+    int32_t checkpoint_slots; /* ring size for checkpoints, default 8 */
+} sip_options;
+
+typedef struct sip_stats {
+    int32_t iterations;       /* CG iterations (all inner iterations for refined mode) */
+    int32_t refinements;      /* outer refinement steps (0 for SIP_CG_FP64) */
+    int32_t applies_fp64;
+    int32_t applies_fp32;
+    double  rel_residual;     /* max over RHS of ||b - A_fp64 x|| / ||b|| at exit */
+    double  seconds;          /* host wall time of the call */
+    int32_t converged;        /* 1 if every RHS met rtol */
+    int32_t checkpoints;      /* checkpoints written during the call */
+} sip_stats;
+
+/* Counts of the host-side plan (mesh analysis); no GPU needed. */
+typedef struct sip_plan_info {
+    int32_t dim;
+    int64_t n_elem, ndof, nquad;
+    int64_t n_faces_interior, n_faces_boundary, n_faces_nonconforming;
+    int64_t n_elem_affine;            /* elements whose map is affine (constant Jacobian) */
+    int64_t orient_hist[8];           /* interior faces per orientation code of the plus side */
+    int64_t order_hist[SIP_MAX_ORDER + 1];
+    int64_t trace_points;             /* sum over faces of the shared face points */
+    double  min_h_face, max_tau;
+} sip_plan_info;
+
+typedef struct sip_plan sip_plan;     /* host-side mesh analysis */
+typedef struct sip_handle sip_handle; /* plan + device tables */
+
+/* Fills *opt with the defaults listed above. */
+void sip_options_default(sip_options* opt);
+
+/* Host-only mesh analysis: face pairing by shared vertex sets, orientation of
+ * each plus side relative to the minus side (the lower element id), geometric
+ * factors at volume and face points, penalties, order buckets.  Copies the
+ * mesh; the caller may free it afterwards.  opt may be NULL (defaults).
+ * Errors: SIP_ERR_ARG (null pointer, dim, order outside 1..SIP_MAX_ORDER),
+ * SIP_ERR_MESH (face shared by more than two elements, non-positive Jacobian
+ * at a volume Gauss point). */
+int  sip_plan_create(const sip_mesh* mesh, const int32_t* orders_host, const sip_options* opt,
+                     sip_plan** out);
+int  sip_plan_info_get(const sip_plan* plan, sip_plan_info* out);
+void sip_plan_destroy(sip_plan* plan);
+
+/* Plan + upload to the current CUDA device.  lambda >= 0 is the Helmholtz
+ * coefficient (Sec. 2.2).  kappa defaults to 1.  Synchronises the device once.
+ * Errors: as sip_plan_create, plus SIP_ERR_NO_DEVICE, SIP_ERR_CUDA, SIP_ERR_OOM. */
+int  sip_create(const sip_mesh* mesh, const int32_t* orders_host, double lambda,
+                const sip_options* opt, sip_handle** out);
+void sip_destroy(sip_handle* h);
+
+int64_t sip_num_dofs(const sip_handle* h);
+int64_t sip_num_quad(const sip_handle* h);
+int  sip_dof_offsets(const sip_handle* h, int64_t* out_host /* [n_elem+1] */);
+int  sip_quad_offsets(const sip_handle* h, int64_t* out_host /* [n_elem+1] */);
+int  sip_get_plan_info(const sip_handle* h, sip_plan_info* out);
+
+/* Coefficients of the operator. lambda >= 0 (SIP_ERR_ARG otherwise).
+ * kappa_dev: [nquad] FP64 diffusivity per volume Gauss point, copied (also to
+ * an FP32 copy for SIP_FP32 applies); NULL resets kappa to 1. */
+int  sip_set_lambda(sip_handle* h, double lambda);
+int  sip_set_kappa(sip_handle* h, const double* kappa_dev, void* stream);
+
+/* y = A x (a1-a7: volume term by sum factorisation, trace evaluation at the
+ * shared face Gauss points, SIP flux, lift to both sides without atomics).
+ * precision SIP_FP64: x_dev, y_dev are double [nrhs][ndof];
+ * SIP_FP32: float [nrhs][ndof] (FP32 arithmetic and accumulation).
+ * x and y must not overlap.  nrhs >= 1. */
+int  sip_apply(sip_handle* h, int precision, const void* x_dev, void* y_dev, int nrhs, void* stream);
+
+/* y = A^T x with the roles of trial side (trace evaluation) and test side
+ * (lift) exchanged in the face terms (Appendix A: A^T has blocks M'_C <-> M_C^T).
+ * For this operator A^T = A, so the result equals sip_apply up to rounding. */
+int  sip_apply_transpose(sip_handle* h, int precision, const void* x_dev, void* y_dev, int nrhs,
+                         void* stream);
+
+/* Solves A x = b by conjugate gradients (Sec. 2.2: the symmetric system is
+ * solved by CG), x0 = 0, to ||b - A x|| <= rtol ||b|| in the FP64 operator for
+ * every RHS.  mode SIP_CG_FP64: FP64 CG.  mode SIP_CG_FP32_REFINED: outer FP64
+ * residual r = b - A x and update x += d, inner CG on A d = r with FP32
+ * applies and FP32 vectors, FP64 dot products, to inner_rtol.
+ * b_dev, x_dev: double [nrhs][ndof].  Dots are deterministic (fixed-order
+ * reductions), so repeated calls give bit-identical x.  stats may be NULL.
+ * Synchronises the stream every check_every iterations (convergence test).
+ * Errors: SIP_ERR_NOT_CONVERGED, SIP_ERR_BREAKDOWN, SIP_ERR_NONFINITE. */
+int  sip_cg_solve(sip_handle* h, int mode, const double* b_dev, double* x_dev, int nrhs,
+                  double rtol, sip_stats* stats, void* stream);
+
+/* Solves A^T x = b with the transpose apply (adjoint solve); same contract. */
+int  sip_cg_solve_transpose(sip_handle* h, int mode, const double* b_dev, double* x_dev, int nrhs,
+                            double rtol, sip_stats* stats, void* stream);
+
+/* Checkpoints of the most recent FP64 solve (options.checkpoint_every > 0,
+ * nrhs = 1): number stored, and copy-out of slot i (0 = oldest kept) into
+ * caller device buffers x, r, p [ndof] plus host scalars rr and k. */
+int  sip_cg_checkpoint_count(const sip_handle* h);
+int  sip_cg_checkpoint_get(sip_handle* h, int slot, double* x_dev, double* r_dev, double* p_dev,
+                           double* rr_host, int* iter_host, void* stream);
+/* Runs `iters` FP64 CG iterations starting from a state (x, r, p, rr) and
+ * writes the resulting state back in place (replay from a checkpoint). */
+int  sip_cg_replay(sip_handle* h, double* x_dev, double* r_dev, double* p_dev, double* rr_host,
+                   int iters, void* stream);
+
+/* kbar[q] (+)= w_q |J_q| grad ybar_h(x_q) . grad x_h(x_q) per volume Gauss
+ * point: d(ybar^T A(kappa) x)/d kappa_q.  ybar, x: double [ndof];
+ * kbar: double [nquad]; accumulate != 0 adds to kbar. */
+int  sip_grad_kappa(sip_handle* h, const double* ybar_dev, const double* x_dev, double* kbar_dev,
+                    int accumulate, void* stream);
+
+/* *out_dev = a^T M b with the (P+2)-point volume rule: d(a^T A(lambda) b)/d lambda. */
+int  sip_mass_dot(sip_handle* h, const double* a_dev, const double* b_dev, double* out_dev,
+                  void* stream);
+
+/* b_i = sum_q w_q |J_q| phi_i(x_q) f_q (IProduct, Eq. iproduct). f: double [nquad]. */
+int  sip_iproduct(sip_handle* h, const double* f_dev, double* b_dev, void* stream);
+
+/* Physical coordinates of the volume Gauss points: double [nquad][dim]. */
+int  sip_quad_points(sip_handle* h, double* xq_dev, void* stream);
+
+/* Algorithmic work of one apply (per RHS) under the library's work model:
+ * flops of the trace kernel and of the main kernel, and the minimum DRAM bytes
+ * (x read, y written, geometry and face data read, traces written and read). */
+typedef struct sip_work {
+    double flops_trace, flops_main;
+    double bytes_x, bytes_y, bytes_geometry, bytes_trace;
+} sip_work;
+int  sip_work_model(const sip_handle* h, int precision, sip_work* out);
+
+/* Device time of the last apply's kernels, per phase, measured with CUDA events
+ * on the apply's stream when timing is enabled (sip_set_timing(h, 1)); ms. */
+int  sip_set_timing(sip_handle* h, int enable);
+int  sip_last_kernel_ms(sip_handle* h, float* trace_ms, float* main_ms);
+
+const char* sip_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIP_H */

@@ -148,8 +148,14 @@ class SipOracle:
         self.ndof = int(self.off[-1])
         self.kappa = kappa
         self._ref = {}
-        self._vol = np.array([self._element_geometry(e)[4].sum() for e in range(self.E)])
+        self._vol_cache = {}
         self._build_faces()
+
+    def volume(self, e):
+        """|K| by the element's own Gauss rule."""
+        if e not in self._vol_cache:
+            self._vol_cache[e] = self._element_geometry(e)[4].sum()
+        return self._vol_cache[e]
 
     # ---- reference data per (N, Q)
     def _ref_volume(self, n, q):
@@ -242,7 +248,7 @@ class SipOracle:
         nvec = nraw / nrm[:, None]
         W = wz * np.abs(np.linalg.det(Jm)) * nrm
         area = W.sum()
-        h = min(self._vol[em], self._vol[ep]) / area
+        h = min(self.volume(em), self.volume(ep)) / area
         tau = self.tau_scale * (max(self.P[em], self.P[ep]) + 1) ** 2 / h
         dnm = np.einsum("pib,pi->pb", gm, nvec)
         dnp = np.einsum("pib,pi->pb", gp, nvec)
@@ -262,7 +268,7 @@ class SipOracle:
         nrm = np.linalg.norm(nraw, axis=1)
         nvec = nraw / nrm[:, None]
         W = wz * np.abs(np.linalg.det(J)) * nrm
-        h = self._vol[e] / W.sum()
+        h = self.volume(e) / W.sum()
         tau = self.tau_scale * (self.P[e] + 1) ** 2 / h
         dn = np.einsum("pib,pi->pb", g, nvec)
         return W, nvec, tau, phi, dn

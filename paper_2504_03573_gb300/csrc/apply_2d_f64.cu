@@ -1,0 +1,4 @@
+// Apply kernels, 2D, double.
+#include "apply_launch.cuh"
+SIP_DEFINE_APPLY_TU(2d_f64, double, 2)
+SIP_DEFINE_AUX_TU(2)

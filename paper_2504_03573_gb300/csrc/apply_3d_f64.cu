@@ -1,0 +1,4 @@
+// Apply kernels, 3D, double.
+#include "apply_launch.cuh"
+SIP_DEFINE_APPLY_TU(3d_f64, double, 3)
+SIP_DEFINE_AUX_TU(3)

@@ -1,0 +1,48 @@
+// Launch wrapper instantiated once per (dimension, precision) translation unit.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "apply_kernels.cuh"
+
+#define SIP_DEFINE_APPLY_TU(SUFFIX, TYPE, DIM)                                                     \
+  namespace sip {                                                                                 \
+  cudaError_t upload_tables_##SUFFIX(const double* tab_d, const float* tab_f, const int* ioff) {   \
+    cudaError_t e = cudaMemcpyToSymbol(c_tab_d, tab_d, sizeof(double) * kTabSize);                 \
+    if (e != cudaSuccess) return e;                                                               \
+    e = cudaMemcpyToSymbol(c_tab_f, tab_f, sizeof(float) * kTabSize);                             \
+    if (e != cudaSuccess) return e;                                                               \
+    return cudaMemcpyToSymbol(c_ioff, ioff, sizeof(int) * (kQMax + 1) * (kQMax + 1));             \
+  }                                                                                               \
+  cudaError_t prepare_##SUFFIX() {                                                                 \
+    cudaError_t e = cudaFuncSetAttribute(k_trace<TYPE, DIM>,                                      \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
+    if (e != cudaSuccess) return e;                                                               \
+    return cudaFuncSetAttribute(k_main<TYPE, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                200 * 1024);                                                      \
+  }                                                                                               \
+  cudaError_t launch_apply_##SUFFIX(const ApplyArgs<TYPE>& a, int ntiles, int nrhs,               \
+                                    size_t smem_trace, size_t smem_main, cudaStream_t s,          \
+                                    cudaEvent_t ev0, cudaEvent_t ev1, cudaEvent_t ev2) {          \
+    if (ntiles == 0) return cudaSuccess;                                                          \
+    dim3 grid(ntiles, nrhs);                                                                      \
+    if (ev0) cudaEventRecord(ev0, s);                                                             \
+    k_trace<TYPE, DIM><<<grid, 256, smem_trace, s>>>(a);                                          \
+    if (ev1) cudaEventRecord(ev1, s);                                                             \
+    k_main<TYPE, DIM><<<grid, 256, smem_main, s>>>(a);                                            \
+    if (ev2) cudaEventRecord(ev2, s);                                                             \
+    return cudaGetLastError();                                                                    \
+  }                                                                                               \
+  }
+
+#define SIP_DEFINE_AUX_TU(DIM)                                                                   \
+  namespace sip {                                                                                \
+  cudaError_t prepare_aux_##DIM##d() {                                                           \
+    return cudaFuncSetAttribute(k_aux<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                                200 * 1024);                                                     \
+  }                                                                                              \
+  cudaError_t launch_aux_##DIM##d(const AuxArgs& a, int ntiles, size_t smem, cudaStream_t s) {   \
+    if (ntiles == 0) return cudaSuccess;                                                         \
+    k_aux<DIM><<<ntiles, 256, smem, s>>>(a);                                                     \
+    return cudaGetLastError();                                                                   \
+  }                                                                                              \
+  }

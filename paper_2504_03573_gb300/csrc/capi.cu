@@ -1,0 +1,368 @@
+// C ABI: plan, handle life cycle, apply, queries.  Solver and gradient entry
+// points live in solver.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "apply_kernels.cuh"
+#include "handle.h"
+
+namespace sip {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? SIP_ERR_OOM : SIP_ERR_CUDA;
+}
+
+int apply_epb(int dim, int n, int /*precision*/) {
+  const int per = smem_per_element(dim, n, true) * (int)sizeof(double);
+  const int cap = dim == 2 ? 32 : 8;
+  int epb = (48 * 1024) / per;
+  return std::max(1, std::min(cap, epb));
+}
+
+cudaError_t upload_tables_2d_f64(const double*, const float*, const int*);
+cudaError_t upload_tables_2d_f32(const double*, const float*, const int*);
+cudaError_t upload_tables_3d_f64(const double*, const float*, const int*);
+cudaError_t upload_tables_3d_f32(const double*, const float*, const int*);
+cudaError_t prepare_2d_f64();
+cudaError_t prepare_2d_f32();
+cudaError_t prepare_3d_f64();
+cudaError_t prepare_3d_f32();
+cudaError_t prepare_aux_2d();
+cudaError_t prepare_aux_3d();
+cudaError_t launch_apply_2d_f64(const ApplyArgs<double>&, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
+cudaError_t launch_apply_3d_f64(const ApplyArgs<double>&, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
+cudaError_t launch_apply_2d_f32(const ApplyArgs<float>&, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
+cudaError_t launch_apply_3d_f32(const ApplyArgs<float>&, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+bool g_tables_uploaded[kMaxDevices] = {false};
+
+template <typename T>
+cudaError_t upload(T** dst, const void* src, size_t bytes) {
+  cudaError_t e = cudaMalloc((void**)dst, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) return e;
+  if (bytes) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  return e;
+}
+
+template <typename T>
+std::vector<float> to_float(const std::vector<T>& v) {
+  std::vector<float> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
+  return o;
+}
+
+int ensure_tables(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(SIP_ERR_CUDA, "device index out of range");
+  if (g_tables_uploaded[dev]) return SIP_OK;
+  std::vector<double> tab;
+  fill_tables(tab);
+  std::vector<float> tabf = to_float(tab);
+  int ioff[kQMax + 1][kQMax + 1];
+  for (int q = 0; q <= kQMax; ++q)
+    for (int f = 0; f <= kQMax; ++f) ioff[q][f] = (q >= kQMin && f > q) ? tab_I(q, f) : 0;
+  cudaError_t e;
+  if ((e = upload_tables_2d_f64(tab.data(), tabf.data(), &ioff[0][0])) != cudaSuccess) return cuda_fail(e, "tables");
+  if ((e = upload_tables_2d_f32(tab.data(), tabf.data(), &ioff[0][0])) != cudaSuccess) return cuda_fail(e, "tables");
+  if ((e = upload_tables_3d_f64(tab.data(), tabf.data(), &ioff[0][0])) != cudaSuccess) return cuda_fail(e, "tables");
+  if ((e = upload_tables_3d_f32(tab.data(), tabf.data(), &ioff[0][0])) != cudaSuccess) return cuda_fail(e, "tables");
+  // dynamic shared-memory limits, set once per device (never during a stream capture)
+  for (auto fn : {prepare_2d_f64, prepare_2d_f32, prepare_3d_f64, prepare_3d_f32, prepare_aux_2d, prepare_aux_3d})
+    if ((e = fn()) != cudaSuccess) return cuda_fail(e, "kernel attributes");
+  g_tables_uploaded[dev] = true;
+  return SIP_OK;
+}
+
+}  // namespace
+
+int handle_grow_trace(sip_handle* h, int nrhs) {
+  const size_t need = (size_t)nrhs * 4 * (size_t)h->plan.trace_points;
+  if (need <= h->trace_cap) return SIP_OK;
+  if (h->trace_d) cudaFree(h->trace_d);
+  h->trace_d = nullptr;
+  h->trace_cap = 0;
+  cudaError_t e = cudaMalloc((void**)&h->trace_d, need * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(e, "trace buffer");
+  h->trace_cap = need;
+  return SIP_OK;
+}
+
+template <typename T>
+ApplyArgs<T> make_args(sip_handle* h, const T* x, T* y, T* trace, int transpose) {
+  ApplyArgs<T> a;
+  const DevGeom<T>& g = h->geom<T>();
+  a.dof_off = h->dof_off;
+  a.vgoff = h->vgoff;
+  a.vgeo = g.vgeo;
+  a.quad_off = h->quad_off;
+  a.kappa = h->kappa_set ? g.kappa : nullptr;
+  a.slots = h->slots;
+  a.f_troff = h->f_troff;
+  a.f_goff = h->f_goff;
+  a.f_tau = g.tau;
+  a.fgeo = g.fgeo;
+  a.elist = h->elist;
+  a.tiles = h->tiles;
+  a.x = x;
+  a.y = y;
+  a.trace = trace;
+  a.ndof = h->plan.ndof;
+  a.trace_stride = 4 * h->plan.trace_points;
+  a.lambda = (T)h->lambda;
+  a.transpose = transpose;
+  return a;
+}
+
+int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cudaStream_t s,
+              int transpose, void* trace_override) {
+  if (!h || !x || !y) return fail(SIP_ERR_ARG, "null handle or vector");
+  if (nrhs < 1) return fail(SIP_ERR_ARG, "nrhs must be >= 1");
+  if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
+  if (!trace_override) {
+    int rc = handle_grow_trace(h, nrhs);
+    if (rc) return rc;
+  }
+  const int nt = (int)h->plan.tiles.size();
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  if (h->timing) { e0 = h->ev[0]; e1 = h->ev[1]; e2 = h->ev[2]; }
+  cudaError_t e;
+  if (precision == SIP_FP64) {
+    double* tr = trace_override ? (double*)trace_override : h->trace_d;
+    auto a = make_args<double>(h, (const double*)x, (double*)y, tr, transpose);
+    e = h->plan.dim == 2 ? launch_apply_2d_f64(a, nt, nrhs, h->smem_trace[0], h->smem_main[0], s, e0, e1, e2)
+                         : launch_apply_3d_f64(a, nt, nrhs, h->smem_trace[0], h->smem_main[0], s, e0, e1, e2);
+  } else {
+    float* tr = trace_override ? (float*)trace_override : (float*)h->trace_d;
+    auto a = make_args<float>(h, (const float*)x, (float*)y, tr, transpose);
+    e = h->plan.dim == 2 ? launch_apply_2d_f32(a, nt, nrhs, h->smem_trace[1], h->smem_main[1], s, e0, e1, e2)
+                         : launch_apply_3d_f32(a, nt, nrhs, h->smem_trace[1], h->smem_main[1], s, e0, e1, e2);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "apply launch");
+  h->timed_pending = h->timing;
+  return SIP_OK;
+}
+
+}  // namespace sip
+
+using namespace sip;
+
+extern "C" {
+
+const char* sip_last_error(void) { return g_err.c_str(); }
+
+void sip_options_default(sip_options* o) {
+  if (!o) return;
+  o->tau_scale = 2.0;
+  o->qvol_extra = 2;
+  o->boundary = 1;
+  o->inner_rtol = 1e-5;
+  o->max_iter = 20000;
+  o->check_every = 16;
+  o->max_refine = 30;
+  o->checkpoint_every = 0;
+  o->checkpoint_slots = 8;
+}
+
+struct sip_plan {
+  Plan p;
+};
+
+static void fill_info(const Plan& p, sip_plan_info* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->dim = p.dim;
+  out->n_elem = p.E;
+  out->ndof = p.ndof;
+  out->nquad = p.nquad;
+  out->n_faces_interior = p.n_int;
+  out->n_faces_boundary = p.n_bnd;
+  out->n_faces_nonconforming = p.n_nonconf;
+  for (int8_t a : p.affine) out->n_elem_affine += a;
+  for (int i = 0; i < 8; ++i) out->orient_hist[i] = p.orient_hist[i];
+  for (int32_t o : p.P) out->order_hist[o] += 1;
+  out->trace_points = p.trace_points;
+  double hmin = 1e300, tmax = 0.0;
+  for (size_t f = 0; f < p.f_tau.size(); ++f) {
+    const int pm = p.f_ep[f] >= 0 ? std::max(p.P[p.f_em[f]], p.P[p.f_ep[f]]) : p.P[p.f_em[f]];
+    const double h = p.opt.tau_scale * (pm + 1.0) * (pm + 1.0) / p.f_tau[f];
+    hmin = std::min(hmin, h);
+    tmax = std::max(tmax, p.f_tau[f]);
+  }
+  out->min_h_face = hmin;
+  out->max_tau = tmax;
+}
+
+int sip_plan_create(const sip_mesh* mesh, const int32_t* orders, const sip_options* opt, sip_plan** out) {
+  if (!out) return fail(SIP_ERR_ARG, "null out");
+  *out = nullptr;
+  sip_plan* p = new sip_plan();
+  std::string err;
+  int rc = build_plan(mesh, orders, opt, p->p, err);
+  if (rc != SIP_OK) {
+    delete p;
+    return fail(rc, err);
+  }
+  *out = p;
+  return SIP_OK;
+}
+
+int sip_plan_info_get(const sip_plan* plan, sip_plan_info* out) {
+  if (!plan || !out) return fail(SIP_ERR_ARG, "null plan or out");
+  fill_info(plan->p, out);
+  return SIP_OK;
+}
+
+void sip_plan_destroy(sip_plan* plan) { delete plan; }
+
+void sip_destroy(sip_handle* h) {
+  if (!h) return;
+  h->release();
+  delete h;
+}
+
+int sip_create(const sip_mesh* mesh, const int32_t* orders, double lambda, const sip_options* opt,
+               sip_handle** out) {
+  if (!out) return fail(SIP_ERR_ARG, "null out");
+  *out = nullptr;
+  if (!(lambda >= 0.0)) return fail(SIP_ERR_ARG, "lambda must be >= 0");
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(SIP_ERR_NO_DEVICE, std::string("no CUDA device: ") + cudaGetErrorString(ce));
+  }
+  sip_handle* h = new sip_handle();
+  std::string err;
+  int rc = build_plan(mesh, orders, opt, h->plan, err);
+  if (rc != SIP_OK) {
+    delete h;
+    return fail(rc, err);
+  }
+  h->lambda = lambda;
+  cudaGetDevice(&h->device);
+  rc = ensure_tables(h->device);
+  if (rc) { delete h; return rc; }
+  const Plan& p = h->plan;
+  cudaError_t e = cudaSuccess;
+#define UP(dst, vec) \
+  if (e == cudaSuccess) e = upload(&(dst), (vec).data(), (vec).size() * sizeof((vec)[0]))
+  UP(h->dof_off, p.dof_off);
+  UP(h->quad_off, p.quad_off);
+  UP(h->vgoff, p.vgoff);
+  UP(h->f_troff, p.f_troff);
+  UP(h->f_goff, p.f_goff);
+  UP(h->slots, p.slots);
+  UP(h->elist, p.elist);
+  UP(h->tiles, p.tiles);
+  UP(h->gd.vgeo, p.vgeo);
+  UP(h->gd.fgeo, p.fgeo);
+  UP(h->gd.tau, p.f_tau);
+  std::vector<float> vf = to_float(p.vgeo), ff = to_float(p.fgeo), tf = to_float(p.f_tau);
+  UP(h->gf.vgeo, vf);
+  UP(h->gf.fgeo, ff);
+  UP(h->gf.tau, tf);
+  UP(h->xq, p.xq);
+#undef UP
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->gd.kappa, std::max<size_t>(16, p.nquad * sizeof(double)));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->gf.kappa, std::max<size_t>(16, p.nquad * sizeof(float)));
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "sip_create upload");
+    sip_destroy(h);
+    return rc;
+  }
+  // shared memory per launch: max over the tiles' orders
+  for (int prec = 0; prec < 2; ++prec) {
+    size_t st = 0, sm = 0;
+    const size_t es = prec == 0 ? sizeof(double) : sizeof(float);
+    for (const Tile& t : p.tiles) {
+      const int epb = apply_epb(p.dim, t.n, prec);
+      st = std::max(st, (size_t)epb * smem_per_element(p.dim, t.n, false) * es);
+      sm = std::max(sm, (size_t)epb * smem_per_element(p.dim, t.n, true) * es);
+    }
+    h->smem_trace[prec] = st;
+    h->smem_main[prec] = sm;
+  }
+  rc = handle_grow_trace(h, 1);
+  if (rc) { sip_destroy(h); return rc; }
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "sip_create sync");
+    sip_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return SIP_OK;
+}
+
+int64_t sip_num_dofs(const sip_handle* h) { return h ? h->plan.ndof : -1; }
+int64_t sip_num_quad(const sip_handle* h) { return h ? h->plan.nquad : -1; }
+
+int sip_dof_offsets(const sip_handle* h, int64_t* out) {
+  if (!h || !out) return fail(SIP_ERR_ARG, "null handle or out");
+  std::memcpy(out, h->plan.dof_off.data(), h->plan.dof_off.size() * sizeof(int64_t));
+  return SIP_OK;
+}
+
+int sip_quad_offsets(const sip_handle* h, int64_t* out) {
+  if (!h || !out) return fail(SIP_ERR_ARG, "null handle or out");
+  std::memcpy(out, h->plan.quad_off.data(), h->plan.quad_off.size() * sizeof(int64_t));
+  return SIP_OK;
+}
+
+int sip_get_plan_info(const sip_handle* h, sip_plan_info* out) {
+  if (!h || !out) return fail(SIP_ERR_ARG, "null handle or out");
+  fill_info(h->plan, out);
+  return SIP_OK;
+}
+
+int sip_set_lambda(sip_handle* h, double lambda) {
+  if (!h) return fail(SIP_ERR_ARG, "null handle");
+  if (!(lambda >= 0.0)) return fail(SIP_ERR_ARG, "lambda must be >= 0");
+  h->lambda = lambda;
+  // lambda is a kernel argument captured in the CG graphs: drop them
+  for (auto* W : {&h->cg64, &h->cg32})
+    if (W->graph) { cudaGraphExecDestroy(W->graph); W->graph = nullptr; }
+  return SIP_OK;
+}
+
+int sip_apply(sip_handle* h, int precision, const void* x, void* y, int nrhs, void* stream) {
+  return apply_any(h, precision, x, y, nrhs, (cudaStream_t)stream, 0, nullptr);
+}
+
+int sip_apply_transpose(sip_handle* h, int precision, const void* x, void* y, int nrhs, void* stream) {
+  return apply_any(h, precision, x, y, nrhs, (cudaStream_t)stream, 1, nullptr);
+}
+
+int sip_set_timing(sip_handle* h, int enable) {
+  if (!h) return fail(SIP_ERR_ARG, "null handle");
+  h->timing = enable != 0;
+  return SIP_OK;
+}
+
+int sip_last_kernel_ms(sip_handle* h, float* trace_ms, float* main_ms) {
+  if (!h || !trace_ms || !main_ms) return fail(SIP_ERR_ARG, "null argument");
+  if (!h->timed_pending) return fail(SIP_ERR_ARG, "no timed apply since timing was enabled");
+  cudaError_t e = cudaEventSynchronize(h->ev[2]);
+  if (e != cudaSuccess) return cuda_fail(e, "event sync");
+  cudaEventElapsedTime(trace_ms, h->ev[0], h->ev[1]);
+  cudaEventElapsedTime(main_ms, h->ev[1], h->ev[2]);
+  return SIP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// sip_handle internals (host side).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "sip_internal.h"
+
+namespace sip {
+
+template <typename T>
+struct DevGeom {
+  T* vgeo = nullptr;
+  T* fgeo = nullptr;
+  T* tau = nullptr;
+  T* kappa = nullptr;
+};
+
+// CG workspace for one (vector type, nrhs) configuration
+struct CgWork {
+  int nrhs = 0;
+  size_t elem = 0;          // bytes per vector element (8 or 4)
+  void* x = nullptr;        // iterate (internal, so captured graphs stay valid)
+  void* r = nullptr;
+  void* p = nullptr;
+  void* ap = nullptr;
+  double* scal = nullptr;   // per RHS: rr, pap, alpha, beta, rr_new, active, scratch...
+  double* partial = nullptr;
+  int* status = nullptr;    // device status word (breakdown / non-finite)
+  cudaGraphExec_t graph = nullptr;
+  int graph_iters = 0;
+  int graph_transpose = -1;
+  void release();
+};
+
+}  // namespace sip
+
+struct sip_handle {
+  sip::Plan plan;
+  int device = 0;
+  double lambda = 1.0;
+  bool kappa_set = false;
+  // device tables
+  int64_t* dof_off = nullptr;
+  int64_t* quad_off = nullptr;
+  int64_t* vgoff = nullptr;
+  int64_t* f_troff = nullptr;
+  int64_t* f_goff = nullptr;
+  sip::FaceSlot* slots = nullptr;
+  int32_t* elist = nullptr;
+  sip::Tile* tiles = nullptr;
+  double* xq = nullptr;
+  sip::DevGeom<double> gd;
+  sip::DevGeom<float> gf;
+  template <typename T>
+  const sip::DevGeom<T>& geom() const;
+  // scratch: trace buffer (sized for the largest nrhs seen, in doubles)
+  double* trace_d = nullptr;
+  size_t trace_cap = 0;
+  size_t smem_trace[2] = {0, 0};
+  size_t smem_main[2] = {0, 0};
+  // timing
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool timing = false;
+  bool timed_pending = false;
+  // solver state
+  cudaStream_t solve_stream = nullptr;
+  sip::CgWork cg64, cg32;
+  double* r64 = nullptr;     // outer residual / true residual workspace [nrhs][ndof]
+  double* x64 = nullptr;     // outer iterate
+  double* red = nullptr;     // reduction partials for aux kernels
+  double* scal_host = nullptr;
+  int work_nrhs = 0;
+  // checkpoints (FP64 CG, nrhs = 1)
+  std::vector<double*> ck_x, ck_r, ck_p;
+  std::vector<double> ck_rr;
+  std::vector<int> ck_iter;
+  int ck_count = 0, ck_next = 0;
+  void release();
+};
+
+template <>
+inline const sip::DevGeom<double>& sip_handle::geom<double>() const { return gd; }
+template <>
+inline const sip::DevGeom<float>& sip_handle::geom<float>() const { return gf; }
+
+namespace sip {
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* where);
+int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cudaStream_t s,
+              int transpose, void* trace_override);
+int handle_grow_trace(sip_handle* h, int nrhs);
+}  // namespace sip

@@ -1,0 +1,414 @@
+// Host mesh analysis for the SIP apply: face pairing, plus-side orientation,
+// geometric factors at volume and face quadrature points, penalties, order
+// buckets.  Runs once per mesh (the paper's preprocessing: traces and
+// trace-conforming elements of Sec. 3.3, orientations of Sec. 5.1, element
+// groups of equal order of Sec. 5.1).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "sip_internal.h"
+
+namespace sip {
+
+namespace {
+
+struct Geo {
+  double x[3];
+  double J[3][3];   // J[i][m] = d x_i / d xi_m
+  double Ji[3][3];  // inverse: Ji[m][i] = d xi_m / d x_i
+  double det;
+};
+
+// multilinear map of one element at reference point xi
+void eval_map(int dim, const double* v /* [2^dim][dim] */, const double* xi, Geo& g) {
+  for (int i = 0; i < 3; ++i) {
+    g.x[i] = 0.0;
+    for (int m = 0; m < 3; ++m) g.J[i][m] = 0.0;
+  }
+  const int nc = 1 << dim;
+  for (int c = 0; c < nc; ++c) {
+    double n[3], dn[3];
+    for (int k = 0; k < dim; ++k) {
+      const int b = (c >> k) & 1;
+      n[k] = b ? 0.5 * (1.0 + xi[k]) : 0.5 * (1.0 - xi[k]);
+      dn[k] = b ? 0.5 : -0.5;
+    }
+    double shape = 1.0;
+    for (int k = 0; k < dim; ++k) shape *= n[k];
+    for (int i = 0; i < dim; ++i) g.x[i] += shape * v[c * dim + i];
+    for (int m = 0; m < dim; ++m) {
+      double ds = dn[m];
+      for (int k = 0; k < dim; ++k)
+        if (k != m) ds *= n[k];
+      for (int i = 0; i < dim; ++i) g.J[i][m] += ds * v[c * dim + i];
+    }
+  }
+  if (dim == 2) {
+    g.det = g.J[0][0] * g.J[1][1] - g.J[0][1] * g.J[1][0];
+    const double id = 1.0 / g.det;
+    g.Ji[0][0] = g.J[1][1] * id;
+    g.Ji[0][1] = -g.J[0][1] * id;
+    g.Ji[1][0] = -g.J[1][0] * id;
+    g.Ji[1][1] = g.J[0][0] * id;
+  } else {
+    const auto& a = g.J;
+    const double c00 = a[1][1] * a[2][2] - a[1][2] * a[2][1];
+    const double c01 = a[1][2] * a[2][0] - a[1][0] * a[2][2];
+    const double c02 = a[1][0] * a[2][1] - a[1][1] * a[2][0];
+    g.det = a[0][0] * c00 + a[0][1] * c01 + a[0][2] * c02;
+    const double id = 1.0 / g.det;
+    g.Ji[0][0] = c00 * id;
+    g.Ji[1][0] = c01 * id;
+    g.Ji[2][0] = c02 * id;
+    g.Ji[0][1] = (a[0][2] * a[2][1] - a[0][1] * a[2][2]) * id;
+    g.Ji[1][1] = (a[0][0] * a[2][2] - a[0][2] * a[2][0]) * id;
+    g.Ji[2][1] = (a[0][1] * a[2][0] - a[0][0] * a[2][1]) * id;
+    g.Ji[0][2] = (a[0][1] * a[1][2] - a[0][2] * a[1][1]) * id;
+    g.Ji[1][2] = (a[0][2] * a[1][0] - a[0][0] * a[1][2]) * id;
+    g.Ji[2][2] = (a[0][0] * a[1][1] - a[0][1] * a[1][0]) * id;
+  }
+}
+
+// local corner of face (axis a, side s) with tangential bits b0 (+ b1)
+int face_corner(int dim, int a, int s, int b0, int b1) {
+  int t[2], nt = 0;
+  for (int k = 0; k < dim; ++k)
+    if (k != a) t[nt++] = k;
+  int c = s << a;
+  c |= b0 << t[0];
+  if (dim == 3) c |= b1 << t[1];
+  return c;
+}
+
+struct FaceKey {
+  std::array<int64_t, 4> v;
+  int32_t e, k;
+  bool operator<(const FaceKey& o) const {
+    if (v != o.v) return v < o.v;
+    if (e != o.e) return e < o.e;
+    return k < o.k;
+  }
+};
+
+// plus-side own tangential index j -> canonical (minus) index z, per orientation
+inline void orient_map(int dim, int code, int qf, const int j[2], int z[2]) {
+  if (dim == 2) {
+    z[0] = (code & 1) ? qf - 1 - j[0] : j[0];
+    z[1] = 0;
+    return;
+  }
+  const int perm0 = (code & 4) ? 1 : 0, perm1 = (code & 4) ? 0 : 1;
+  z[perm0] = (code & 1) ? qf - 1 - j[0] : j[0];
+  z[perm1] = (code & 2) ? qf - 1 - j[1] : j[1];
+}
+
+}  // namespace
+
+int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* opt_in, Plan& p,
+               std::string& err) {
+  if (!mesh || !orders) { err = "null mesh or orders"; return SIP_ERR_ARG; }
+  const int dim = mesh->dim;
+  if (dim != 2 && dim != 3) { err = "dim must be 2 or 3"; return SIP_ERR_ARG; }
+  if (mesh->n_elem < 1 || mesh->n_vert < 1 || !mesh->vert || !mesh->elem_vert) {
+    err = "empty mesh or null arrays"; return SIP_ERR_ARG;
+  }
+  sip_options opt;
+  if (opt_in) opt = *opt_in; else sip_options_default(&opt);
+  if (opt.qvol_extra != 2) { err = "only qvol_extra = 2 (Q = P + 2) is supported"; return SIP_ERR_ARG; }
+  if (!(opt.tau_scale > 0.0)) { err = "tau_scale must be > 0"; return SIP_ERR_ARG; }
+  p.opt = opt;
+  p.dim = dim;
+  const int64_t E = mesh->n_elem;
+  p.E = E;
+  const int nc = 1 << dim, nf = 2 * dim;
+  for (int64_t e = 0; e < E; ++e) {
+    if (orders[e] < 1 || orders[e] > kMaxOrder) {
+      err = "element " + std::to_string(e) + ": order outside 1.." + std::to_string(kMaxOrder);
+      return SIP_ERR_ARG;
+    }
+    for (int c = 0; c < nc; ++c) {
+      int64_t v = mesh->elem_vert[e * nc + c];
+      if (v < 0 || v >= mesh->n_vert) {
+        err = "element " + std::to_string(e) + ": vertex id out of range"; return SIP_ERR_ARG;
+      }
+    }
+  }
+  p.P.assign(orders, orders + E);
+  p.dof_off.assign(E + 1, 0);
+  p.quad_off.assign(E + 1, 0);
+  for (int64_t e = 0; e < E; ++e) {
+    int64_t n = p.P[e] + 1, q = p.P[e] + 2;
+    p.dof_off[e + 1] = p.dof_off[e] + (dim == 2 ? n * n : n * n * n);
+    p.quad_off[e + 1] = p.quad_off[e] + (dim == 2 ? q * q : q * q * q);
+  }
+  p.ndof = p.dof_off[E];
+  p.nquad = p.quad_off[E];
+
+  // element corner coordinates
+  std::vector<double> ev((size_t)E * nc * dim);
+  for (int64_t e = 0; e < E; ++e)
+    for (int c = 0; c < nc; ++c)
+      for (int i = 0; i < dim; ++i)
+        ev[(e * nc + c) * dim + i] = mesh->vert[mesh->elem_vert[e * nc + c] * dim + i];
+
+  // ---- volume geometry
+  std::vector<double> xg, wg;
+  const int nG = dim == 2 ? 4 : 7;
+  p.vgoff.assign(E + 1, 0);
+  for (int64_t e = 0; e < E; ++e) p.vgoff[e + 1] = p.vgoff[e] + (int64_t)nG * (p.quad_off[e + 1] - p.quad_off[e]);
+  p.vgeo.assign(p.vgoff[E], 0.0);
+  p.xq.assign((size_t)p.nquad * dim, 0.0);
+  p.vol.assign(E, 0.0);
+  p.affine.assign(E, 0);
+  for (int64_t e = 0; e < E; ++e) {
+    const int Q = p.P[e] + 2;
+    gauss_legendre(Q, xg, wg);
+    const double* v = &ev[(size_t)e * nc * dim];
+    const int nq = dim == 2 ? Q * Q : Q * Q * Q;
+    double* G = &p.vgeo[p.vgoff[e]];
+    double vol = 0.0;
+    for (int q = 0; q < nq; ++q) {
+      int qi[3] = {q % Q, (q / Q) % Q, q / (Q * Q)};
+      double xi[3], w = 1.0;
+      for (int k = 0; k < dim; ++k) { xi[k] = xg[qi[k]]; w *= wg[qi[k]]; }
+      Geo g;
+      eval_map(dim, v, xi, g);
+      if (!(g.det > 0.0)) {
+        err = "element " + std::to_string(e) + ": non-positive Jacobian at a volume Gauss point";
+        return SIP_ERR_MESH;
+      }
+      const double wj = w * g.det;
+      vol += wj;
+      // G = w|J| Ji Ji^T  (Ji[m][i] = d xi_m / d x_i)
+      double Gm[3][3];
+      for (int a = 0; a < dim; ++a)
+        for (int b = 0; b < dim; ++b) {
+          double s = 0.0;
+          for (int i = 0; i < dim; ++i) s += g.Ji[a][i] * g.Ji[b][i];
+          Gm[a][b] = wj * s;
+        }
+      if (dim == 2) {
+        G[0 * nq + q] = Gm[0][0]; G[1 * nq + q] = Gm[0][1]; G[2 * nq + q] = Gm[1][1];
+        G[3 * nq + q] = wj;
+      } else {
+        G[0 * nq + q] = Gm[0][0]; G[1 * nq + q] = Gm[0][1]; G[2 * nq + q] = Gm[0][2];
+        G[3 * nq + q] = Gm[1][1]; G[4 * nq + q] = Gm[1][2]; G[5 * nq + q] = Gm[2][2];
+        G[6 * nq + q] = wj;
+      }
+      for (int i = 0; i < dim; ++i) p.xq[(size_t)(p.quad_off[e] + q) * dim + i] = g.x[i];
+    }
+    p.vol[e] = vol;
+    // affine iff every mixed (bi/tri-linear) coefficient of the map vanishes
+    double hmax = 0.0, mixed = 0.0;
+    for (int c = 1; c < nc; ++c)
+      for (int i = 0; i < dim; ++i) hmax = std::max(hmax, std::fabs(v[c * dim + i] - v[i]));
+    for (int m = 3; m < nc; ++m) {
+      if ((m & (m - 1)) == 0) continue;  // single-axis terms are the linear part
+      for (int i = 0; i < dim; ++i) {
+        double s = 0.0;
+        for (int c = 0; c < nc; ++c) {
+          if ((c & ~m) != 0) continue;   // corners inside the sub-cube spanned by m
+          const int par = __builtin_popcount((unsigned)(m & ~c)) & 1;
+          s += par ? -v[c * dim + i] : v[c * dim + i];
+        }
+        mixed = std::max(mixed, std::fabs(s));
+      }
+    }
+    p.affine[e] = mixed <= 1e-13 * hmax ? 1 : 0;
+  }
+
+  // ---- face pairing by vertex sets
+  const int nfc = 1 << (dim - 1);
+  std::vector<FaceKey> keys;
+  keys.reserve((size_t)E * nf);
+  for (int64_t e = 0; e < E; ++e)
+    for (int k = 0; k < nf; ++k) {
+      const int a = k / 2, s = k % 2;
+      FaceKey fk;
+      fk.v = {-1, -1, -1, -1};
+      for (int c = 0; c < nfc; ++c) {
+        const int lc = face_corner(dim, a, s, c & 1, (c >> 1) & 1);
+        fk.v[c] = mesh->elem_vert[e * nc + lc];
+      }
+      std::sort(fk.v.begin(), fk.v.begin() + nfc);
+      for (int c = 1; c < nfc; ++c)
+        if (fk.v[c] == fk.v[c - 1]) {
+          err = "element " + std::to_string(e) + ": degenerate face (repeated vertex)";
+          return SIP_ERR_MESH;
+        }
+      fk.e = (int32_t)e;
+      fk.k = k;
+      keys.push_back(fk);
+    }
+  std::sort(keys.begin(), keys.end());
+  struct Pair { int32_t em, km, ep, kp; };
+  std::vector<Pair> inter, bnd;
+  for (size_t i = 0; i < keys.size();) {
+    size_t j = i + 1;
+    while (j < keys.size() && keys[j].v == keys[i].v) ++j;
+    if (j - i == 1) bnd.push_back({keys[i].e, keys[i].k, -1, -1});
+    else if (j - i == 2) {
+      if (keys[i].e == keys[i + 1].e) { err = "element glued to itself"; return SIP_ERR_MESH; }
+      inter.push_back({keys[i].e, keys[i].k, keys[i + 1].e, keys[i + 1].k});
+    } else {
+      err = "non-manifold face shared by more than two elements"; return SIP_ERR_MESH;
+    }
+    i = j;
+  }
+  auto cmp = [](const Pair& a, const Pair& b) { return a.em != b.em ? a.em < b.em : a.km < b.km; };
+  std::sort(inter.begin(), inter.end(), cmp);
+  std::sort(bnd.begin(), bnd.end(), cmp);
+  p.n_int = (int64_t)inter.size();
+  p.n_bnd = (int64_t)bnd.size();
+  const int64_t F = p.n_int + p.n_bnd;
+  p.f_em.resize(F); p.f_km.resize(F); p.f_ep.resize(F); p.f_kp.resize(F);
+  p.f_orient.assign(F, 0); p.f_qf.resize(F);
+  p.f_troff.assign(F + 1, 0); p.f_goff.assign(F + 1, 0); p.f_tau.assign(F, 0.0);
+  p.slots.assign((size_t)E * nf, FaceSlot{-1, 0, 0, 0, 0});
+  for (int64_t f = 0; f < F; ++f) {
+    const Pair& pr = f < p.n_int ? inter[f] : bnd[f - p.n_int];
+    p.f_em[f] = pr.em; p.f_km[f] = pr.km; p.f_ep[f] = pr.ep; p.f_kp[f] = pr.kp;
+    const int qm = p.P[pr.em] + 2;
+    const int qf = pr.ep >= 0 ? std::max(qm, p.P[pr.ep] + 2) : qm;
+    p.f_qf[f] = qf;
+    if (pr.ep >= 0 && p.P[pr.ep] != p.P[pr.em]) ++p.n_nonconf;
+    const int64_t npts = dim == 2 ? qf : (int64_t)qf * qf;
+    p.f_troff[f + 1] = p.f_troff[f] + npts;
+    p.f_goff[f + 1] = p.f_goff[f] + npts * (pr.ep >= 0 ? 1 + 2 * dim : 1 + dim);
+    if (pr.ep >= 0) {
+      // orientation: plus corner (beta0, beta1) must carry the same vertex as minus
+      // corner b with b_perm[m] = beta_m xor flip_m
+      const int am = pr.km / 2, sm = pr.km % 2, ap = pr.kp / 2, sp = pr.kp % 2;
+      int64_t gm[4], gp[4];
+      for (int c = 0; c < nfc; ++c) {
+        gm[c] = mesh->elem_vert[(int64_t)pr.em * nc + face_corner(dim, am, sm, c & 1, (c >> 1) & 1)];
+        gp[c] = mesh->elem_vert[(int64_t)pr.ep * nc + face_corner(dim, ap, sp, c & 1, (c >> 1) & 1)];
+      }
+      int found = -1;
+      const int ncode = dim == 2 ? 2 : 8;
+      for (int code = 0; code < ncode && found < 0; ++code) {
+        bool ok = true;
+        for (int c = 0; c < nfc && ok; ++c) {
+          int beta[2] = {c & 1, (c >> 1) & 1}, b[2] = {0, 0};
+          if (dim == 2) b[0] = beta[0] ^ (code & 1);
+          else {
+            const int p0 = (code & 4) ? 1 : 0, p1 = (code & 4) ? 0 : 1;
+            b[p0] = beta[0] ^ (code & 1);
+            b[p1] = beta[1] ^ ((code >> 1) & 1);
+          }
+          ok = gm[b[0] + 2 * b[1]] == gp[c];
+        }
+        if (ok) found = code;
+      }
+      if (found < 0) { err = "face " + std::to_string(f) + ": no orientation matches"; return SIP_ERR_MESH; }
+      p.f_orient[f] = found;
+      p.orient_hist[found] += 1;
+      p.slots[(size_t)pr.em * nf + pr.km] = FaceSlot{(int32_t)f, 0, 0, (int8_t)qf, 0};
+      p.slots[(size_t)pr.ep * nf + pr.kp] = FaceSlot{(int32_t)f, 1, (int8_t)found, (int8_t)qf, 0};
+    } else {
+      p.slots[(size_t)pr.em * nf + pr.km] = FaceSlot{(int32_t)f, 0, 0, (int8_t)qf, 1};
+    }
+  }
+  p.trace_points = p.f_troff[F];
+
+  // ---- face geometry in canonical (minus side) point order
+  p.fgeo.assign(p.f_goff[F], 0.0);
+  for (int64_t f = 0; f < F; ++f) {
+    const int qf = p.f_qf[f];
+    gauss_legendre(qf, xg, wg);
+    const int npts = dim == 2 ? qf : qf * qf;
+    const int em = p.f_em[f], km = p.f_km[f], ep = p.f_ep[f], kp = p.f_kp[f];
+    const int am = km / 2, sm = km % 2;
+    int tm[2], ntm = 0;
+    for (int k = 0; k < dim; ++k) if (k != am) tm[ntm++] = k;
+    double* fg = &p.fgeo[p.f_goff[f]];
+    double area = 0.0;
+    for (int z = 0; z < npts; ++z) {
+      const int zi[2] = {z % qf, z / qf};
+      double xi[3];
+      xi[am] = sm ? 1.0 : -1.0;
+      double w = 1.0;
+      for (int m = 0; m < dim - 1; ++m) { xi[tm[m]] = xg[zi[m]]; w *= wg[zi[m]]; }
+      Geo g;
+      eval_map(dim, &ev[(size_t)em * nc * dim], xi, g);
+      double nraw[3], nn = 0.0;
+      for (int i = 0; i < dim; ++i) { nraw[i] = (sm ? 1.0 : -1.0) * g.Ji[am][i]; nn += nraw[i] * nraw[i]; }
+      nn = std::sqrt(nn);
+      double n[3];
+      for (int i = 0; i < dim; ++i) n[i] = nraw[i] / nn;
+      const double W = w * std::fabs(g.det) * nn;
+      area += W;
+      fg[z] = W;
+      for (int m = 0; m < dim; ++m) {
+        double c = 0.0;
+        for (int i = 0; i < dim; ++i) c += g.Ji[m][i] * n[i];
+        fg[(1 + m) * npts + z] = c;
+      }
+      if (ep >= 0) {
+        // plus-side reference point of the same physical point: invert orient_map
+        const int ap = kp / 2, sp = kp % 2;
+        int tp[2], ntp = 0;
+        for (int k = 0; k < dim; ++k) if (k != ap) tp[ntp++] = k;
+        const int code = p.f_orient[f];
+        int jj[2] = {0, 0};
+        // find plus index j with orient_map(j) == zi (qf^(dim-1) candidates at most 100)
+        bool hit = false;
+        for (int j1 = 0; j1 < (dim == 3 ? qf : 1) && !hit; ++j1)
+          for (int j0 = 0; j0 < qf && !hit; ++j0) {
+            int jt[2] = {j0, j1}, zz[2];
+            orient_map(dim, code, qf, jt, zz);
+            if (zz[0] == zi[0] && (dim == 2 || zz[1] == zi[1])) { jj[0] = j0; jj[1] = j1; hit = true; }
+          }
+        double xip[3];
+        xip[ap] = sp ? 1.0 : -1.0;
+        for (int m = 0; m < dim - 1; ++m) xip[tp[m]] = xg[jj[m]];
+        Geo gp;
+        eval_map(dim, &ev[(size_t)ep * nc * dim], xip, gp);
+        double dx = 0.0, h = 0.0;
+        for (int i = 0; i < dim; ++i) {
+          dx = std::max(dx, std::fabs(gp.x[i] - g.x[i]));
+          h = std::max(h, std::fabs(g.J[i][0]) + std::fabs(g.J[i][1]) + (dim == 3 ? std::fabs(g.J[i][2]) : 0.0));
+        }
+        if (dx > 1e-11 * h) {
+          err = "face " + std::to_string(f) + ": sides do not coincide (mesh not conforming)";
+          return SIP_ERR_MESH;
+        }
+        for (int m = 0; m < dim; ++m) {
+          double c = 0.0;
+          for (int i = 0; i < dim; ++i) c -= gp.Ji[m][i] * n[i];   // c+ = J+^-1 (-n)
+          fg[(1 + dim + m) * npts + z] = c;
+        }
+      }
+    }
+    const double vmin = ep >= 0 ? std::min(p.vol[em], p.vol[ep]) : p.vol[em];
+    const double hf = vmin / area;
+    const int pmax = ep >= 0 ? std::max(p.P[em], p.P[ep]) : p.P[em];
+    p.f_tau[f] = opt.tau_scale * (pmax + 1.0) * (pmax + 1.0) / hf;
+    if (ep < 0 && !opt.boundary)  // pure-Neumann variant: boundary faces contribute nothing
+      for (int z = 0; z < npts; ++z) fg[z] = 0.0;
+  }
+
+  // ---- order buckets and tiles
+  p.elist.resize(E);
+  std::iota(p.elist.begin(), p.elist.end(), 0);
+  std::stable_sort(p.elist.begin(), p.elist.end(),
+                   [&](int32_t a, int32_t b) { return p.P[a] < p.P[b]; });
+  p.tiles.clear();
+  for (int64_t i = 0; i < E;) {
+    const int n = p.P[p.elist[i]] + 1;
+    int64_t j = i;
+    while (j < E && p.P[p.elist[j]] + 1 == n) ++j;
+    const int epb = apply_epb(dim, n, SIP_FP64);
+    for (int64_t s = i; s < j; s += epb)
+      p.tiles.push_back(Tile{n, (int32_t)s, (int32_t)std::min<int64_t>(epb, j - s), 0});
+    i = j;
+  }
+  return SIP_OK;
+}
+
+}  // namespace sip

@@ -1,0 +1,770 @@
+// Conjugate gradients on the SIP operator (Sec. 2.2: the symmetric SIP system
+// is solved by CG), FP64 and FP32-apply inside FP64 iterative refinement; and
+// the auxiliary entry points (kappa, gradients, IProduct, quadrature points,
+// work model).
+//
+// Every reduction is deterministic: fixed grid, fixed per-thread strides,
+// fixed-order shared-memory trees, then one fixed-order final pass.  So a
+// solve, and a replay from a checkpoint, reproduce their iterates bit for bit.
+// The CG iteration (apply + 2 dots + 3 vector updates = 7 launches) is
+// captured in a CUDA graph of `check_every` iterations; the host reads the
+// residual norms only between graph launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "apply_kernels.cuh"
+#include "handle.h"
+
+namespace sip {
+
+cudaError_t launch_aux_2d(const AuxArgs&, int, size_t, cudaStream_t);
+cudaError_t launch_aux_3d(const AuxArgs&, int, size_t, cudaStream_t);
+
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kScal = 8;  // per-RHS scalars
+enum { S_RR = 0, S_PAP = 1, S_ALPHA = 2, S_BETA = 3, S_ACTIVE = 4, S_RR0 = 5, S_AUX = 6 };
+enum { ST_BREAKDOWN = 1, ST_NONFINITE = 2 };
+
+int red_blocks(int64_t n) {
+  int64_t b = (n + kRedThreads * 4 - 1) / (kRedThreads * 4);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(1024, b));
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int h = kRedThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  return red[0];
+}
+
+// partial[rhs][block] = sum over this block's fixed strided subset of a*b
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(kRedThreads) k_dot_partial(const TA* a, const TB* b, int64_t n, double* partial) {
+  __shared__ double red[kRedThreads];
+  const int rhs = blockIdx.y;
+  a += rhs * n;
+  b += rhs * n;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads)
+    s += (double)a[i] * (double)b[i];
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0) partial[rhs * gridDim.x + blockIdx.x] = t;
+}
+
+// out = sum of nblk partials (fixed order), stored into scal[rhs*kScal + slot],
+// then the CG scalar step selected by `what`:
+//   0: plain store; 1: alpha = rr / pAp (breakdown check); 2: beta = rr_new / rr, rr = rr_new
+__global__ void __launch_bounds__(kRedThreads) k_final(const double* partial, int nblk, double* scal, int slot,
+                                                       int what, int* status) {
+  __shared__ double red[kRedThreads];
+  const int rhs = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += kRedThreads) s += partial[rhs * nblk + i];
+  const double t = block_sum(s, red);
+  if (threadIdx.x != 0) return;
+  double* sc = scal + rhs * kScal;
+  const bool active = sc[S_ACTIVE] != 0.0;
+  if (what == 0) {
+    sc[slot] = t;
+  } else if (what == 1) {
+    sc[S_PAP] = t;
+    double alpha = 0.0;
+    if (active) {
+      if (!(t > 0.0)) {
+        if (!isfinite(t)) atomicOr(status, ST_NONFINITE);
+        else atomicOr(status, ST_BREAKDOWN);
+        sc[S_ACTIVE] = 0.0;
+      } else {
+        alpha = sc[S_RR] / t;
+      }
+    }
+    sc[S_ALPHA] = alpha;
+  } else {
+    double beta = 0.0;
+    if (active) {
+      if (!isfinite(t)) atomicOr(status, ST_NONFINITE);
+      beta = t / sc[S_RR];
+      sc[S_RR] = t;
+    }
+    sc[S_BETA] = beta;
+  }
+}
+
+// x += alpha p, r -= alpha Ap, partial sums of r.r
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_update_xr(T* x, T* r, const T* p, const T* ap, int64_t n,
+                                                           const double* scal, double* partial) {
+  __shared__ double red[kRedThreads];
+  const int rhs = blockIdx.y;
+  const T alpha = (T)scal[rhs * kScal + S_ALPHA];
+  x += rhs * n; r += rhs * n; p += rhs * n; ap += rhs * n;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const T ri = fma(-alpha, ap[i], r[i]);
+    r[i] = ri;
+    s += (double)ri * (double)ri;
+  }
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0) partial[rhs * gridDim.x + blockIdx.x] = t;
+}
+
+// p = r + beta p
+template <typename T>
+__global__ void k_update_p(const T* r, T* p, int64_t n, const double* scal) {
+  const int rhs = blockIdx.y;
+  const T beta = (T)scal[rhs * kScal + S_BETA];
+  r += rhs * n; p += rhs * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], r[i]);
+}
+
+// r = b - r (in place, r holds A x); FP64
+__global__ void k_residual(const double* b, double* r, int64_t total) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = b[i] - r[i];
+}
+
+// r32 = float(s[rhs] * r64), x32 = 0, p32 = r32
+__global__ void k_to_f32(const double* r64, float* r32, float* x32, float* p32, int64_t n, const double* s) {
+  const int rhs = blockIdx.y;
+  const double sc = s[rhs];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = (float)(sc * r64[rhs * n + i]);
+    r32[rhs * n + i] = v;
+    p32[rhs * n + i] = v;
+    x32[rhs * n + i] = 0.0f;
+  }
+}
+
+// x64 += s[rhs] * d32
+__global__ void k_add_f32(double* x64, const float* d32, int64_t n, const double* s) {
+  const int rhs = blockIdx.y;
+  const double sc = s[rhs];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x64[rhs * n + i] += sc * (double)d32[rhs * n + i];
+}
+
+// kappa double -> float copy
+__global__ void k_d2f(const double* a, float* b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+__global__ void k_nonfinite(const double* a, int64_t n, int* flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(a[i])) *flag = 1;
+}
+
+dim3 vgrid(int64_t n, int nrhs) {
+  int64_t b = (n + 255) / 256;
+  return dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(2048, b)), (unsigned)nrhs);
+}
+
+}  // namespace
+
+void CgWork::release() {
+  if (graph) cudaGraphExecDestroy(graph);
+  graph = nullptr;
+  cudaFree(x); cudaFree(r); cudaFree(p); cudaFree(ap);
+  cudaFree(scal); cudaFree(partial); cudaFree(status);
+  x = r = p = ap = nullptr;
+  scal = partial = nullptr;
+  status = nullptr;
+  nrhs = 0;
+}
+
+}  // namespace sip
+
+void sip_handle::release() {
+  cg64.release();
+  cg32.release();
+  cudaFree(r64); cudaFree(x64); cudaFree(red);
+  if (scal_host) cudaFreeHost(scal_host);
+  for (auto* p : ck_x) cudaFree(p);
+  for (auto* p : ck_r) cudaFree(p);
+  for (auto* p : ck_p) cudaFree(p);
+  ck_x.clear(); ck_r.clear(); ck_p.clear();
+  if (solve_stream) cudaStreamDestroy(solve_stream);
+  cudaFree(dof_off); cudaFree(quad_off); cudaFree(vgoff); cudaFree(f_troff); cudaFree(f_goff);
+  cudaFree(slots); cudaFree(elist); cudaFree(tiles); cudaFree(xq);
+  cudaFree(gd.vgeo); cudaFree(gd.fgeo); cudaFree(gd.tau); cudaFree(gd.kappa);
+  cudaFree(gf.vgeo); cudaFree(gf.fgeo); cudaFree(gf.tau); cudaFree(gf.kappa);
+  cudaFree(trace_d);
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+}
+
+namespace sip {
+namespace {
+
+int ensure_cg(sip_handle* h, CgWork& W, size_t es, int nrhs) {
+  if (W.nrhs == nrhs && W.elem == es) return SIP_OK;
+  W.release();
+  const size_t n = (size_t)h->plan.ndof * nrhs;
+  const int nblk = red_blocks(h->plan.ndof);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&W.x, n * es);
+  if (e == cudaSuccess) e = cudaMalloc(&W.r, n * es);
+  if (e == cudaSuccess) e = cudaMalloc(&W.p, n * es);
+  if (e == cudaSuccess) e = cudaMalloc(&W.ap, n * es);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&W.scal, sizeof(double) * kScal * nrhs);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&W.partial, sizeof(double) * nblk * nrhs);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&W.status, sizeof(int));
+  if (e != cudaSuccess) { W.release(); return cuda_fail(e, "CG workspace"); }
+  W.nrhs = nrhs;
+  W.elem = es;
+  return SIP_OK;
+}
+
+int ensure_solver(sip_handle* h, int nrhs) {
+  if (!h->solve_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->solve_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "solver stream");
+  }
+  if (!h->scal_host) {
+    cudaError_t e = cudaMallocHost((void**)&h->scal_host, sizeof(double) * kScal * 1024);
+    if (e != cudaSuccess) return cuda_fail(e, "pinned scalars");
+  }
+  if (nrhs > 1000) return fail(SIP_ERR_ARG, "nrhs > 1000");
+  if (h->work_nrhs < nrhs) {
+    cudaFree(h->r64); cudaFree(h->x64);
+    h->r64 = h->x64 = nullptr;
+    const size_t n = (size_t)h->plan.ndof * nrhs;
+    cudaError_t e = cudaMalloc((void**)&h->r64, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->x64, n * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(e, "solver vectors");
+    h->work_nrhs = nrhs;
+  }
+  if (!h->red) {
+    const size_t nb = std::max<size_t>(h->plan.tiles.size(), 1024) * 1024 / 1024 + 2048;
+    cudaError_t e = cudaMalloc((void**)&h->red, nb * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(e, "reduction buffer");
+  }
+  return handle_grow_trace(h, nrhs);
+}
+
+// dot products a_r . b_r for every RHS into scal[rhs*kScal + slot]
+template <typename TA, typename TB>
+void enqueue_dot(sip_handle* h, CgWork& W, const TA* a, const TB* b, int nrhs, int slot, int what, cudaStream_t s) {
+  const int nblk = red_blocks(h->plan.ndof);
+  k_dot_partial<TA, TB><<<dim3(nblk, nrhs), kRedThreads, 0, s>>>(a, b, h->plan.ndof, W.partial);
+  k_final<<<nrhs, kRedThreads, 0, s>>>(W.partial, nblk, W.scal, slot, what, W.status);
+}
+
+// one CG iteration on workspace W (vector type T, apply precision prec)
+template <typename T>
+int enqueue_iter(sip_handle* h, CgWork& W, int nrhs, int prec, int transpose, cudaStream_t s) {
+  const int64_t n = h->plan.ndof;
+  int rc = apply_any(h, prec, W.p, W.ap, nrhs, s, transpose, nullptr);
+  if (rc) return rc;
+  enqueue_dot<T, T>(h, W, (const T*)W.p, (const T*)W.ap, nrhs, S_PAP, 1, s);
+  const int nblk = red_blocks(n);
+  k_update_xr<T><<<dim3(nblk, nrhs), kRedThreads, 0, s>>>((T*)W.x, (T*)W.r, (const T*)W.p, (const T*)W.ap, n,
+                                                          W.scal, W.partial);
+  k_final<<<nrhs, kRedThreads, 0, s>>>(W.partial, nblk, W.scal, S_RR, 2, W.status);
+  k_update_p<T><<<vgrid(n, nrhs), 256, 0, s>>>((const T*)W.r, (T*)W.p, n, W.scal);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SIP_OK : cuda_fail(e, "CG iteration");
+}
+
+// run `iters` iterations: as a captured graph (cached per workspace) or directly
+template <typename T>
+int run_iters(sip_handle* h, CgWork& W, int nrhs, int prec, int transpose, int iters, cudaStream_t s, bool use_graph) {
+  if (!use_graph) {
+    for (int i = 0; i < iters; ++i) {
+      int rc = enqueue_iter<T>(h, W, nrhs, prec, transpose, s);
+      if (rc) return rc;
+    }
+    return SIP_OK;
+  }
+  if (!W.graph || W.graph_iters != iters || W.graph_transpose != transpose) {
+    if (W.graph) cudaGraphExecDestroy(W.graph);
+    W.graph = nullptr;
+    const bool timing = h->timing;
+    h->timing = false;
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { h->timing = timing; return cuda_fail(e, "begin capture"); }
+    int rc = SIP_OK;
+    for (int i = 0; i < iters && rc == SIP_OK; ++i) rc = enqueue_iter<T>(h, W, nrhs, prec, transpose, s);
+    e = cudaStreamEndCapture(s, &g);
+    h->timing = timing;
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&W.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    W.graph_iters = iters;
+    W.graph_transpose = transpose;
+  }
+  cudaError_t e = cudaGraphLaunch(W.graph, s);
+  return e == cudaSuccess ? SIP_OK : cuda_fail(e, "graph launch");
+}
+
+int read_scal(sip_handle* h, CgWork& W, int nrhs, cudaStream_t s, int* status) {
+  cudaMemcpyAsync(h->scal_host, W.scal, sizeof(double) * kScal * nrhs, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(h->scal_host + kScal * 1023, W.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "CG scalars");
+  std::memcpy(status, h->scal_host + kScal * 1023, sizeof(int));
+  return SIP_OK;
+}
+
+int write_scal(sip_handle* h, CgWork& W, int nrhs, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(W.scal, h->scal_host, sizeof(double) * kScal * nrhs, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? SIP_OK : cuda_fail(e, "CG scalars upload");
+}
+
+// Inner CG loop from the state already in W (r, p, x, scal with RR and ACTIVE set).
+// Runs until every active RHS has sqrt(rr) <= tol[rhs], or `budget` iterations.
+template <typename T>
+int cg_loop(sip_handle* h, CgWork& W, int nrhs, int prec, int transpose, const std::vector<double>& tol,
+            int budget, int* iters_done, cudaStream_t s, bool checkpoint) {
+  const int chunk = std::max(1, checkpoint ? h->plan.opt.checkpoint_every : h->plan.opt.check_every);
+  int done = 0;
+  while (true) {
+    int status = 0;
+    int rc = read_scal(h, W, nrhs, s, &status);
+    if (rc) return rc;
+    if (status & ST_NONFINITE) return fail(SIP_ERR_NONFINITE, "non-finite CG scalar");
+    if (status & ST_BREAKDOWN) return fail(SIP_ERR_BREAKDOWN, "CG breakdown: p^T A p <= 0");
+    bool any = false, changed = false;
+    for (int r = 0; r < nrhs; ++r) {
+      double* sc = h->scal_host + r * kScal;
+      if (sc[S_ACTIVE] == 0.0) continue;
+      if (!std::isfinite(sc[S_RR])) return fail(SIP_ERR_NONFINITE, "non-finite residual");
+      if (std::sqrt(sc[S_RR]) <= tol[r]) { sc[S_ACTIVE] = 0.0; changed = true; }
+      else any = true;
+    }
+    if (changed) { rc = write_scal(h, W, nrhs, s); if (rc) return rc; }
+    if (!any || done >= budget) break;
+    const int it = std::min(chunk, budget - done);
+    rc = run_iters<T>(h, W, nrhs, prec, transpose, it, s, it == chunk);
+    if (rc) return rc;
+    done += it;
+    if (checkpoint && it == chunk && !h->ck_x.empty()) {
+      const int slot = h->ck_next;
+      const size_t bytes = sizeof(double) * h->plan.ndof;
+      cudaMemcpyAsync(h->ck_x[slot], W.x, bytes, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(h->ck_r[slot], W.r, bytes, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(h->ck_p[slot], W.p, bytes, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(&h->scal_host[kScal * 1022], W.scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      h->ck_rr[slot] = h->scal_host[kScal * 1022];
+      h->ck_iter[slot] = *iters_done + done;
+      h->ck_next = (slot + 1) % (int)h->ck_x.size();
+      h->ck_count = std::min(h->ck_count + 1, (int)h->ck_x.size());
+    }
+  }
+  *iters_done += done;
+  return SIP_OK;
+}
+
+// ||v_r||^2 for every RHS (FP64), to host
+int norms2(sip_handle* h, CgWork& W, const double* v, int nrhs, cudaStream_t s, std::vector<double>& out) {
+  enqueue_dot<double, double>(h, W, v, v, nrhs, S_AUX, 0, s);
+  int st = 0;
+  int rc = read_scal(h, W, nrhs, s, &st);
+  if (rc) return rc;
+  out.resize(nrhs);
+  for (int r = 0; r < nrhs; ++r) out[r] = h->scal_host[r * kScal + S_AUX];
+  return SIP_OK;
+}
+
+int solve_impl(sip_handle* h, int mode, const double* b, double* x_out, int nrhs, double rtol,
+               sip_stats* stats, cudaStream_t user, int transpose) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!h || !b || !x_out) return fail(SIP_ERR_ARG, "null argument");
+  if (nrhs < 1) return fail(SIP_ERR_ARG, "nrhs must be >= 1");
+  if (!(rtol > 0.0)) return fail(SIP_ERR_ARG, "rtol must be > 0");
+  if (mode != SIP_CG_FP64 && mode != SIP_CG_FP32_REFINED) return fail(SIP_ERR_ARG, "mode");
+  int rc = ensure_solver(h, nrhs);
+  if (rc) return rc;
+  const int64_t n = h->plan.ndof;
+  const size_t bytes = sizeof(double) * n * nrhs;
+  cudaStream_t s = h->solve_stream;
+  // order after the caller's pending work
+  cudaEvent_t evu;
+  cudaEventCreateWithFlags(&evu, cudaEventDisableTiming);
+  cudaEventRecord(evu, user);
+  cudaStreamWaitEvent(s, evu, 0);
+  sip_stats st;
+  std::memset(&st, 0, sizeof(st));
+  rc = ensure_cg(h, h->cg64, sizeof(double), nrhs);
+  if (rc) { cudaEventDestroy(evu); return rc; }
+  CgWork& W = h->cg64;
+  // input check and ||b||
+  {
+    int zero = 0;
+    cudaMemcpyAsync(W.status, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
+    k_nonfinite<<<vgrid(n * nrhs, 1), 256, 0, s>>>(b, n * nrhs, W.status);
+    int flag = 0;
+    cudaMemcpyAsync(&flag, W.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    if (flag) { cudaEventDestroy(evu); return fail(SIP_ERR_NONFINITE, "non-finite right-hand side"); }
+  }
+  std::vector<double> bn2;
+  rc = norms2(h, W, b, nrhs, s, bn2);
+  if (rc) { cudaEventDestroy(evu); return rc; }
+  std::vector<double> tol(nrhs);
+  for (int r = 0; r < nrhs; ++r) tol[r] = rtol * std::sqrt(bn2[r]);
+  const int max_iter = h->plan.opt.max_iter;
+  bool converged = false;
+  double worst = 0.0;
+  h->ck_count = 0;
+  h->ck_next = 0;
+  const bool ckpt = h->plan.opt.checkpoint_every > 0 && nrhs == 1 && mode == SIP_CG_FP64;
+  if (ckpt && (int)h->ck_x.size() != std::max(1, h->plan.opt.checkpoint_slots)) {
+    for (auto* p : h->ck_x) cudaFree(p);
+    for (auto* p : h->ck_r) cudaFree(p);
+    for (auto* p : h->ck_p) cudaFree(p);
+    const int ns = std::max(1, h->plan.opt.checkpoint_slots);
+    h->ck_x.assign(ns, nullptr); h->ck_r.assign(ns, nullptr); h->ck_p.assign(ns, nullptr);
+    h->ck_rr.assign(ns, 0.0); h->ck_iter.assign(ns, 0);
+    for (int i = 0; i < ns; ++i) {
+      cudaError_t e = cudaMalloc((void**)&h->ck_x[i], sizeof(double) * n);
+      if (e == cudaSuccess) e = cudaMalloc((void**)&h->ck_r[i], sizeof(double) * n);
+      if (e == cudaSuccess) e = cudaMalloc((void**)&h->ck_p[i], sizeof(double) * n);
+      if (e != cudaSuccess) { cudaEventDestroy(evu); return cuda_fail(e, "checkpoint ring"); }
+    }
+  }
+  if (mode == SIP_CG_FP64) {
+    // x = 0, r = b, p = b, rr = ||b||^2
+    cudaMemsetAsync(W.x, 0, bytes, s);
+    cudaMemcpyAsync(W.r, b, bytes, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(W.p, b, bytes, cudaMemcpyDeviceToDevice, s);
+    for (int r = 0; r < nrhs; ++r) {
+      double* sc = h->scal_host + r * kScal;
+      std::fill(sc, sc + kScal, 0.0);
+      sc[S_RR] = bn2[r];
+      sc[S_RR0] = bn2[r];
+      sc[S_ACTIVE] = bn2[r] > 0.0 ? 1.0 : 0.0;
+    }
+    int zero = 0;
+    cudaMemcpyAsync(W.status, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
+    rc = write_scal(h, W, nrhs, s);
+    int restarts = 0;
+    while (rc == SIP_OK) {
+      rc = cg_loop<double>(h, W, nrhs, SIP_FP64, transpose, tol, max_iter - st.iterations, &st.iterations, s, ckpt);
+      if (rc) break;
+      // true residual r64 = b - A x
+      rc = apply_any(h, SIP_FP64, W.x, h->r64, nrhs, s, transpose, nullptr);
+      if (rc) break;
+      st.applies_fp64 += 1;
+      k_residual<<<vgrid(n * nrhs, 1), 256, 0, s>>>(b, h->r64, n * nrhs);
+      std::vector<double> rn2;
+      rc = norms2(h, W, h->r64, nrhs, s, rn2);
+      if (rc) break;
+      bool all = true;
+      worst = 0.0;
+      for (int r = 0; r < nrhs; ++r) {
+        const double rel = bn2[r] > 0 ? std::sqrt(rn2[r] / bn2[r]) : 0.0;
+        worst = std::max(worst, rel);
+        double* sc = h->scal_host + r * kScal;
+        if (std::sqrt(rn2[r]) > tol[r]) {
+          all = false;
+          sc[S_RR] = rn2[r];
+          sc[S_ACTIVE] = 1.0;
+        } else {
+          sc[S_ACTIVE] = 0.0;
+        }
+      }
+      if (all) { converged = true; break; }
+      if (st.iterations >= max_iter || restarts > 50) break;
+      // residual replacement for the columns that have not converged: r = r_true, p = r
+      ++restarts;
+      cudaMemcpyAsync(W.r, h->r64, bytes, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(W.p, h->r64, bytes, cudaMemcpyDeviceToDevice, s);
+      rc = write_scal(h, W, nrhs, s);
+    }
+    st.applies_fp64 += st.iterations;
+    if (rc == SIP_OK) cudaMemcpyAsync(x_out, W.x, bytes, cudaMemcpyDeviceToDevice, s);
+  } else {
+    rc = ensure_cg(h, h->cg32, sizeof(float), nrhs);
+    CgWork& V = h->cg32;
+    if (rc == SIP_OK) cudaMemsetAsync(h->x64, 0, bytes, s);
+    const double itol = h->plan.opt.inner_rtol;
+    double* sdev = W.partial;  // scale factors per RHS live in W.partial (free here)
+    int total_inner = 0;
+    for (int outer = 0; rc == SIP_OK; ++outer) {
+      // r64 = b - A x64 (x64 = 0 at the first step)
+      if (outer == 0) {
+        cudaMemcpyAsync(h->r64, b, bytes, cudaMemcpyDeviceToDevice, s);
+      } else {
+        rc = apply_any(h, SIP_FP64, h->x64, h->r64, nrhs, s, transpose, nullptr);
+        if (rc) break;
+        st.applies_fp64 += 1;
+        k_residual<<<vgrid(n * nrhs, 1), 256, 0, s>>>(b, h->r64, n * nrhs);
+      }
+      std::vector<double> rn2;
+      rc = norms2(h, W, h->r64, nrhs, s, rn2);
+      if (rc) break;
+      bool all = true;
+      worst = 0.0;
+      std::vector<double> scale(nrhs, 0.0), inv(nrhs, 0.0);
+      for (int r = 0; r < nrhs; ++r) {
+        worst = std::max(worst, bn2[r] > 0 ? std::sqrt(rn2[r] / bn2[r]) : 0.0);
+        if (std::sqrt(rn2[r]) > tol[r]) {
+          all = false;
+          inv[r] = 1.0 / std::sqrt(rn2[r]);
+          scale[r] = std::sqrt(rn2[r]);
+        }
+      }
+      if (all) { converged = true; break; }
+      if (outer >= h->plan.opt.max_refine || total_inner >= max_iter) break;
+      st.refinements += 1;
+      // inner system A d = r / ||r|| in FP32
+      cudaMemcpyAsync(sdev, inv.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s);
+      k_to_f32<<<vgrid(n, nrhs), 256, 0, s>>>(h->r64, (float*)V.r, (float*)V.x, (float*)V.p, n, sdev);
+      std::vector<double> rr32;
+      enqueue_dot<float, float>(h, V, (const float*)V.r, (const float*)V.r, nrhs, S_AUX, 0, s);
+      int stt = 0;
+      rc = read_scal(h, V, nrhs, s, &stt);
+      if (rc) break;
+      std::vector<double> itl(nrhs);
+      for (int r = 0; r < nrhs; ++r) {
+        double* sc = h->scal_host + r * kScal;
+        const double rr = sc[S_AUX];
+        std::fill(sc, sc + kScal, 0.0);
+        sc[S_RR] = rr;
+        sc[S_RR0] = rr;
+        sc[S_ACTIVE] = scale[r] > 0.0 ? 1.0 : 0.0;
+        itl[r] = itol * std::sqrt(rr);
+      }
+      int zero = 0;
+      cudaMemcpyAsync(V.status, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
+      rc = write_scal(h, V, nrhs, s);
+      if (rc) break;
+      int inner = 0;
+      rc = cg_loop<float>(h, V, nrhs, SIP_FP32, transpose, itl, max_iter - total_inner, &inner, s, false);
+      if (rc) break;
+      total_inner += inner;
+      st.applies_fp32 += inner;
+      cudaMemcpyAsync(sdev, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s);
+      k_add_f32<<<vgrid(n, nrhs), 256, 0, s>>>(h->x64, (const float*)V.x, n, sdev);
+    }
+    st.iterations = total_inner;
+    if (rc == SIP_OK) cudaMemcpyAsync(x_out, h->x64, bytes, cudaMemcpyDeviceToDevice, s);
+  }
+  cudaEventRecord(evu, s);
+  cudaStreamWaitEvent(user, evu, 0);
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(evu);
+  st.rel_residual = worst;
+  st.converged = converged ? 1 : 0;
+  st.checkpoints = ckpt ? h->ck_count : 0;
+  st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = st;
+  if (rc) return rc;
+  if (!converged) return fail(SIP_ERR_NOT_CONVERGED, "CG did not reach the tolerance within max_iter");
+  return SIP_OK;
+}
+
+size_t aux_smem(sip_handle* h) {
+  size_t m = 0;
+  for (const Tile& t : h->plan.tiles) {
+    const int epb = apply_epb(h->plan.dim, t.n, SIP_FP64);
+    m = std::max(m, (size_t)epb * aux_smem_per_element(h->plan.dim, t.n) * sizeof(double));
+  }
+  return m + kRedThreads * sizeof(double);
+}
+
+int launch_aux(sip_handle* h, AuxArgs& a, cudaStream_t s) {
+  a.dof_off = h->dof_off;
+  a.quad_off = h->quad_off;
+  a.vgoff = h->vgoff;
+  a.vgeo = h->gd.vgeo;
+  a.elist = h->elist;
+  a.tiles = h->tiles;
+  const int nt = (int)h->plan.tiles.size();
+  cudaError_t e = h->plan.dim == 2 ? launch_aux_2d(a, nt, aux_smem(h), s) : launch_aux_3d(a, nt, aux_smem(h), s);
+  return e == cudaSuccess ? SIP_OK : cuda_fail(e, "aux kernel");
+}
+
+}  // namespace
+}  // namespace sip
+
+using namespace sip;
+
+extern "C" {
+
+int sip_cg_solve(sip_handle* h, int mode, const double* b, double* x, int nrhs, double rtol, sip_stats* stats,
+                 void* stream) {
+  return solve_impl(h, mode, b, x, nrhs, rtol, stats, (cudaStream_t)stream, 0);
+}
+
+int sip_cg_solve_transpose(sip_handle* h, int mode, const double* b, double* x, int nrhs, double rtol,
+                           sip_stats* stats, void* stream) {
+  return solve_impl(h, mode, b, x, nrhs, rtol, stats, (cudaStream_t)stream, 1);
+}
+
+int sip_cg_checkpoint_count(const sip_handle* h) { return h ? h->ck_count : -1; }
+
+int sip_cg_checkpoint_get(sip_handle* h, int slot, double* x, double* r, double* p, double* rr_host, int* iter_host,
+                          void* stream) {
+  if (!h || !x || !r || !p || !rr_host || !iter_host) return fail(SIP_ERR_ARG, "null argument");
+  if (slot < 0 || slot >= h->ck_count) return fail(SIP_ERR_ARG, "checkpoint slot out of range");
+  const int ns = (int)h->ck_x.size();
+  const int idx = (h->ck_next - h->ck_count + slot + 2 * ns) % ns;
+  const size_t bytes = sizeof(double) * h->plan.ndof;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaMemcpyAsync(x, h->ck_x[idx], bytes, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(r, h->ck_r[idx], bytes, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(p, h->ck_p[idx], bytes, cudaMemcpyDeviceToDevice, s);
+  *rr_host = h->ck_rr[idx];
+  *iter_host = h->ck_iter[idx];
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SIP_OK : cuda_fail(e, "checkpoint copy");
+}
+
+int sip_cg_replay(sip_handle* h, double* x, double* r, double* p, double* rr_host, int iters, void* stream) {
+  if (!h || !x || !r || !p || !rr_host || iters < 0) return fail(SIP_ERR_ARG, "bad argument");
+  int rc = ensure_solver(h, 1);
+  if (rc) return rc;
+  rc = ensure_cg(h, h->cg64, sizeof(double), 1);
+  if (rc) return rc;
+  CgWork& W = h->cg64;
+  cudaStream_t s = h->solve_stream;
+  cudaStream_t user = (cudaStream_t)stream;
+  cudaEvent_t ev;
+  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  cudaEventRecord(ev, user);
+  cudaStreamWaitEvent(s, ev, 0);
+  const size_t bytes = sizeof(double) * h->plan.ndof;
+  cudaMemcpyAsync(W.x, x, bytes, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(W.r, r, bytes, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(W.p, p, bytes, cudaMemcpyDeviceToDevice, s);
+  double* sc = h->scal_host;
+  std::fill(sc, sc + kScal, 0.0);
+  sc[S_RR] = *rr_host;
+  sc[S_ACTIVE] = 1.0;
+  int zero = 0;
+  cudaMemcpyAsync(W.status, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
+  rc = write_scal(h, W, 1, s);
+  if (rc == SIP_OK) rc = run_iters<double>(h, W, 1, SIP_FP64, 0, iters, s, false);
+  if (rc == SIP_OK) {
+    cudaMemcpyAsync(x, W.x, bytes, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(r, W.r, bytes, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(p, W.p, bytes, cudaMemcpyDeviceToDevice, s);
+    int st = 0;
+    rc = read_scal(h, W, 1, s, &st);
+    if (rc == SIP_OK) *rr_host = h->scal_host[S_RR];
+  }
+  cudaEventRecord(ev, s);
+  cudaStreamWaitEvent(user, ev, 0);
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(ev);
+  return rc;
+}
+
+int sip_set_kappa(sip_handle* h, const double* kappa, void* stream) {
+  if (!h) return fail(SIP_ERR_ARG, "null handle");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (auto* W : {&h->cg64, &h->cg32})
+    if (W->graph) { cudaGraphExecDestroy(W->graph); W->graph = nullptr; }
+  if (!kappa) { h->kappa_set = false; return SIP_OK; }
+  const int64_t n = h->plan.nquad;
+  cudaMemcpyAsync(h->gd.kappa, kappa, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  k_d2f<<<vgrid(n, 1), 256, 0, s>>>(h->gd.kappa, h->gf.kappa, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "set kappa");
+  h->kappa_set = true;
+  return SIP_OK;
+}
+
+int sip_grad_kappa(sip_handle* h, const double* ybar, const double* x, double* kbar, int accumulate, void* stream) {
+  if (!h || !ybar || !x || !kbar) return fail(SIP_ERR_ARG, "null argument");
+  AuxArgs a{};
+  a.a = ybar;
+  a.b = x;
+  a.out = kbar;
+  a.accumulate = accumulate;
+  a.mode = 0;
+  return launch_aux(h, a, (cudaStream_t)stream);
+}
+
+int sip_mass_dot(sip_handle* h, const double* av, const double* bv, double* out, void* stream) {
+  if (!h || !av || !bv || !out) return fail(SIP_ERR_ARG, "null argument");
+  int rc = ensure_solver(h, 1);
+  if (rc) return rc;
+  AuxArgs a{};
+  a.a = av;
+  a.b = bv;
+  a.out = h->red;
+  a.mode = 1;
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = launch_aux(h, a, s);
+  if (rc) return rc;
+  // fixed-order final sum of the per-tile partials, straight into *out
+  const int nt = (int)h->plan.tiles.size();
+  static_assert(S_RR == 0, "slot 0");
+  // reuse k_final in "store" mode with a 1-RHS scalar block at h->red + nt
+  k_final<<<1, kRedThreads, 0, s>>>(h->red, nt, h->red + nt, 0, 0, nullptr);
+  cudaMemcpyAsync(out, h->red + nt, sizeof(double), cudaMemcpyDeviceToDevice, s);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SIP_OK : cuda_fail(e, "mass dot");
+}
+
+int sip_iproduct(sip_handle* h, const double* f, double* b, void* stream) {
+  if (!h || !f || !b) return fail(SIP_ERR_ARG, "null argument");
+  AuxArgs a{};
+  a.a = f;
+  a.out = b;
+  a.mode = 2;
+  return launch_aux(h, a, (cudaStream_t)stream);
+}
+
+int sip_quad_points(sip_handle* h, double* xq, void* stream) {
+  if (!h || !xq) return fail(SIP_ERR_ARG, "null argument");
+  cudaError_t e = cudaMemcpyAsync(xq, h->xq, sizeof(double) * h->plan.nquad * h->plan.dim, cudaMemcpyDeviceToDevice,
+                                  (cudaStream_t)stream);
+  return e == cudaSuccess ? SIP_OK : cuda_fail(e, "quad points");
+}
+
+int sip_work_model(const sip_handle* h, int precision, sip_work* out) {
+  if (!h || !out) return fail(SIP_ERR_ARG, "null argument");
+  const Plan& p = h->plan;
+  const int d = p.dim;
+  const double es = precision == SIP_FP32 ? 4.0 : 8.0;
+  double ft = 0.0, fm = 0.0;
+  for (int64_t e = 0; e < p.E; ++e) {
+    const double N = p.P[e] + 1, Q = N + 1;
+    const double QV = d == 2 ? Q * Q : Q * Q * Q;
+    const double QF1 = d == 2 ? Q : Q * Q;
+    // one sum-factorised interpolation GLL -> Gauss (FMA = 2 flops)
+    const double interp = 2.0 * (d == 2 ? (N * N * Q + N * Q * Q) : (N * N * N * Q + N * N * Q * Q + N * Q * Q * Q));
+    const double grad = 2.0 * d * QV * Q;
+    ft += interp;
+    fm += grad + (2.0 * d * d + d + 2.0) * QV + grad + interp;  // gradient, pointwise, D^T, B^T
+    for (int k = 0; k < 2 * d; ++k) {
+      const FaceSlot& sl = p.slots[(size_t)e * 2 * d + k];
+      const double qf = sl.qf;
+      const double np = d == 2 ? qf : qf * qf;
+      double interp_f = 0.0;
+      if (sl.qf != (int)Q) interp_f = 2.0 * (d + 1) * (d == 2 ? qf * Q : (Q * qf * Q + qf * qf * Q));
+      ft += 2.0 * 2.0 * QF1 * Q + 2.0 * (d - 1) * QF1 * Q + interp_f + 2.0 * d * np;
+      fm += 12.0 * np + d * np + interp_f + 2.0 * (1 + d) * QV;
+    }
+  }
+  out->flops_trace = ft;
+  out->flops_main = fm;
+  out->bytes_x = es * p.ndof;
+  out->bytes_y = es * p.ndof;
+  out->bytes_geometry = es * (p.vgeo.size() + p.fgeo.size() + p.f_tau.size());
+  out->bytes_trace = 2.0 * es * 4.0 * p.trace_points;
+  return SIP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,167 @@
+"""Parity of the CUDA apply (y = A x, and A^T x) with the FP64 oracle.
+
+Small meshes are compared element by element on every output; the full-size
+workloads (the 64x64 jittered p-non-conforming quads, the 32^3, 24^3 and
+16^3 hexes) on the rows of a sample of elements, which the oracle computes
+one block row at a time.  Tolerances: 1e-12 relative (2-norm) in FP64,
+1e-5 relative in FP32.
+"""
+import numpy as np
+import pytest
+
+import sip_inputs as si
+from oracle import SipOracle
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2504_03573_gb300 import build
+    build.build()
+    import paper_2504_03573_gb300 as g
+    return g
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gpu_apply(op, x, precision="f64", transpose=False):
+    import torch
+    dt = torch.float64 if precision == "f64" else torch.float32
+    xt = torch.tensor(x, dtype=dt, device="cuda")
+    y = op.apply(xt, transpose=transpose)
+    torch.cuda.synchronize()
+    return y.double().cpu().numpy()
+
+
+def small_meshes():
+    out = {
+        "c1": si.workload("c1_2d_4x4_p3"),
+        "2d_rot_jitter_p1to8": si.rotate_elements(si.structured_mesh(2, 9, jitter=0.2, seed=21, order_range=(1, 8)), 22),
+        "2d_single_p5": si.structured_mesh(2, 1, order=5),
+        "3d_rot_jitter_p1to5": si.rotate_elements(si.structured_mesh(3, 3, jitter=0.15, seed=23, order_range=(1, 5)), 24),
+        "3d_rot_p6to8": si.rotate_elements(si.structured_mesh(3, 2, jitter=0.1, seed=25, order_range=(6, 8)), 26),
+        "3d_single_p3": si.structured_mesh(3, 1, order=3),
+        "2d_affine_skew": si.affine_map_vertices(si.rotate_elements(si.structured_mesh(2, 5, seed=27, order_range=(2, 5)), 28),
+                                                 np.array([[1.1, 0.4], [-0.3, 0.8]])),
+        "3d_affine_skew": si.affine_map_vertices(si.structured_mesh(3, 3, seed=29, order_range=(2, 4)),
+                                                 np.array([[1.0, 0.3, 0.1], [0.0, 0.9, -0.2], [0.2, 0.0, 1.2]])),
+    }
+    return out
+
+
+MESHES = small_meshes()
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+def test_apply_fp64_full_parity(pkg, name):
+    m = MESHES[name]
+    orc = SipOracle(m, lam=m.lam)
+    A = orc.assemble()
+    op = pkg.SipOperator.from_mesh(m)
+    x = si.random_vector(orc.ndof, 0)
+    y = gpu_apply(op, x)
+    yr = A @ x
+    assert rel(y, yr) <= TOL64, rel(y, yr)
+    # element-wise, scaled by the row magnitude
+    scale = np.abs(A) @ np.abs(x)
+    assert np.max(np.abs(y - yr) / scale) <= 1e-13
+    yt = gpu_apply(op, x, transpose=True)
+    assert rel(yt, A.T @ x) <= TOL64
+    y32 = gpu_apply(op, x, "f32")
+    assert rel(y32, yr) <= TOL32, rel(y32, yr)
+
+
+@pytest.mark.parametrize("name", ["2d_rot_jitter_p1to8", "3d_rot_jitter_p1to5"])
+def test_neumann_variant_and_lambda_zero(pkg, name):
+    m = MESHES[name]
+    opts = pkg.options(boundary=0)
+    op = pkg.SipOperator(m.dim, m.vert, m.elem_vert, m.orders, 0.0, opts)
+    orc = SipOracle(m, lam=0.0, boundary=False)
+    A = orc.assemble()
+    x = si.random_vector(orc.ndof, 3)
+    assert rel(gpu_apply(op, x), A @ x) <= TOL64
+    # the constant is in the kernel of the pure-Neumann stiffness
+    one = np.ones(orc.ndof)
+    y1 = gpu_apply(op, one)
+    assert np.max(np.abs(y1)) <= 1e-11 * np.max(np.abs(A).sum(axis=1))
+
+
+def test_multi_rhs(pkg):
+    import torch
+    m = MESHES["3d_rot_jitter_p1to5"]
+    orc = SipOracle(m)
+    A = orc.assemble()
+    op = pkg.SipOperator.from_mesh(m)
+    X = si.random_rhs_batch(5, orc.ndof, 9)
+    Y = op.apply(torch.tensor(X, device="cuda")).cpu().numpy()
+    for r in range(5):
+        assert rel(Y[r], A @ X[r]) <= TOL64
+    Y32 = op.apply(torch.tensor(X, device="cuda", dtype=torch.float32)).double().cpu().numpy()
+    for r in range(5):
+        assert rel(Y32[r], A @ X[r]) <= TOL32
+
+
+def _sample_elements(m, k, seed):
+    rng = np.random.default_rng(seed)
+    E = m.n_elem
+    s = set(rng.choice(E, size=min(k, E), replace=False).tolist())
+    s.update({0, E - 1})
+    # one element of every order present
+    for p in np.unique(m.orders):
+        s.add(int(np.flatnonzero(m.orders == p)[0]))
+    return sorted(s)
+
+
+@pytest.mark.parametrize("name,k", [("c2_2d_64x64_jitter_p2to6", 48), ("c3_3d_32cube_p4", 12),
+                                    ("c4_3d_24cube_jitter_p2to7", 12), ("c5_3d_16cube_p5", 12)])
+def test_full_size_sampled_rows(pkg, name, k):
+    import torch
+    m = si.workload(name)
+    op = pkg.SipOperator.from_mesh(m)
+    orc = SipOracle(m)
+    sample = _sample_elements(m, k, 5)
+    R = orc.rows_for_elements(sample)
+    dofs = orc.dofs_of(sample)
+    nrhs = 32 if name.startswith("c4") else 1
+    X = si.random_rhs_batch(nrhs, orc.ndof, 4) if nrhs > 1 else si.random_vector(orc.ndof, 0)[None]
+    Xt = torch.tensor(X, device="cuda")
+    Y = op.apply(Xt if nrhs > 1 else Xt[0]).reshape(nrhs, -1).cpu().numpy()
+    X32 = Xt.float()
+    Y32 = op.apply(X32 if nrhs > 1 else X32[0]).reshape(nrhs, -1).double().cpu().numpy()
+    for r in ([0, nrhs // 2, nrhs - 1] if nrhs > 1 else [0]):
+        yr = R @ X[r]
+        assert rel(Y[r][dofs], yr) <= TOL64, (r, rel(Y[r][dofs], yr))
+        assert rel(Y32[r][dofs], yr) <= TOL32, (r, rel(Y32[r][dofs], yr))
+
+
+def test_symmetry_c2_via_gpu(pkg):
+    import torch
+    m = si.workload("c2_2d_64x64_jitter_p2to6")
+    op = pkg.SipOperator.from_mesh(m)
+    n = op.ndof
+    x1 = torch.tensor(si.random_vector(n, 0), device="cuda")
+    x2 = torch.tensor(si.random_vector(n, 1), device="cuda")
+    a = float(x1 @ op.apply(x2))
+    b = float(x2 @ op.apply(x1))
+    den = float(torch.linalg.norm(x1) * torch.linalg.norm(op.apply(x2)))
+    assert abs(a - b) / den <= 1e-13
+    # A^T x via the transpose apply equals A x to rounding
+    y = op.apply(x1)
+    yt = op.apply_transpose(x1)
+    assert float(torch.linalg.norm(y - yt) / torch.linalg.norm(y)) <= 1e-13
+
+
+def test_bad_inputs_raise(pkg):
+    import torch
+    m = MESHES["c1"]
+    op = pkg.SipOperator.from_mesh(m)
+    with pytest.raises(pkg.SipError):
+        op.apply(torch.zeros(op.ndof + 1, dtype=torch.float64, device="cuda"))
+    with pytest.raises(pkg.SipError):
+        op.apply(torch.zeros(op.ndof, dtype=torch.float64))

@@ -1,0 +1,140 @@
+"""CPU-side checks of the C ABI library: it loads, exports every function that
+include/sip.h declares, and its host-side mesh analysis (face pairing,
+orientation, geometry, penalties, argument and mesh errors) is right.  No GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import sip_inputs as si
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+HEADER = os.path.join(HERE, "..", "include", "sip.h")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2504_03573_gb300 import build
+    build.build()
+    import paper_2504_03573_gb300 as g
+    return g
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**(sip_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(pkg):
+    names = declared_functions()
+    assert len(names) >= 25, names
+    so = C.CDLL(pkg._lib.LIB_PATH)
+    for n in names:
+        assert hasattr(so, n), n
+    # and the binding wraps exactly the declared set
+    assert set(names) == set(pkg._lib.SIGNATURES), set(names) ^ set(pkg._lib.SIGNATURES)
+
+
+def test_defaults(pkg):
+    o = pkg.options()
+    assert o.tau_scale == 2.0 and o.qvol_extra == 2 and o.boundary == 1
+    assert o.inner_rtol == 1e-5 and o.check_every == 16
+
+
+def _info(pkg, m, **kw):
+    return pkg.plan_info(m.dim, m.vert, m.elem_vert, m.orders, pkg.options(**kw) if kw else None)
+
+
+def test_plan_counts_c1(pkg):
+    m = si.workload("c1_2d_4x4_p3")
+    i = _info(pkg, m)
+    assert i["ndof"] == 256 and i["nquad"] == 16 * 25
+    assert i["n_faces_interior"] == 24 and i["n_faces_boundary"] == 16
+    assert i["n_elem_affine"] == 16 and i["n_faces_nonconforming"] == 0
+    assert abs(i["min_h_face"] - 0.25) < 1e-14
+    assert abs(i["max_tau"] - 2 * 16 / 0.25) < 1e-10
+
+
+def test_plan_counts_c2(pkg):
+    m = si.workload("c2_2d_64x64_jitter_p2to6")
+    i = _info(pkg, m)
+    assert i["n_faces_interior"] == 8064 and i["n_faces_boundary"] == 256
+    assert i["ndof"] == si.ndof(m.orders, 2)
+    # non-conforming faces counted independently
+    n = 64
+    o = m.orders.reshape(n, n)
+    nc = int(np.sum(o[:, 1:] != o[:, :-1]) + np.sum(o[1:, :] != o[:-1, :]))
+    assert i["n_faces_nonconforming"] == nc
+    assert i["n_elem_affine"] == 0
+    # trace points: sum over faces of (max(P-,P+)+2)
+    q = o + 2
+    tp = int(np.sum(np.maximum(q[:, 1:], q[:, :-1])) + np.sum(np.maximum(q[1:, :], q[:-1, :])))
+    tp += int(np.sum(q[:, 0]) + np.sum(q[:, -1]) + np.sum(q[0, :]) + np.sum(q[-1, :]))
+    assert i["trace_points"] == tp
+
+
+@pytest.mark.parametrize("dim,n", [(2, 5), (3, 3)])
+def test_orientations_cover_rotations(pkg, dim, n):
+    m = si.rotate_elements(si.structured_mesh(dim, n, jitter=0.1, seed=2, order_range=(1, 4)), 7)
+    i = _info(pkg, m)
+    hist = i["orient_hist"]
+    assert sum(hist) == i["n_faces_interior"]
+    used = sum(1 for h in hist if h > 0)
+    assert used == (2 if dim == 2 else 8)
+    plain = _info(pkg, si.structured_mesh(dim, n, jitter=0.1, seed=2, order_range=(1, 4)))
+    assert plain["orient_hist"][0] == plain["n_faces_interior"]
+
+
+def test_face_counts_match_oracle(pkg):
+    from oracle import SipOracle
+    m = si.rotate_elements(si.structured_mesh(3, 3, jitter=0.1, seed=4, order_range=(1, 3)), 1)
+    orc = SipOracle(m)
+    i = _info(pkg, m)
+    assert i["n_faces_interior"] == len(orc.interior)
+    assert i["n_faces_boundary"] == len(orc.bfaces)
+
+
+def test_errors(pkg):
+    m = si.workload("c1_2d_4x4_p3")
+    bad = m.orders.copy()
+    bad[3] = 0
+    with pytest.raises(pkg.SipError) as e:
+        pkg.plan_info(2, m.vert, m.elem_vert, bad)
+    assert e.value.code == 1
+    bad[3] = 9
+    with pytest.raises(pkg.SipError) as e:
+        pkg.plan_info(2, m.vert, m.elem_vert, bad)
+    assert e.value.code == 1
+    with pytest.raises(pkg.SipError) as e:
+        pkg.plan_info(2, m.vert, m.elem_vert, m.orders, pkg.options(qvol_extra=3))
+    assert e.value.code == 1
+    # inverted element: swap two corners -> non-positive Jacobian
+    ev = m.elem_vert.copy()
+    ev[5, [0, 1]] = ev[5, [1, 0]]
+    with pytest.raises(pkg.SipError) as e:
+        pkg.plan_info(2, m.vert, ev, m.orders)
+    assert e.value.code == 2
+    # three elements on one face: duplicate an element
+    ev = np.vstack([m.elem_vert, m.elem_vert[6:7]])
+    with pytest.raises(pkg.SipError) as e:
+        pkg.plan_info(2, m.vert, ev, np.append(m.orders, 3))
+    assert e.value.code == 2
+    # vertex id out of range
+    ev = m.elem_vert.copy()
+    ev[0, 0] = 10 ** 6
+    with pytest.raises(pkg.SipError) as e:
+        pkg.plan_info(2, m.vert, ev, m.orders)
+    assert e.value.code == 1
+
+
+def test_create_without_gpu_fails_loudly(pkg):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    m = si.workload("c1_2d_4x4_p3")
+    with pytest.raises(pkg.SipError):
+        pkg.SipOperator.from_mesh(m)
