@@ -173,9 +173,9 @@ def run_gb300(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    from paper_2504_03573_gb300 import build
     if rank == 0:
-        build.build()
+        import __graft_entry__
+        __graft_entry__.build()
     if world > 1:
         torch.distributed.barrier()
     import paper_2504_03573_gb300 as g

@@ -16,3 +16,15 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def repo_root():
     return ROOT
+
+
+def build_library():
+    """Build libsip.so (if stale) and import the package."""
+    import importlib.util
+    path = os.path.join(ROOT, "paper_2504_03573_gb300", "build.py")
+    spec = importlib.util.spec_from_file_location("_sip_build", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build()
+    import paper_2504_03573_gb300
+    return paper_2504_03573_gb300

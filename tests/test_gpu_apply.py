@@ -20,10 +20,8 @@ TOL32 = 1e-5
 
 @pytest.fixture(scope="module")
 def pkg():
-    from paper_2504_03573_gb300 import build
-    build.build()
-    import paper_2504_03573_gb300 as g
-    return g
+    from conftest import build_library
+    return build_library()
 
 
 def rel(a, b):

@@ -16,10 +16,8 @@ HEADER = os.path.join(HERE, "..", "include", "sip.h")
 
 @pytest.fixture(scope="module")
 def pkg():
-    from paper_2504_03573_gb300 import build
-    build.build()
-    import paper_2504_03573_gb300 as g
-    return g
+    from conftest import build_library
+    return build_library()
 
 
 def declared_functions():
