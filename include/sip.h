@@ -215,6 +215,31 @@ int  sip_work_model(const sip_handle* h, int precision, sip_work* out);
 int  sip_set_timing(sip_handle* h, int enable);
 int  sip_last_kernel_ms(sip_handle* h, float* trace_ms, float* main_ms);
 
+/* y = A x like sip_apply, but allocating nothing: the trace scratch is a
+ * file-scope device array of 16 MiB (SIP_STATIC_TRACE_BYTES) that every GPU
+ * loading the library holds until the process exits.  For callers that must
+ * not allocate device memory once running (e.g. a process whose device memory
+ * is fully reserved by its own caching allocator, or a latency-critical loop
+ * where cudaMalloc and its implicit synchronisation are not allowed); the
+ * handle itself is still created (and allocated) by sip_create beforehand.
+ * The paper has no counterpart; this is an interface variant, not part of the
+ * method.
+ * - Needs nrhs * 4 * trace_points * sizeof(element) <= SIP_STATIC_TRACE_BYTES
+ *   (trace_points from sip_get_plan_info); larger requests return
+ *   SIP_ERR_ARG without launching anything.
+ * - The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ * - All calls on all handles of a device share the one array and it keeps the
+ *   last call's contents (nothing in it needs clearing: every entry read is
+ *   written earlier in the same call).  Calls whose kernels overlap on the GPU
+ *   (different streams, or different host threads) race on it: serialise them.
+ * Arguments, layout and other errors as sip_apply; the handle must belong to the
+ * current device. */
+#define SIP_STATIC_TRACE_BYTES (16u << 20)
+int  sip_apply_static_scratch(sip_handle* h, int precision, const void* x_dev, void* y_dev, int nrhs,
+                              void* stream);
+
 const char* sip_last_error(void);
 
 #ifdef __cplusplus

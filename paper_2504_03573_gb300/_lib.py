@@ -23,6 +23,7 @@ SIP_FP32 = 1
 SIP_CG_FP64 = 0
 SIP_CG_FP32_REFINED = 1
 SIP_MAX_ORDER = 8
+SIP_STATIC_TRACE_BYTES = 16 << 20
 
 ERROR_NAMES = {1: "SIP_ERR_ARG", 2: "SIP_ERR_MESH", 3: "SIP_ERR_CUDA", 4: "SIP_ERR_OOM",
                5: "SIP_ERR_NONFINITE", 6: "SIP_ERR_NOT_CONVERGED", 7: "SIP_ERR_BREAKDOWN",
@@ -113,6 +114,7 @@ SIGNATURES = {
     "sip_work_model": (_I, [_H, _I, C.POINTER(sip_work)]),
     "sip_set_timing": (_I, [_H, _I]),
     "sip_last_kernel_ms": (_I, [_H, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "sip_apply_static_scratch": (_I, [_H, _I, _P, _P, _I, _P]),
     "sip_last_error": (C.c_char_p, []),
 }
 
