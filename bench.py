@@ -243,7 +243,7 @@ def run_gb300(args):
     pk = peaks()
     ach = w64["flops_main"] / (main_ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_main<double,2>",
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": f"k_main<double,{mesh.dim}>",
             "peak_src": "FP64 vendor figure 1.25 TFLOP/s (dense)",
             "kernel_ms": main_ms, "trace_kernel_ms": trace_ms,
             "hbm_frac": (w64["bytes_x"] + w64["bytes_y"] + w64["bytes_geometry"] + w64["bytes_trace"])

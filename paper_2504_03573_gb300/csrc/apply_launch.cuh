@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "apply_kernels.cuh"
+#include "aux_kernels.cuh"
 
 #define SIP_DEFINE_APPLY_TU(SUFFIX, TYPE, DIM)                                                     \
   namespace sip {                                                                                 \

@@ -31,8 +31,7 @@ extern "C" int sip_apply_static_scratch(sip_handle* h, int precision, const void
   if (!h || !x || !y) return sip::fail(SIP_ERR_ARG, "null handle or vector");
   if (nrhs < 1) return sip::fail(SIP_ERR_ARG, "nrhs must be >= 1");
   if (precision != SIP_FP64 && precision != SIP_FP32) return sip::fail(SIP_ERR_ARG, "precision");
-  const size_t es = precision == SIP_FP64 ? sizeof(double) : sizeof(float);
-  const size_t need = (size_t)nrhs * 4 * (size_t)h->plan.trace_points * es;
+  const size_t need = sip::apply_scratch_bytes(h, precision, nrhs, nullptr);
   if (need > kStaticTraceBytes)
     return sip::fail(SIP_ERR_ARG, "sip_apply_static_scratch: this mesh and nrhs need " + std::to_string(need) +
                                       " bytes of trace scratch, above the static limit of " +
@@ -55,7 +54,7 @@ extern "C" int sip_apply_static_scratch(sip_handle* h, int precision, const void
     }
     scratch = g_trace_scratch_addr[dev];
   }
-  // k_trace writes every trace entry that k_main then reads, so the scratch needs
-  // no clearing between calls.
+  // k_trace writes every scratch entry that k_main then reads, so the scratch
+  // needs no clearing between calls.
   return sip::apply_any(h, precision, x, y, nrhs, (cudaStream_t)stream, 0, scratch);
 }

@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "apply_kernels.cuh"
+#include "common.cuh"
 #include "handle.h"
 
 namespace sip {
@@ -26,11 +26,19 @@ int cuda_fail(cudaError_t e, const char* where) {
   return e == cudaErrorMemoryAllocation ? SIP_ERR_OOM : SIP_ERR_CUDA;
 }
 
-int apply_epb(int dim, int n, int /*precision*/) {
-  const int per = smem_per_element(dim, n, true) * (int)sizeof(double);
-  const int cap = dim == 2 ? 32 : 8;
-  int epb = (48 * 1024) / per;
-  return std::max(1, std::min(cap, epb));
+// Elements per tile: enough work items per CTA to keep 256 threads busy in every
+// stage (Gauss points in 2D, lines of Gauss points in 3D), within 64 KB of
+// shared memory.
+int apply_epb(int dim, int n, int precision) {
+  const int q = n + 1;
+  // one Gauss point per work item (2D; FP64 in 3D) or one line of Q points (FP32 in 3D)
+  const bool lines = dim == 3 && precision == SIP_FP32;
+  const int items = lines ? q * q : (dim == 2 ? q * q : q * q * q);
+  int epb = std::max(1, (dim == 3 && !lines ? 384 : 256) / items);
+  const int es = precision == SIP_FP32 ? 4 : 8;
+  const int per = std::max(per_elem_trace(dim, n), per_elem_main(dim, n)) * es;
+  const int room = (64 * 1024 - table_block_bytes(es, n) - kMetaBytes) / per;
+  return std::max(1, std::min(std::min(epb, room), kMaxEpb));
 }
 
 cudaError_t upload_tables_2d_f64(const double*, const float*, const int*);
@@ -93,18 +101,72 @@ int ensure_tables(int dev) {
 
 int handle_grow_trace(sip_handle* h, int nrhs) {
   const size_t need = (size_t)nrhs * 4 * (size_t)h->plan.trace_points;
-  if (need <= h->trace_cap) return SIP_OK;
-  if (h->trace_d) cudaFree(h->trace_d);
-  h->trace_d = nullptr;
-  h->trace_cap = 0;
-  cudaError_t e = cudaMalloc((void**)&h->trace_d, need * sizeof(double));
-  if (e != cudaSuccess) return cuda_fail(e, "trace buffer");
-  h->trace_cap = need;
+  if (need > h->trace_cap) {
+    if (h->trace_d) cudaFree(h->trace_d);
+    h->trace_d = nullptr;
+    h->trace_cap = 0;
+    cudaError_t e = cudaMalloc((void**)&h->trace_d, need * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(e, "trace buffer");
+    h->trace_cap = need;
+  }
+  const size_t needu = (size_t)nrhs * (size_t)h->plan.nquad;
+  if (needu > h->ug_cap) {
+    if (h->ug_d) cudaFree(h->ug_d);
+    h->ug_d = nullptr;
+    h->ug_cap = 0;
+    cudaError_t e = cudaMalloc((void**)&h->ug_d, needu * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(e, "Gauss-point buffer");
+    h->ug_cap = needu;
+  }
+  return SIP_OK;
+}
+
+// Scratch of one apply: trace buffer [nrhs][4 trace_points], then (FP64 only)
+// the Gauss-point buffer [nrhs][nquad], 256-byte aligned.
+size_t apply_scratch_bytes(const sip_handle* h, int precision, int nrhs, size_t* ug_offset) {
+  const size_t es = precision == SIP_FP64 ? sizeof(double) : sizeof(float);
+  const size_t tr = ((size_t)nrhs * 4 * (size_t)h->plan.trace_points * es + 255) / 256 * 256;
+  if (ug_offset) *ug_offset = tr;
+  return precision == SIP_FP64 ? tr + (size_t)nrhs * (size_t)h->plan.nquad * es : tr;
+}
+
+// (Re)build the tiles of one precision (epb_by_n[n] > 0 overrides the default
+// elements per tile for order n - 1), upload them and size the shared memory.
+int set_tiles(sip_handle* h, int precision, const int* epb_by_n) {
+  const int pi = precision == SIP_FP32 ? 1 : 0;
+  std::vector<Tile> tiles;
+  build_tiles(h->plan, precision, epb_by_n, tiles);
+  const int es = precision == SIP_FP32 ? 4 : 8;
+  size_t st = 0, sm = 0;
+  for (const Tile& t : tiles) {
+    const size_t fixed = (size_t)table_block_bytes(es, t.n) + kMetaBytes;
+    st = std::max(st, fixed + (size_t)t.count * per_elem_trace(h->plan.dim, t.n) * es);
+    sm = std::max(sm, fixed + (size_t)t.count * per_elem_main(h->plan.dim, t.n) * es);
+  }
+  if (st > 200 * 1024 || sm > 200 * 1024) return fail(SIP_ERR_ARG, "tile too large for shared memory");
+  Tile* d = nullptr;
+  cudaError_t e = cudaMalloc((void**)&d, std::max<size_t>(16, tiles.size() * sizeof(Tile)));
+  if (e == cudaSuccess && !tiles.empty())
+    e = cudaMemcpy(d, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return cuda_fail(e, "tiles");
+  }
+  if (h->tiles_d[pi]) {
+    cudaDeviceSynchronize();  // earlier launches may still read the old tiles
+    cudaFree(h->tiles_d[pi]);
+  }
+  h->tiles_d[pi] = d;
+  h->tiles_h[pi] = std::move(tiles);
+  h->smem_trace[pi] = st;
+  h->smem_main[pi] = sm;
+  for (auto* W : {&h->cg64, &h->cg32})
+    if (W->graph) { cudaGraphExecDestroy(W->graph); W->graph = nullptr; }
   return SIP_OK;
 }
 
 template <typename T>
-ApplyArgs<T> make_args(sip_handle* h, const T* x, T* y, T* trace, int transpose) {
+ApplyArgs<T> make_args(sip_handle* h, const T* x, T* y, T* trace, T* ug, int transpose) {
   ApplyArgs<T> a;
   const DevGeom<T>& g = h->geom<T>();
   a.dof_off = h->dof_off;
@@ -118,11 +180,13 @@ ApplyArgs<T> make_args(sip_handle* h, const T* x, T* y, T* trace, int transpose)
   a.f_tau = g.tau;
   a.fgeo = g.fgeo;
   a.elist = h->elist;
-  a.tiles = h->tiles;
+  a.tiles = h->tiles_d[std::is_same<T, float>::value ? 1 : 0];
   a.x = x;
   a.y = y;
   a.trace = trace;
+  a.ug = ug;
   a.ndof = h->plan.ndof;
+  a.nquad = h->plan.nquad;
   a.trace_stride = 4 * h->plan.trace_points;
   a.lambda = (T)h->lambda;
   a.transpose = transpose;
@@ -130,26 +194,30 @@ ApplyArgs<T> make_args(sip_handle* h, const T* x, T* y, T* trace, int transpose)
 }
 
 int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cudaStream_t s,
-              int transpose, void* trace_override) {
+              int transpose, void* scratch_override) {
   if (!h || !x || !y) return fail(SIP_ERR_ARG, "null handle or vector");
   if (nrhs < 1) return fail(SIP_ERR_ARG, "nrhs must be >= 1");
   if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
-  if (!trace_override) {
+  if (!scratch_override) {
     int rc = handle_grow_trace(h, nrhs);
     if (rc) return rc;
   }
-  const int nt = (int)h->plan.tiles.size();
+  size_t ug_off = 0;
+  apply_scratch_bytes(h, precision, nrhs, &ug_off);
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   if (h->timing) { e0 = h->ev[0]; e1 = h->ev[1]; e2 = h->ev[2]; }
   cudaError_t e;
   if (precision == SIP_FP64) {
-    double* tr = trace_override ? (double*)trace_override : h->trace_d;
-    auto a = make_args<double>(h, (const double*)x, (double*)y, tr, transpose);
+    double* tr = scratch_override ? (double*)scratch_override : h->trace_d;
+    double* ug = scratch_override ? (double*)((char*)scratch_override + ug_off) : h->ug_d;
+    auto a = make_args<double>(h, (const double*)x, (double*)y, tr, ug, transpose);
+    const int nt = (int)h->tiles_h[0].size();
     e = h->plan.dim == 2 ? launch_apply_2d_f64(a, nt, nrhs, h->smem_trace[0], h->smem_main[0], s, e0, e1, e2)
                          : launch_apply_3d_f64(a, nt, nrhs, h->smem_trace[0], h->smem_main[0], s, e0, e1, e2);
   } else {
-    float* tr = trace_override ? (float*)trace_override : (float*)h->trace_d;
-    auto a = make_args<float>(h, (const float*)x, (float*)y, tr, transpose);
+    float* tr = scratch_override ? (float*)scratch_override : (float*)h->trace_d;
+    auto a = make_args<float>(h, (const float*)x, (float*)y, tr, nullptr, transpose);
+    const int nt = (int)h->tiles_h[1].size();
     e = h->plan.dim == 2 ? launch_apply_2d_f32(a, nt, nrhs, h->smem_trace[1], h->smem_main[1], s, e0, e1, e2)
                          : launch_apply_3d_f32(a, nt, nrhs, h->smem_trace[1], h->smem_main[1], s, e0, e1, e2);
   }
@@ -268,7 +336,6 @@ int sip_create(const sip_mesh* mesh, const int32_t* orders, double lambda, const
   UP(h->f_goff, p.f_goff);
   UP(h->slots, p.slots);
   UP(h->elist, p.elist);
-  UP(h->tiles, p.tiles);
   UP(h->gd.vgeo, p.vgeo);
   UP(h->gd.fgeo, p.fgeo);
   UP(h->gd.tau, p.f_tau);
@@ -286,17 +353,9 @@ int sip_create(const sip_mesh* mesh, const int32_t* orders, double lambda, const
     sip_destroy(h);
     return rc;
   }
-  // shared memory per launch: max over the tiles' orders
-  for (int prec = 0; prec < 2; ++prec) {
-    size_t st = 0, sm = 0;
-    const size_t es = prec == 0 ? sizeof(double) : sizeof(float);
-    for (const Tile& t : p.tiles) {
-      const int epb = apply_epb(p.dim, t.n, prec);
-      st = std::max(st, (size_t)epb * smem_per_element(p.dim, t.n, false) * es);
-      sm = std::max(sm, (size_t)epb * smem_per_element(p.dim, t.n, true) * es);
-    }
-    h->smem_trace[prec] = st;
-    h->smem_main[prec] = sm;
+  for (int prec : {SIP_FP64, SIP_FP32}) {
+    rc = set_tiles(h, prec, nullptr);
+    if (rc) { sip_destroy(h); return rc; }
   }
   rc = handle_grow_trace(h, 1);
   if (rc) { sip_destroy(h); return rc; }

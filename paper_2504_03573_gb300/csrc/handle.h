@@ -31,9 +31,11 @@ struct CgWork {
   double* scal = nullptr;   // per RHS: rr, pap, alpha, beta, rr_new, active, scratch...
   double* partial = nullptr;
   int* status = nullptr;    // device status word (breakdown / non-finite)
+  void* xext = nullptr;     // FP64 iterate updated instead of x (mixed-precision CG)
   cudaGraphExec_t graph = nullptr;
   int graph_iters = 0;
   int graph_transpose = -1;
+  void* graph_xext = nullptr;
   void release();
 };
 
@@ -52,15 +54,19 @@ struct sip_handle {
   int64_t* f_goff = nullptr;
   sip::FaceSlot* slots = nullptr;
   int32_t* elist = nullptr;
-  sip::Tile* tiles = nullptr;
+  sip::Tile* tiles_d[2] = {nullptr, nullptr};   // per precision (FP64, FP32)
+  std::vector<sip::Tile> tiles_h[2];
   double* xq = nullptr;
   sip::DevGeom<double> gd;
   sip::DevGeom<float> gf;
   template <typename T>
   const sip::DevGeom<T>& geom() const;
-  // scratch: trace buffer (sized for the largest nrhs seen, in doubles)
+  // scratch (sized for the largest nrhs seen, in doubles): trace buffer and, for
+  // FP64 applies, the Gauss-point values handed from the trace to the main kernel
   double* trace_d = nullptr;
   size_t trace_cap = 0;
+  double* ug_d = nullptr;
+  size_t ug_cap = 0;
   size_t smem_trace[2] = {0, 0};
   size_t smem_main[2] = {0, 0};
   // timing
@@ -72,6 +78,7 @@ struct sip_handle {
   sip::CgWork cg64, cg32;
   double* r64 = nullptr;     // outer residual / true residual workspace [nrhs][ndof]
   double* x64 = nullptr;     // outer iterate
+  double* xbak = nullptr;    // outer iterate at the last refinement (mixed-precision CG)
   double* red = nullptr;     // reduction partials for aux kernels
   double* scal_host = nullptr;
   int work_nrhs = 0;
@@ -91,7 +98,11 @@ inline const sip::DevGeom<float>& sip_handle::geom<float>() const { return gf; }
 namespace sip {
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* where);
+// scratch_override: caller-provided scratch holding the trace buffer followed by
+// (FP64) the Gauss-point buffer, laid out as apply_scratch_bytes() describes.
 int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cudaStream_t s,
-              int transpose, void* trace_override);
+              int transpose, void* scratch_override);
+size_t apply_scratch_bytes(const sip_handle* h, int precision, int nrhs, size_t* ug_offset);
+int set_tiles(sip_handle* h, int precision, const int* epb_by_n);
 int handle_grow_trace(sip_handle* h, int nrhs);
 }  // namespace sip

@@ -311,7 +311,7 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
       p.slots[(size_t)pr.em * nf + pr.km] = FaceSlot{(int32_t)f, 0, 0, (int8_t)qf, 0};
       p.slots[(size_t)pr.ep * nf + pr.kp] = FaceSlot{(int32_t)f, 1, (int8_t)found, (int8_t)qf, 0};
     } else {
-      p.slots[(size_t)pr.em * nf + pr.km] = FaceSlot{(int32_t)f, 0, 0, (int8_t)qf, 1};
+      p.slots[(size_t)pr.em * nf + pr.km] = FaceSlot{(int32_t)f, 0, 0, (int8_t)qf, (int8_t)kFaceBnd};
     }
   }
   p.trace_points = p.f_troff[F];
@@ -385,6 +385,25 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
         }
       }
     }
+    // orthogonal face: c has no tangential component on either side
+    {
+      bool orth = true;
+      for (int z = 0; z < npts && orth; ++z) {
+        const double cn = std::fabs(fg[(1 + am) * npts + z]);
+        for (int m = 0; m < dim; ++m)
+          if (m != am && std::fabs(fg[(1 + m) * npts + z]) > 1e-13 * cn) orth = false;
+        if (ep >= 0) {
+          const int ap = kp / 2;
+          const double cp = std::fabs(fg[(1 + dim + ap) * npts + z]);
+          for (int m = 0; m < dim; ++m)
+            if (m != ap && std::fabs(fg[(1 + dim + m) * npts + z]) > 1e-13 * cp) orth = false;
+        }
+      }
+      if (orth) {
+        p.slots[(size_t)em * 2 * dim + km].flags |= kFaceOrth;
+        if (ep >= 0) p.slots[(size_t)ep * 2 * dim + kp].flags |= kFaceOrth;
+      }
+    }
     const double vmin = ep >= 0 ? std::min(p.vol[em], p.vol[ep]) : p.vol[em];
     const double hf = vmin / area;
     const int pmax = ep >= 0 ? std::max(p.P[em], p.P[ep]) : p.P[em];
@@ -393,22 +412,42 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
       for (int z = 0; z < npts; ++z) fg[z] = 0.0;
   }
 
-  // ---- order buckets and tiles
+  // ---- elements sorted by order (the paper's element groups)
   p.elist.resize(E);
   std::iota(p.elist.begin(), p.elist.end(), 0);
   std::stable_sort(p.elist.begin(), p.elist.end(),
                    [&](int32_t a, int32_t b) { return p.P[a] < p.P[b]; });
-  p.tiles.clear();
+  return SIP_OK;
+}
+
+// Tiles of at most epb(n) elements of one order, cut from the order-sorted list.
+void build_tiles(const Plan& p, int precision, const int* epb_override, std::vector<Tile>& tiles) {
+  tiles.clear();
+  const int64_t E = p.E;
   for (int64_t i = 0; i < E;) {
     const int n = p.P[p.elist[i]] + 1;
     int64_t j = i;
     while (j < E && p.P[p.elist[j]] + 1 == n) ++j;
-    const int epb = apply_epb(dim, n, SIP_FP64);
-    for (int64_t s = i; s < j; s += epb)
-      p.tiles.push_back(Tile{n, (int32_t)s, (int32_t)std::min<int64_t>(epb, j - s), 0});
+    int epb = epb_override && epb_override[n] > 0 ? epb_override[n] : apply_epb(p.dim, n, precision);
+    epb = std::max(1, std::min(epb, kMaxEpb));
+    // spread the bucket evenly over ceil(count / epb) tiles
+    const int64_t cnt = j - i;
+    const int64_t ntile = (cnt + epb - 1) / epb;
+    for (int64_t k = 0; k < ntile; ++k) {
+      const int64_t s0 = i + (cnt * k) / ntile, s1 = i + (cnt * (k + 1)) / ntile;
+      int qfm = n + 1;
+      bool orth = true;
+      for (int64_t s = s0; s < s1; ++s)
+        for (int f = 0; f < 2 * p.dim; ++f) {
+          const FaceSlot& sl = p.slots[(size_t)p.elist[s] * 2 * p.dim + f];
+          qfm = std::max(qfm, (int)sl.qf);
+          orth = orth && (sl.flags & kFaceOrth);
+        }
+      const int flags = qfm | (qfm > n + 1 ? kTileFine : 0) | (orth ? kTileOrth : 0);
+      tiles.push_back(Tile{n, (int32_t)s0, (int32_t)(s1 - s0), flags});
+    }
     i = j;
   }
-  return SIP_OK;
 }
 
 }  // namespace sip

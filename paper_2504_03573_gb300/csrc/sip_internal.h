@@ -54,22 +54,76 @@ constexpr int tab_I(int Q, int F) {
 constexpr int kTabSize = tab_I(kQMax + 1, kQMax + 2);
 
 // ---------------------------------------------------------------------------
+// Shared-memory layout of the apply kernels (host computes launch sizes, device
+// indexes with the same constexpr functions).
+//
+// Per-CTA table block for one order (N, Q = N + 1), laid out so that a warp whose
+// lanes compute consecutive outputs reads consecutive addresses:
+//   BT [N][Q]  B[q][i] at i*Q + q      forward interpolation GLL -> Gauss
+//   BB [Q][N]  B[q][i] at q*N + i      transposed interpolation
+//   DT [Q][Q]  D[q][r] at r*Q + q      collocation derivative
+//   DD [Q][Q]  D[q][r] at q*Q + r      transposed derivative
+//   LL [4][Q]  l(-1), l(+1), l'(-1), l'(+1)
+//   for F = Q+1 .. kQMax:  IT_F [Q][F] (I[z][r] at r*F + z), II_F [F][Q] (I[z][r] at z*Q + r)
+// ---------------------------------------------------------------------------
+struct TabLayout {
+  static constexpr int BT(int) { return 0; }
+  static constexpr int BB(int n) { return n * (n + 1); }
+  static constexpr int DT(int n) { return 2 * n * (n + 1); }
+  static constexpr int DD(int n) { return DT(n) + (n + 1) * (n + 1); }
+  static constexpr int LL(int n) { return DD(n) + (n + 1) * (n + 1); }
+  static constexpr int IT(int n, int f) {
+    int o = LL(n) + 4 * (n + 1);
+    for (int g = n + 2; g < f; ++g) o += 2 * g * (n + 1);
+    return o;
+  }
+  static constexpr int II(int n, int f) { return IT(n, f) + f * (n + 1); }
+  static constexpr int size(int n) { return IT(n, kQMax + 1); }
+};
+
+constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * cpow(b, e - 1); }
+
+// faces processed together in one pass: all four in 2D, one at a time in 3D
+constexpr int faces_per_batch(int dim) { return dim == 2 ? 4 : 1; }
+
+// per-element shared memory (in elements of T) of the trace and main kernels
+constexpr int face_buf(int dim, int n, int fields) {
+  return faces_per_batch(dim) * fields *
+         (cpow(n + 1, dim - 1) + (dim == 3 ? kQMax * (n + 1) : 0) + cpow(kQMax, dim - 1));
+}
+constexpr int per_elem_trace(int dim, int n) { return 2 * cpow(n + 1, dim) + face_buf(dim, n, 4); }
+constexpr int per_elem_main(int dim, int n) { return (1 + dim) * cpow(n + 1, dim) + face_buf(dim, n, 1 + dim); }
+// bytes of the CTA's table block (padded to 16) that precedes the element buffers
+constexpr int table_block_bytes(int bytes_per, int n) { return ((TabLayout::size(n) * bytes_per + 15) / 16) * 16; }
+
+// ---------------------------------------------------------------------------
 // Per element local face slot (2*dim per element; local face k = 2*axis + side).
 // ---------------------------------------------------------------------------
+constexpr int kFaceBnd = 1;   // boundary face
+constexpr int kFaceOrth = 2;  // c = J^-1 n has no tangential component on either side
+
 struct FaceSlot {
   int32_t face;    // face id
   int8_t side;     // 0: minus side (or boundary), 1: plus side
   int8_t orient;   // plus side: bit0 flip t0, bit1 flip t1, bit2 transpose; else 0
   int8_t qf;       // points per direction of the shared face rule
-  int8_t bnd;      // 1: boundary face
+  int8_t flags;    // kFaceBnd | kFaceOrth
 };
+
+constexpr int kTileQfMask = 0xff;  // bits 0-7: largest face rule of the tile
+constexpr int kTileFine = 1 << 8;  // some face of the tile has a finer rule than Q
+constexpr int kTileOrth = 1 << 9;  // every face of the tile is orthogonal (kFaceOrth)
+constexpr int kMaxEpb = 32;        // elements per tile, at most
 
 struct Tile {
   int32_t n;       // nodes per direction (P + 1) of every element of the tile
   int32_t start;   // first index into the order-sorted element list
   int32_t count;   // elements in the tile
-  int32_t pad;
+  int32_t flags;   // kTileQfMask | kTileFine | kTileOrth
 };
+
+// per-tile copy of element ids and face slots, after the table block
+constexpr int kMetaBytes = ((kMaxEpb * (4 + 6 * (int)sizeof(FaceSlot)) + 15) / 16) * 16;
 
 // Host plan: everything the device needs, in FP64.
 struct Plan {
@@ -97,9 +151,8 @@ struct Plan {
   std::vector<double> fgeo;
   int64_t trace_points = 0;
   std::vector<FaceSlot> slots;   // [E][2 dim]
-  // order buckets
+  // elements sorted by order (stable); tiles are cut from this list per precision
   std::vector<int32_t> elist;
-  std::vector<Tile> tiles;
   int64_t orient_hist[8] = {0};
 };
 
@@ -113,7 +166,8 @@ double lagrange(const std::vector<double>& nodes, int j, double x);
 double lagrange_deriv(const std::vector<double>& nodes, int j, double x);
 void fill_tables(std::vector<double>& tab);
 
-// elements per tile for the apply kernels (host choice, also used by launchers)
+// elements per tile for the apply kernels (host choice), and the tiles for it
 int apply_epb(int dim, int n, int precision);
+void build_tiles(const Plan& p, int precision, const int* epb_override, std::vector<Tile>& tiles);
 
 }  // namespace sip

@@ -17,7 +17,7 @@
 #include <cstring>
 #include <vector>
 
-#include "apply_kernels.cuh"
+#include "aux_kernels.cuh"
 #include "handle.h"
 
 namespace sip {
@@ -93,24 +93,25 @@ __global__ void __launch_bounds__(kRedThreads) k_final(const double* partial, in
     double beta = 0.0;
     if (active) {
       if (!isfinite(t)) atomicOr(status, ST_NONFINITE);
-      beta = t / sc[S_RR];
+      beta = sc[S_RR] > 0.0 ? t / sc[S_RR] : 0.0;
       sc[S_RR] = t;
     }
     sc[S_BETA] = beta;
   }
 }
 
-// x += alpha p, r -= alpha Ap, partial sums of r.r
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_update_xr(T* x, T* r, const T* p, const T* ap, int64_t n,
+// x += alpha p (in the precision of x), r -= alpha Ap, partial sums of r.r
+template <typename TX, typename T>
+__global__ void __launch_bounds__(kRedThreads) k_update_xr(TX* x, T* r, const T* p, const T* ap, int64_t n,
                                                            const double* scal, double* partial) {
   __shared__ double red[kRedThreads];
   const int rhs = blockIdx.y;
+  const TX alpha_x = (TX)scal[rhs * kScal + S_ALPHA];
   const T alpha = (T)scal[rhs * kScal + S_ALPHA];
   x += rhs * n; r += rhs * n; p += rhs * n; ap += rhs * n;
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
-    x[i] = fma(alpha, p[i], x[i]);
+    x[i] = fma(alpha_x, (TX)p[i], x[i]);
     const T ri = fma(-alpha, ap[i], r[i]);
     r[i] = ri;
     s += (double)ri * (double)ri;
@@ -133,6 +134,15 @@ __global__ void k_update_p(const T* r, T* p, int64_t n, const double* scal) {
 __global__ void k_residual(const double* b, double* r, int64_t total) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
     r[i] = b[i] - r[i];
+}
+
+// r32 = float(r64) (and p32 = r32 when p32 is given)
+__global__ void k_r64_to_r32(const double* r64, float* r32, float* p32, int64_t total) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = (float)r64[i];
+    r32[i] = v;
+    if (p32) p32[i] = v;
+  }
 }
 
 // r32 = float(s[rhs] * r64), x32 = 0, p32 = r32
@@ -189,7 +199,7 @@ void CgWork::release() {
 void sip_handle::release() {
   cg64.release();
   cg32.release();
-  cudaFree(r64); cudaFree(x64); cudaFree(red);
+  cudaFree(r64); cudaFree(x64); cudaFree(xbak); cudaFree(red);
   if (scal_host) cudaFreeHost(scal_host);
   for (auto* p : ck_x) cudaFree(p);
   for (auto* p : ck_r) cudaFree(p);
@@ -197,10 +207,11 @@ void sip_handle::release() {
   ck_x.clear(); ck_r.clear(); ck_p.clear();
   if (solve_stream) cudaStreamDestroy(solve_stream);
   cudaFree(dof_off); cudaFree(quad_off); cudaFree(vgoff); cudaFree(f_troff); cudaFree(f_goff);
-  cudaFree(slots); cudaFree(elist); cudaFree(tiles); cudaFree(xq);
+  cudaFree(slots); cudaFree(elist); cudaFree(tiles_d[0]); cudaFree(tiles_d[1]); cudaFree(xq);
   cudaFree(gd.vgeo); cudaFree(gd.fgeo); cudaFree(gd.tau); cudaFree(gd.kappa);
   cudaFree(gf.vgeo); cudaFree(gf.fgeo); cudaFree(gf.tau); cudaFree(gf.kappa);
   cudaFree(trace_d);
+  cudaFree(ug_d);
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);
 }
@@ -238,16 +249,17 @@ int ensure_solver(sip_handle* h, int nrhs) {
   }
   if (nrhs > 1000) return fail(SIP_ERR_ARG, "nrhs > 1000");
   if (h->work_nrhs < nrhs) {
-    cudaFree(h->r64); cudaFree(h->x64);
-    h->r64 = h->x64 = nullptr;
+    cudaFree(h->r64); cudaFree(h->x64); cudaFree(h->xbak);
+    h->r64 = h->x64 = h->xbak = nullptr;
     const size_t n = (size_t)h->plan.ndof * nrhs;
     cudaError_t e = cudaMalloc((void**)&h->r64, n * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->x64, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->xbak, n * sizeof(double));
     if (e != cudaSuccess) return cuda_fail(e, "solver vectors");
     h->work_nrhs = nrhs;
   }
   if (!h->red) {
-    const size_t nb = std::max<size_t>(h->plan.tiles.size(), 1024) * 1024 / 1024 + 2048;
+    const size_t nb = std::max<size_t>(h->tiles_h[0].size(), 1024) + 2048;
     cudaError_t e = cudaMalloc((void**)&h->red, nb * sizeof(double));
     if (e != cudaSuccess) return cuda_fail(e, "reduction buffer");
   }
@@ -270,8 +282,12 @@ int enqueue_iter(sip_handle* h, CgWork& W, int nrhs, int prec, int transpose, cu
   if (rc) return rc;
   enqueue_dot<T, T>(h, W, (const T*)W.p, (const T*)W.ap, nrhs, S_PAP, 1, s);
   const int nblk = red_blocks(n);
-  k_update_xr<T><<<dim3(nblk, nrhs), kRedThreads, 0, s>>>((T*)W.x, (T*)W.r, (const T*)W.p, (const T*)W.ap, n,
-                                                          W.scal, W.partial);
+  if (W.xext)
+    k_update_xr<double, T><<<dim3(nblk, nrhs), kRedThreads, 0, s>>>((double*)W.xext, (T*)W.r, (const T*)W.p,
+                                                                   (const T*)W.ap, n, W.scal, W.partial);
+  else
+    k_update_xr<T, T><<<dim3(nblk, nrhs), kRedThreads, 0, s>>>((T*)W.x, (T*)W.r, (const T*)W.p, (const T*)W.ap, n,
+                                                              W.scal, W.partial);
   k_final<<<nrhs, kRedThreads, 0, s>>>(W.partial, nblk, W.scal, S_RR, 2, W.status);
   k_update_p<T><<<vgrid(n, nrhs), 256, 0, s>>>((const T*)W.r, (T*)W.p, n, W.scal);
   cudaError_t e = cudaGetLastError();
@@ -288,7 +304,7 @@ int run_iters(sip_handle* h, CgWork& W, int nrhs, int prec, int transpose, int i
     }
     return SIP_OK;
   }
-  if (!W.graph || W.graph_iters != iters || W.graph_transpose != transpose) {
+  if (!W.graph || W.graph_iters != iters || W.graph_transpose != transpose || W.graph_xext != W.xext) {
     if (W.graph) cudaGraphExecDestroy(W.graph);
     W.graph = nullptr;
     const bool timing = h->timing;
@@ -307,6 +323,7 @@ int run_iters(sip_handle* h, CgWork& W, int nrhs, int prec, int transpose, int i
     if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
     W.graph_iters = iters;
     W.graph_transpose = transpose;
+    W.graph_xext = W.xext;
   }
   cudaError_t e = cudaGraphLaunch(W.graph, s);
   return e == cudaSuccess ? SIP_OK : cuda_fail(e, "graph launch");
@@ -440,33 +457,31 @@ int solve_impl(sip_handle* h, int mode, const double* b, double* x_out, int nrhs
       if (e != cudaSuccess) { cudaEventDestroy(evu); return cuda_fail(e, "checkpoint ring"); }
     }
   }
-  if (mode == SIP_CG_FP64) {
-    // x = 0, r = b, p = b, rr = ||b||^2
-    cudaMemsetAsync(W.x, 0, bytes, s);
-    cudaMemcpyAsync(W.r, b, bytes, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(W.p, b, bytes, cudaMemcpyDeviceToDevice, s);
+  // FP64 CG from the state (W.x, W.r = b - A W.x, rr) until the true residual meets tol
+  auto fp64_cg = [&](const std::vector<double>& r0n2) -> int {
+    cudaMemcpyAsync(W.p, W.r, bytes, cudaMemcpyDeviceToDevice, s);
     for (int r = 0; r < nrhs; ++r) {
       double* sc = h->scal_host + r * kScal;
       std::fill(sc, sc + kScal, 0.0);
-      sc[S_RR] = bn2[r];
-      sc[S_RR0] = bn2[r];
-      sc[S_ACTIVE] = bn2[r] > 0.0 ? 1.0 : 0.0;
+      sc[S_RR] = r0n2[r];
+      sc[S_RR0] = r0n2[r];
+      sc[S_ACTIVE] = std::sqrt(r0n2[r]) > tol[r] ? 1.0 : 0.0;
     }
     int zero = 0;
     cudaMemcpyAsync(W.status, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
-    rc = write_scal(h, W, nrhs, s);
+    int rc2 = write_scal(h, W, nrhs, s);
     int restarts = 0;
-    while (rc == SIP_OK) {
-      rc = cg_loop<double>(h, W, nrhs, SIP_FP64, transpose, tol, max_iter - st.iterations, &st.iterations, s, ckpt);
-      if (rc) break;
+    while (rc2 == SIP_OK) {
+      rc2 = cg_loop<double>(h, W, nrhs, SIP_FP64, transpose, tol, max_iter - st.iterations, &st.iterations, s, ckpt);
+      if (rc2) break;
       // true residual r64 = b - A x
-      rc = apply_any(h, SIP_FP64, W.x, h->r64, nrhs, s, transpose, nullptr);
-      if (rc) break;
+      rc2 = apply_any(h, SIP_FP64, W.x, h->r64, nrhs, s, transpose, nullptr);
+      if (rc2) break;
       st.applies_fp64 += 1;
       k_residual<<<vgrid(n * nrhs, 1), 256, 0, s>>>(b, h->r64, n * nrhs);
       std::vector<double> rn2;
-      rc = norms2(h, W, h->r64, nrhs, s, rn2);
-      if (rc) break;
+      rc2 = norms2(h, W, h->r64, nrhs, s, rn2);
+      if (rc2) break;
       bool all = true;
       worst = 0.0;
       for (int r = 0; r < nrhs; ++r) {
@@ -487,75 +502,138 @@ int solve_impl(sip_handle* h, int mode, const double* b, double* x_out, int nrhs
       ++restarts;
       cudaMemcpyAsync(W.r, h->r64, bytes, cudaMemcpyDeviceToDevice, s);
       cudaMemcpyAsync(W.p, h->r64, bytes, cudaMemcpyDeviceToDevice, s);
-      rc = write_scal(h, W, nrhs, s);
+      rc2 = write_scal(h, W, nrhs, s);
     }
+    return rc2;
+  };
+  if (mode == SIP_CG_FP64) {
+    // x = 0, r = b, rr = ||b||^2
+    cudaMemsetAsync(W.x, 0, bytes, s);
+    cudaMemcpyAsync(W.r, b, bytes, cudaMemcpyDeviceToDevice, s);
+    rc = fp64_cg(bn2);
     st.applies_fp64 += st.iterations;
     if (rc == SIP_OK) cudaMemcpyAsync(x_out, W.x, bytes, cudaMemcpyDeviceToDevice, s);
   } else {
+    // FP32 apply inside FP64 iterative refinement, in reliable-update form: one
+    // CG recurrence runs with FP32 vectors and the FP32 operator (FP64 dot
+    // products, FP64 iterate x); whenever the FP32 residual has fallen by
+    // kDelta since the last refinement, the FP64 residual r = b - A_64 x is
+    // recomputed and replaces it, keeping the search direction.
+    const double kDelta = 0.1;
     rc = ensure_cg(h, h->cg32, sizeof(float), nrhs);
     CgWork& V = h->cg32;
-    if (rc == SIP_OK) cudaMemsetAsync(h->x64, 0, bytes, s);
-    const double itol = h->plan.opt.inner_rtol;
-    double* sdev = W.partial;  // scale factors per RHS live in W.partial (free here)
-    int total_inner = 0;
-    for (int outer = 0; rc == SIP_OK; ++outer) {
-      // r64 = b - A x64 (x64 = 0 at the first step)
-      if (outer == 0) {
-        cudaMemcpyAsync(h->r64, b, bytes, cudaMemcpyDeviceToDevice, s);
-      } else {
-        rc = apply_any(h, SIP_FP64, h->x64, h->r64, nrhs, s, transpose, nullptr);
-        if (rc) break;
-        st.applies_fp64 += 1;
-        k_residual<<<vgrid(n * nrhs, 1), 256, 0, s>>>(b, h->r64, n * nrhs);
-      }
-      std::vector<double> rn2;
-      rc = norms2(h, W, h->r64, nrhs, s, rn2);
-      if (rc) break;
-      bool all = true;
-      worst = 0.0;
-      std::vector<double> scale(nrhs, 0.0), inv(nrhs, 0.0);
-      for (int r = 0; r < nrhs; ++r) {
-        worst = std::max(worst, bn2[r] > 0 ? std::sqrt(rn2[r] / bn2[r]) : 0.0);
-        if (std::sqrt(rn2[r]) > tol[r]) {
-          all = false;
-          inv[r] = 1.0 / std::sqrt(rn2[r]);
-          scale[r] = std::sqrt(rn2[r]);
-        }
-      }
-      if (all) { converged = true; break; }
-      if (outer >= h->plan.opt.max_refine || total_inner >= max_iter) break;
-      st.refinements += 1;
-      // inner system A d = r / ||r|| in FP32
-      cudaMemcpyAsync(sdev, inv.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s);
-      k_to_f32<<<vgrid(n, nrhs), 256, 0, s>>>(h->r64, (float*)V.r, (float*)V.x, (float*)V.p, n, sdev);
-      std::vector<double> rr32;
-      enqueue_dot<float, float>(h, V, (const float*)V.r, (const float*)V.r, nrhs, S_AUX, 0, s);
-      int stt = 0;
-      rc = read_scal(h, V, nrhs, s, &stt);
-      if (rc) break;
-      std::vector<double> itl(nrhs);
+    V.xext = h->x64;
+    if (rc == SIP_OK) {
+      cudaMemsetAsync(h->x64, 0, bytes, s);
+      cudaMemcpyAsync(h->r64, b, bytes, cudaMemcpyDeviceToDevice, s);
+      k_r64_to_r32<<<vgrid(n * nrhs, 1), 256, 0, s>>>(h->r64, (float*)V.r, (float*)V.p, n * nrhs);
       for (int r = 0; r < nrhs; ++r) {
         double* sc = h->scal_host + r * kScal;
-        const double rr = sc[S_AUX];
         std::fill(sc, sc + kScal, 0.0);
-        sc[S_RR] = rr;
-        sc[S_RR0] = rr;
-        sc[S_ACTIVE] = scale[r] > 0.0 ? 1.0 : 0.0;
-        itl[r] = itol * std::sqrt(rr);
+        sc[S_RR] = bn2[r];
+        sc[S_RR0] = bn2[r];
+        sc[S_ACTIVE] = bn2[r] > 0.0 ? 1.0 : 0.0;
       }
       int zero = 0;
       cudaMemcpyAsync(V.status, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
       rc = write_scal(h, V, nrhs, s);
-      if (rc) break;
-      int inner = 0;
-      rc = cg_loop<float>(h, V, nrhs, SIP_FP32, transpose, itl, max_iter - total_inner, &inner, s, false);
-      if (rc) break;
-      total_inner += inner;
-      st.applies_fp32 += inner;
-      cudaMemcpyAsync(sdev, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s);
-      k_add_f32<<<vgrid(n, nrhs), 256, 0, s>>>(h->x64, (const float*)V.x, n, sdev);
     }
-    st.iterations = total_inner;
+    std::vector<double> rmax(nrhs);
+    for (int r = 0; r < nrhs; ++r) rmax[r] = std::sqrt(bn2[r]);
+    const int chunk = std::max(1, h->plan.opt.check_every);
+    int total = 0;
+    bool all_conv = false;
+    double best = 1e300;   // best worst-case true residual so far
+    int stalled = 0;       // refinements without a 2x improvement of it
+    bool polish = false;   // fall back to FP64 CG from the last refined iterate
+    int since = 0;         // FP32 iterations since the last refinement
+    cudaMemsetAsync(h->xbak, 0, bytes, s);
+    while (rc == SIP_OK) {
+      // iterate until some RHS's FP32 residual has dropped by kDelta (or is below
+      // tol), or for a bounded number of iterations
+      bool trigger = false, broke = false;
+      const int cap = std::max(512, 4 * (st.refinements > 0 ? total / st.refinements : 0));
+      while (rc == SIP_OK && !trigger && total < max_iter) {
+        rc = run_iters<float>(h, V, nrhs, SIP_FP32, transpose, chunk, s, true);
+        if (rc) break;
+        total += chunk;
+        since += chunk;
+        int status = 0;
+        rc = read_scal(h, V, nrhs, s, &status);
+        if (rc) break;
+        if (status & (ST_NONFINITE | ST_BREAKDOWN)) { broke = true; break; }
+        for (int r = 0; r < nrhs; ++r) {
+          const double* sc = h->scal_host + r * kScal;
+          if (sc[S_ACTIVE] == 0.0) continue;
+          const double rn = std::sqrt(sc[S_RR]);
+          if (!std::isfinite(rn)) broke = true;
+          else if (rn <= kDelta * rmax[r] || rn <= tol[r]) trigger = true;
+        }
+        if (broke) break;
+        if (since >= cap) trigger = true;
+      }
+      if (rc) break;
+      if (broke) {
+        // the FP32 recurrence broke down (typically below the FP64 residual
+        // floor): return to the last refined iterate and finish in FP64
+        cudaMemcpyAsync(h->x64, h->xbak, bytes, cudaMemcpyDeviceToDevice, s);
+        if (st.refinements == 0) cudaMemcpyAsync(h->r64, b, bytes, cudaMemcpyDeviceToDevice, s);
+        polish = true;
+        break;
+      }
+      since = 0;
+      // refinement: FP64 residual of the FP64 iterate
+      rc = apply_any(h, SIP_FP64, h->x64, h->r64, nrhs, s, transpose, nullptr);
+      if (rc) break;
+      st.applies_fp64 += 1;
+      st.refinements += 1;
+      k_residual<<<vgrid(n * nrhs, 1), 256, 0, s>>>(b, h->r64, n * nrhs);
+      cudaMemcpyAsync(h->xbak, h->x64, bytes, cudaMemcpyDeviceToDevice, s);  // r64 is its residual
+      std::vector<double> rn2;
+      rc = norms2(h, W, h->r64, nrhs, s, rn2);
+      if (rc) break;
+      // norms2 overwrote nothing in V; reload V's scalars to edit them
+      int status = 0;
+      rc = read_scal(h, V, nrhs, s, &status);
+      if (rc) break;
+      all_conv = true;
+      worst = 0.0;
+      for (int r = 0; r < nrhs; ++r) {
+        double* sc = h->scal_host + r * kScal;
+        worst = std::max(worst, bn2[r] > 0 ? std::sqrt(rn2[r] / bn2[r]) : 0.0);
+        if (std::sqrt(rn2[r]) <= tol[r]) {
+          sc[S_ACTIVE] = 0.0;
+        } else {
+          all_conv = false;
+          sc[S_RR] = rn2[r];
+          sc[S_ACTIVE] = 1.0;
+          rmax[r] = std::sqrt(rn2[r]);
+        }
+      }
+      if (all_conv || total >= max_iter) break;
+      if (worst < 0.5 * best) { best = worst; stalled = 0; }
+      else if (++stalled >= 4) { polish = true; break; }  // FP32 recurrence no longer gains: finish in FP64
+      // replace the FP32 residual by the FP64 one, keep the search direction
+      k_r64_to_r32<<<vgrid(n * nrhs, 1), 256, 0, s>>>(h->r64, (float*)V.r, nullptr, n * nrhs);
+      rc = write_scal(h, V, nrhs, s);
+    }
+    converged = rc == SIP_OK && all_conv;
+    st.iterations = total;
+    st.applies_fp32 = total;
+    V.xext = nullptr;
+    if (rc == SIP_OK && polish) {
+      // FP64 CG from x64 with r = b - A_64 x64 (already in r64)
+      std::vector<double> rn2;
+      rc = norms2(h, W, h->r64, nrhs, s, rn2);
+      if (rc == SIP_OK) {
+        cudaMemcpyAsync(W.x, h->x64, bytes, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(W.r, h->r64, bytes, cudaMemcpyDeviceToDevice, s);
+        const int before = st.iterations;
+        rc = fp64_cg(rn2);
+        st.applies_fp64 += st.iterations - before;
+        if (rc == SIP_OK) cudaMemcpyAsync(h->x64, W.x, bytes, cudaMemcpyDeviceToDevice, s);
+      }
+    }
     if (rc == SIP_OK) cudaMemcpyAsync(x_out, h->x64, bytes, cudaMemcpyDeviceToDevice, s);
   }
   cudaEventRecord(evu, s);
@@ -574,9 +652,8 @@ int solve_impl(sip_handle* h, int mode, const double* b, double* x_out, int nrhs
 
 size_t aux_smem(sip_handle* h) {
   size_t m = 0;
-  for (const Tile& t : h->plan.tiles) {
-    const int epb = apply_epb(h->plan.dim, t.n, SIP_FP64);
-    m = std::max(m, (size_t)epb * aux_smem_per_element(h->plan.dim, t.n) * sizeof(double));
+  for (const Tile& t : h->tiles_h[0]) {
+    m = std::max(m, (size_t)t.count * aux_smem_per_element(h->plan.dim, t.n) * sizeof(double));
   }
   return m + kRedThreads * sizeof(double);
 }
@@ -587,8 +664,8 @@ int launch_aux(sip_handle* h, AuxArgs& a, cudaStream_t s) {
   a.vgoff = h->vgoff;
   a.vgeo = h->gd.vgeo;
   a.elist = h->elist;
-  a.tiles = h->tiles;
-  const int nt = (int)h->plan.tiles.size();
+  a.tiles = h->tiles_d[0];
+  const int nt = (int)h->tiles_h[0].size();
   cudaError_t e = h->plan.dim == 2 ? launch_aux_2d(a, nt, aux_smem(h), s) : launch_aux_3d(a, nt, aux_smem(h), s);
   return e == cudaSuccess ? SIP_OK : cuda_fail(e, "aux kernel");
 }
@@ -708,7 +785,7 @@ int sip_mass_dot(sip_handle* h, const double* av, const double* bv, double* out,
   rc = launch_aux(h, a, s);
   if (rc) return rc;
   // fixed-order final sum of the per-tile partials, straight into *out
-  const int nt = (int)h->plan.tiles.size();
+  const int nt = (int)h->tiles_h[0].size();
   static_assert(S_RR == 0, "slot 0");
   // reuse k_final in "store" mode with a 1-RHS scalar block at h->red + nt
   k_final<<<1, kRedThreads, 0, s>>>(h->red, nt, h->red + nt, 0, 0, nullptr);
@@ -750,12 +827,18 @@ int sip_work_model(const sip_handle* h, int precision, sip_work* out) {
     fm += grad + (2.0 * d * d + d + 2.0) * QV + grad + interp;  // gradient, pointwise, D^T, B^T
     for (int k = 0; k < 2 * d; ++k) {
       const FaceSlot& sl = p.slots[(size_t)e * 2 * d + k];
+      const bool orth = sl.flags & kFaceOrth;  // tangential terms vanish identically
       const double qf = sl.qf;
       const double np = d == 2 ? qf : qf * qf;
-      double interp_f = 0.0;
-      if (sl.qf != (int)Q) interp_f = 2.0 * (d + 1) * (d == 2 ? qf * Q : (Q * qf * Q + qf * qf * Q));
-      ft += 2.0 * 2.0 * QF1 * Q + 2.0 * (d - 1) * QF1 * Q + interp_f + 2.0 * d * np;
-      fm += 12.0 * np + d * np + interp_f + 2.0 * (1 + d) * QV;
+      const double nfl_t = orth ? 2.0 : 4.0, nfl_m = orth ? 2.0 : 1.0 + d;
+      double interp_t = 0.0, interp_m = 0.0;
+      if (sl.qf != (int)Q) {
+        const double per_field = 2.0 * (d == 2 ? qf * Q : (Q * qf * Q + qf * qf * Q));
+        interp_t = nfl_t * per_field;
+        interp_m = nfl_m * per_field;
+      }
+      ft += 2.0 * 2.0 * QF1 * Q + (orth ? 0.0 : 2.0 * (d - 1) * QF1 * Q) + interp_t + 2.0 * (orth ? 1.0 : d) * np;
+      fm += 12.0 * np + (orth ? 1.0 : d) * np + interp_m + 2.0 * nfl_m * QV;
     }
   }
   out->flops_trace = ft;

@@ -126,9 +126,9 @@ def _loss_at(op, b, ut, lam, kap):
     import torch
     op.set_lambda(lam)
     op.set_kappa(kap)
-    # FP32-apply CG inside FP64 refinement, to a 1e-12 FP64 residual (near the
-    # rounding floor of the FP64 residual b - A x for this conditioning)
-    u, st = op.cg_solve(b, mode=1, rtol=1e-12)
+    # FP64 CG to a 1e-12 residual (near the rounding floor of the FP64 residual
+    # b - A x at this conditioning, where FP32-apply refinement gains nothing)
+    u, st = op.cg_solve(b, mode=0, rtol=1e-12)
     return float(torch.sum((u - ut) ** 2))
 
 
