@@ -210,6 +210,21 @@ typedef struct sip_work {
 } sip_work;
 int  sip_work_model(const sip_handle* h, int precision, sip_work* out);
 
+/* Autotuner of the tile shape (elements per CTA for each polynomial order):
+ * coordinate descent over the orders present, timing the whole apply (best of
+ * three batches of reps launches) for a few candidate tile sizes of one order
+ * at a time, and installs the fastest for this precision.
+ * Set-up call: allocates temporaries and synchronises the stream.  The paper
+ * picks a kernel configuration per order (Sec. 5.1); this chooses it by
+ * measurement on the current GPU. */
+int  sip_autotune(sip_handle* h, int precision, int reps, void* stream);
+
+/* Current tiling: epb_out[P] = largest number of elements per tile used for
+ * order P (0 if the order is absent), P = 0..SIP_MAX_ORDER; *ntiles_out = tiles
+ * per apply (may be NULL). */
+int  sip_get_tiling(const sip_handle* h, int precision, int32_t* epb_out /* [SIP_MAX_ORDER+1] */,
+                    int64_t* ntiles_out);
+
 /* Device time of the last apply's kernels, per phase, measured with CUDA events
  * on the apply's stream when timing is enabled (sip_set_timing(h, 1)); ms. */
 int  sip_set_timing(sip_handle* h, int enable);

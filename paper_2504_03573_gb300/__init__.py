@@ -217,6 +217,17 @@ class SipOperator:
         check(lib.sip_cg_replay(self._h, _ptr(x), _ptr(r), _ptr(p), C.byref(rrc), int(iters), _stream()))
         return rrc.value
 
+    # ---- tile shape
+    def autotune(self, precision=SIP_FP64, reps=5):
+        check(lib.sip_autotune(self._h, precision, int(reps), _stream()))
+        return self.tiling(precision)
+
+    def tiling(self, precision=SIP_FP64):
+        epb = (C.c_int32 * (_lib.SIP_MAX_ORDER + 1))()
+        nt = C.c_int64()
+        check(lib.sip_get_tiling(self._h, precision, epb, C.byref(nt)))
+        return {"epb_by_order": list(epb), "ntiles": nt.value}
+
     # ---- timing of the apply kernels
     def set_timing(self, on: bool):
         check(lib.sip_set_timing(self._h, int(on)))

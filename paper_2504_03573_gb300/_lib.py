@@ -114,6 +114,8 @@ SIGNATURES = {
     "sip_work_model": (_I, [_H, _I, C.POINTER(sip_work)]),
     "sip_set_timing": (_I, [_H, _I]),
     "sip_last_kernel_ms": (_I, [_H, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "sip_autotune": (_I, [_H, _I, _I, _P]),
+    "sip_get_tiling": (_I, [_H, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     "sip_apply_static_scratch": (_I, [_H, _I, _P, _P, _I, _P]),
     "sip_last_error": (C.c_char_p, []),
 }

@@ -1,0 +1,131 @@
+// Autotuner of the tile shape: coordinate descent over the orders present,
+// trying a few elements-per-tile choices for one order at a time and timing the
+// whole apply (all order buckets in one launch), keeping a change only for a
+// clear gain.  The GPU counterpart of choosing a per-order kernel configuration
+// (Sec. 5.1).  Runs at set-up time; it allocates and synchronises.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <set>
+#include <vector>
+
+#include "handle.h"
+
+namespace sip {
+namespace {
+
+}  // namespace
+}  // namespace sip
+
+using namespace sip;
+
+extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream) {
+  if (!h) return fail(SIP_ERR_ARG, "null handle");
+  if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
+  if (reps < 1) reps = 10;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Plan& p = h->plan;
+  const int pi = precision == SIP_FP32 ? 1 : 0;
+  const int es = precision == SIP_FP32 ? 4 : 8;
+  int rc = handle_grow_trace(h, 1);
+  if (rc) return rc;
+  const size_t vb = (size_t)p.ndof * es;
+  void* x = nullptr;
+  void* y = nullptr;
+  cudaError_t e = cudaMalloc(&x, vb);
+  if (e == cudaSuccess) e = cudaMalloc(&y, vb);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, vb, s);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e != cudaSuccess) {
+    cudaFree(x); cudaFree(y);
+    return cuda_fail(e, "autotune set-up");
+  }
+  std::set<int> orders;
+  for (int32_t o : p.P) orders.insert(o + 1);
+  // coordinate descent over the orders, each candidate timed on the full apply
+  // (all buckets in one launch, as the solver runs it)
+  int cur[kNMax + 2] = {};
+  for (int n : orders) cur[n] = apply_epb(p.dim, n, precision);
+  const bool timing = h->timing;
+  h->timing = false;
+  auto time_full = [&](const int* epb, float* ms_out) -> int {
+    std::vector<Tile> t;
+    build_tiles(p, precision, epb, t);
+    size_t st = 0, sm = 0;
+    for (const Tile& tt : t) {
+      const size_t fixed = (size_t)table_block_bytes(es, tt.n) + kMetaBytes;
+      st = std::max(st, fixed + (size_t)tt.count * per_elem_trace(p.dim, tt.n) * es);
+      sm = std::max(sm, fixed + (size_t)tt.count * per_elem_main(p.dim, tt.n) * es);
+    }
+    if (st > 200 * 1024 || sm > 200 * 1024) { *ms_out = 1e30f; return SIP_OK; }
+    Tile* td = nullptr;
+    cudaError_t ee = cudaMalloc((void**)&td, t.size() * sizeof(Tile));
+    if (ee == cudaSuccess) ee = cudaMemcpy(td, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+    if (ee != cudaSuccess) { cudaFree(td); return cuda_fail(ee, "autotune tiles"); }
+    int r2 = SIP_OK;
+    for (int w = 0; w < 2 && r2 == SIP_OK; ++w)
+      r2 = apply_tiles(h, precision, td, (int)t.size(), st, sm, x, y, 1, s, 0, nullptr);
+    // best of three batches of reps launches
+    float best = 1e30f;
+    for (int batch = 0; batch < 3 && r2 == SIP_OK; ++batch) {
+      cudaEventRecord(a, s);
+      for (int r = 0; r < reps && r2 == SIP_OK; ++r)
+        r2 = apply_tiles(h, precision, td, (int)t.size(), st, sm, x, y, 1, s, 0, nullptr);
+      cudaEventRecord(b, s);
+      ee = cudaEventSynchronize(b);
+      if (ee != cudaSuccess) { r2 = cuda_fail(ee, "autotune timing"); break; }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, a, b);
+      best = std::min(best, ms);
+    }
+    cudaFree(td);
+    *ms_out = best;
+    return r2;
+  };
+  float cur_ms = 1e30f;
+  rc = time_full(cur, &cur_ms);
+  for (int n : orders) {
+    if (rc) break;
+    const int base = cur[n];
+    const int per = std::max(per_elem_trace(p.dim, n), per_elem_main(p.dim, n)) * es;
+    const int room = (160 * 1024 - table_block_bytes(es, n) - kMetaBytes) / per;
+    std::set<int> cand;
+    for (int c : {base / 4, base / 2, 2 * base, 4 * base}) cand.insert(std::max(1, std::min({c, room, kMaxEpb})));
+    cand.erase(base);
+    for (int c : cand) {
+      int trial[kNMax + 2];
+      std::memcpy(trial, cur, sizeof(trial));
+      trial[n] = c;
+      float ms = 0.0f;
+      rc = time_full(trial, &ms);
+      if (rc) break;
+      if (ms < 0.97f * cur_ms) {  // keep a change only for a clear gain
+        cur_ms = ms;
+        cur[n] = c;
+      }
+    }
+  }
+  int* best = cur;
+  h->timing = timing;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(x);
+  cudaFree(y);
+  if (rc) return rc;
+  rc = set_tiles(h, precision, best);
+  if (rc) return rc;
+  std::memcpy(h->epb[pi], best, sizeof(best));
+  return SIP_OK;
+}
+
+extern "C" int sip_get_tiling(const sip_handle* h, int precision, int32_t* epb_out, int64_t* ntiles_out) {
+  if (!h || !epb_out) return fail(SIP_ERR_ARG, "null argument");
+  const int pi = precision == SIP_FP32 ? 1 : 0;
+  for (int n = 0; n <= kNMax; ++n) epb_out[n] = 0;
+  for (const Tile& t : h->tiles_h[pi]) epb_out[t.n - 1] = std::max(epb_out[t.n - 1], (int32_t)t.count);
+  if (ntiles_out) *ntiles_out = (int64_t)h->tiles_h[pi].size();
+  return SIP_OK;
+}

@@ -193,15 +193,8 @@ ApplyArgs<T> make_args(sip_handle* h, const T* x, T* y, T* trace, T* ug, int tra
   return a;
 }
 
-int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cudaStream_t s,
-              int transpose, void* scratch_override) {
-  if (!h || !x || !y) return fail(SIP_ERR_ARG, "null handle or vector");
-  if (nrhs < 1) return fail(SIP_ERR_ARG, "nrhs must be >= 1");
-  if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
-  if (!scratch_override) {
-    int rc = handle_grow_trace(h, nrhs);
-    if (rc) return rc;
-  }
+int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, int ntiles, size_t smem_t, size_t smem_m,
+                const void* x, void* y, int nrhs, cudaStream_t s, int transpose, void* scratch_override) {
   size_t ug_off = 0;
   apply_scratch_bytes(h, precision, nrhs, &ug_off);
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
@@ -211,19 +204,33 @@ int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cu
     double* tr = scratch_override ? (double*)scratch_override : h->trace_d;
     double* ug = scratch_override ? (double*)((char*)scratch_override + ug_off) : h->ug_d;
     auto a = make_args<double>(h, (const double*)x, (double*)y, tr, ug, transpose);
-    const int nt = (int)h->tiles_h[0].size();
-    e = h->plan.dim == 2 ? launch_apply_2d_f64(a, nt, nrhs, h->smem_trace[0], h->smem_main[0], s, e0, e1, e2)
-                         : launch_apply_3d_f64(a, nt, nrhs, h->smem_trace[0], h->smem_main[0], s, e0, e1, e2);
+    a.tiles = tiles_d;
+    e = h->plan.dim == 2 ? launch_apply_2d_f64(a, ntiles, nrhs, smem_t, smem_m, s, e0, e1, e2)
+                         : launch_apply_3d_f64(a, ntiles, nrhs, smem_t, smem_m, s, e0, e1, e2);
   } else {
     float* tr = scratch_override ? (float*)scratch_override : (float*)h->trace_d;
     auto a = make_args<float>(h, (const float*)x, (float*)y, tr, nullptr, transpose);
-    const int nt = (int)h->tiles_h[1].size();
-    e = h->plan.dim == 2 ? launch_apply_2d_f32(a, nt, nrhs, h->smem_trace[1], h->smem_main[1], s, e0, e1, e2)
-                         : launch_apply_3d_f32(a, nt, nrhs, h->smem_trace[1], h->smem_main[1], s, e0, e1, e2);
+    a.tiles = tiles_d;
+    e = h->plan.dim == 2 ? launch_apply_2d_f32(a, ntiles, nrhs, smem_t, smem_m, s, e0, e1, e2)
+                         : launch_apply_3d_f32(a, ntiles, nrhs, smem_t, smem_m, s, e0, e1, e2);
   }
   if (e != cudaSuccess) return cuda_fail(e, "apply launch");
   h->timed_pending = h->timing;
   return SIP_OK;
+}
+
+int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cudaStream_t s,
+              int transpose, void* scratch_override) {
+  if (!h || !x || !y) return fail(SIP_ERR_ARG, "null handle or vector");
+  if (nrhs < 1) return fail(SIP_ERR_ARG, "nrhs must be >= 1");
+  if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
+  if (!scratch_override) {
+    int rc = handle_grow_trace(h, nrhs);
+    if (rc) return rc;
+  }
+  const int pi = precision == SIP_FP32 ? 1 : 0;
+  return apply_tiles(h, precision, h->tiles_d[pi], (int)h->tiles_h[pi].size(), h->smem_trace[pi], h->smem_main[pi],
+                     x, y, nrhs, s, transpose, scratch_override);
 }
 
 }  // namespace sip

@@ -56,6 +56,7 @@ struct sip_handle {
   int32_t* elist = nullptr;
   sip::Tile* tiles_d[2] = {nullptr, nullptr};   // per precision (FP64, FP32)
   std::vector<sip::Tile> tiles_h[2];
+  int epb[2][sip::kNMax + 2] = {};                // elements per tile per order in use (0: default)
   double* xq = nullptr;
   sip::DevGeom<double> gd;
   sip::DevGeom<float> gf;
@@ -103,6 +104,8 @@ int cuda_fail(cudaError_t e, const char* where);
 int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cudaStream_t s,
               int transpose, void* scratch_override);
 size_t apply_scratch_bytes(const sip_handle* h, int precision, int nrhs, size_t* ug_offset);
+int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, int ntiles, size_t smem_t, size_t smem_m,
+                const void* x, void* y, int nrhs, cudaStream_t s, int transpose, void* scratch_override);
 int set_tiles(sip_handle* h, int precision, const int* epb_by_n);
 int handle_grow_trace(sip_handle* h, int nrhs);
 }  // namespace sip

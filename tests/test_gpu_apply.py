@@ -163,3 +163,20 @@ def test_bad_inputs_raise(pkg):
         op.apply(torch.zeros(op.ndof + 1, dtype=torch.float64, device="cuda"))
     with pytest.raises(pkg.SipError):
         op.apply(torch.zeros(op.ndof, dtype=torch.float64))
+
+
+@pytest.mark.parametrize("name", ["2d_rot_jitter_p1to8", "3d_rot_jitter_p1to5"])
+def test_autotuned_tiles_keep_parity(pkg, name):
+    import torch
+    m = MESHES[name]
+    orc = SipOracle(m)
+    A = orc.assemble()
+    op = pkg.SipOperator.from_mesh(m)
+    x = si.random_vector(orc.ndof, 0)
+    for prec, dt, tol in ((pkg.SIP_FP64, torch.float64, TOL64), (pkg.SIP_FP32, torch.float32, TOL32)):
+        before = op.tiling(prec)
+        after = op.autotune(prec, reps=2)
+        assert after["ntiles"] > 0
+        assert [b > 0 for b in before["epb_by_order"]] == [a > 0 for a in after["epb_by_order"]]
+        y = op.apply(torch.tensor(x, device="cuda", dtype=dt)).double().cpu().numpy()
+        assert rel(y, A @ x) <= tol
