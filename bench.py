@@ -198,7 +198,7 @@ def run_gb300(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def timed_applies(xin, yout, steps, warmup, kernel_times=False):
+    def timed_applies(xin, yout, steps, warmup, kernel_times=False, label="timed"):
         for _ in range(warmup):
             op.apply(xin, out=yout)
         op.set_timing(kernel_times)
@@ -206,6 +206,7 @@ def run_gb300(args):
         kt = []
         barrier()
         t0 = time.perf_counter()
+        torch.cuda.nvtx.range_push(label)   # lets ncu --nvtx-include select the timed launches
         for i in range(steps):
             flush.fill_(float(i))
             evs[i][0].record(stream)
@@ -213,6 +214,7 @@ def run_gb300(args):
             evs[i][1].record(stream)
             if kernel_times:
                 kt.append(op.last_kernel_ms())
+        torch.cuda.nvtx.range_pop()
         barrier()
         wall = time.perf_counter() - t0
         op.set_timing(False)
@@ -221,7 +223,7 @@ def run_gb300(args):
 
     # ---- headline: FP64 apply
     with ClockSampler(local) as clk:
-        ms, kt, wall = timed_applies(x, y, args.steps, args.warmup, kernel_times=True)
+        ms, kt, wall = timed_applies(x, y, args.steps, args.warmup, kernel_times=True, label="timed_fp64")
     clocks = clk.summary()
     t_step = sum(ms) / len(ms) / 1e3
     t_max = t_step
@@ -232,7 +234,7 @@ def run_gb300(args):
     value = world * n / t_max / 1e9
 
     # ---- FP32 apply (same protocol)
-    ms32, kt32, _ = timed_applies(x32, y32, args.steps, args.warmup, kernel_times=True)
+    ms32, kt32, _ = timed_applies(x32, y32, args.steps, args.warmup, kernel_times=True, label="timed_fp32")
     t32 = sum(ms32) / len(ms32) / 1e3
 
     # ---- roofline of the dominant kernel (the main kernel), FP64

@@ -46,7 +46,7 @@ struct Shape {
   static constexpr int QF1 = cpow(Q, DIM - 1);       // own points on one face
   static constexpr int FMAX = cpow(kQMax, DIM - 1);  // points on one face at the finest rule
   static constexpr int FT = DIM == 3 ? kQMax * Q : 0;
-  static constexpr int NFB = faces_per_batch(DIM);
+  static constexpr int NFACE = 2 * DIM;
   static constexpr int PER_TRACE = per_elem_trace(DIM, N);
   static constexpr int PER_MAIN = per_elem_main(DIM, N);
 };
@@ -77,6 +77,8 @@ __device__ __forceinline__ void load_tables(T* tb) {
       tb[TabLayout::II(N, f) + z * Q + r] = v;
     }
   }
+  for (int f = Q; f <= kQMax; ++f)
+    for (int z = threadIdx.x; z < f; z += blockDim.x) tb[TabLayout::GW(N, f) + z] = cgw<T>(f, z);
   __syncthreads();
 }
 
@@ -147,39 +149,63 @@ __device__ __forceinline__ int qpow(int e) { return e == 0 ? 1 : (e == 1 ? Q : Q
 struct TileMeta {
   int32_t eid[kMaxEpb];
   FaceSlot slot[kMaxEpb * 6];
+  int8_t aff[kMaxEpb];
 };
+static_assert(sizeof(TileMeta) <= kMetaBytes, "TileMeta exceeds its shared-memory block");
 
 template <int DIM>
-__device__ __forceinline__ void load_meta(const int32_t* elist, const FaceSlot* slots, const Tile& t, TileMeta* mt) {
+__device__ __forceinline__ void load_meta(const int32_t* elist, const FaceSlot* slots, const int8_t* eaff,
+                                          const Tile& t, TileMeta* mt) {
   for (int w = threadIdx.x; w < t.count * 2 * DIM; w += blockDim.x) {
     const int el = w / (2 * DIM), k = w - el * 2 * DIM;
     const int e = elist[t.start + el];
-    if (k == 0) mt->eid[el] = e;
+    if (k == 0) {
+      mt->eid[el] = e;
+      mt->aff[el] = eaff[e];
+    }
     mt->slot[el * 2 * DIM + k] = slots[(int64_t)e * 2 * DIM + k];
   }
 }
 
-// Faces K0 .. K0+NFB-1 of every element of the tile, processed together.
-template <typename T, int DIM, int N, int K0>
-__device__ __forceinline__ void trace_faces(const ApplyArgs<T>& a, const Tile& t, const TileMeta* mt, int rhs,
-                                            const T* tb, T* sm, const T* U) {
+// face geometry at canonical point zc: W, and component m of c on the given side
+template <typename T>
+struct FaceGeo {
+  const T* g;
+  int npts, zc, side, dim;
+  bool aff;
+  T w;  // Gauss weight of the point (affine faces)
+  __device__ __forceinline__ T W() const { return aff ? g[0] * w : g[zc]; }
+  __device__ __forceinline__ T c(int m) const {
+    const int comp = 1 + side * dim + m;
+    return aff ? g[comp] : g[(int64_t)comp * npts + zc];
+  }
+};
+
+// Trace values of all 2 DIM faces of every element of the tile.  Conforming
+// faces (shared rule = own Q points) go straight from the per-face buffer to the
+// trace; faces with a finer shared rule are interpolated one face at a time in
+// the element's scratch.
+template <typename T, int DIM, int N>
+__device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Tile& t, const TileMeta* mt, int rhs,
+                                                const T* tb, T* sm, const T* U) {
   using S = Shape<DIM, N>;
-  constexpr int Q = S::Q, QF1 = S::QF1, FMAX = S::FMAX, FT = S::FT, NFB = S::NFB, PER = S::PER_TRACE;
-  constexpr int FB = 4 * (QF1 + FT + FMAX);  // per face in the batch: Fq [4][QF1], Ft [4][FT], Ff [4][FMAX]
+  constexpr int Q = S::Q, QF1 = S::QF1, FMAX = S::FMAX, FT = S::FT, NFACE = S::NFACE, PER = S::PER_TRACE;
   const int ne = t.count;
   const int qfm = t.flags & kTileQfMask;
   const bool fine = t.flags & kTileFine;
   const bool orth = t.flags & kTileOrth;
   const int npm = DIM == 2 ? qfm : qfm * qfm;
+  // per element: Fq [NFACE][4][QF1] (u, du/dn_ref, two tangential derivatives), then scratch
   T* const F0 = sm + 2 * S::QV;
+  constexpr int SC = NFACE * 4 * QF1;  // scratch offset from F0: Ft [4][FT], Ff [4][FMAX]
   const T* LL = tb + TabLayout::LL(N);
   const T* DT = tb + TabLayout::DT(N);
   // 1. value and reference normal derivative at the element's own face points
-  for (int w = threadIdx.x; w < ne * NFB * QF1; w += blockDim.x) {
-    const int el = w / (NFB * QF1);
-    const int rem = w - el * NFB * QF1;
-    const int fb = rem / QF1, j = rem - fb * QF1;
-    const int k = K0 + fb, ax = k >> 1, sd = k & 1;
+  for (int w = threadIdx.x; w < ne * NFACE * QF1; w += blockDim.x) {
+    const int el = w / (NFACE * QF1);
+    const int rem = w - el * NFACE * QF1;
+    const int k = rem / QF1, j = rem - k * QF1;
+    const int ax = k >> 1, sd = k & 1;
     int t0, t1;
     tang_axes<DIM>(ax, t0, t1);
     const int j0 = j % Q, j1 = j / Q;
@@ -192,22 +218,22 @@ __device__ __forceinline__ void trace_faces(const ApplyArgs<T>& a, const Tile& t
       uf = fma(LL[sd * Q + r], v, uf);
       dn = fma(LL[(2 + sd) * Q + r], v, dn);
     }
-    T* fq = F0 + el * PER + fb * FB;
+    T* fq = F0 + el * PER + k * 4 * QF1;
     fq[j] = uf;
     fq[QF1 + j] = dn;
   }
   __syncthreads();
-  // 2. tangential derivatives of the face values (collocation on the Gauss
-  //    points); not needed where c has no tangential component
+  // 2. tangential derivatives of the face values (collocation on the Gauss points);
+  //    not needed where c has no tangential component
   if (!orth) {
-    for (int w = threadIdx.x; w < ne * NFB * (DIM - 1) * QF1; w += blockDim.x) {
-      const int el = w / (NFB * (DIM - 1) * QF1);
-      const int rem = w - el * NFB * (DIM - 1) * QF1;
-      const int fb = rem / ((DIM - 1) * QF1);
-      const int r2 = rem - fb * (DIM - 1) * QF1;
+    for (int w = threadIdx.x; w < ne * NFACE * (DIM - 1) * QF1; w += blockDim.x) {
+      const int el = w / (NFACE * (DIM - 1) * QF1);
+      const int rem = w - el * NFACE * (DIM - 1) * QF1;
+      const int k = rem / ((DIM - 1) * QF1);
+      const int r2 = rem - k * (DIM - 1) * QF1;
       const int m = r2 / QF1, j = r2 - m * QF1;
       const int j0 = j % Q, j1 = j / Q;
-      T* fq = F0 + el * PER + fb * FB;
+      T* fq = F0 + el * PER + k * 4 * QF1;
       T d = 0;
       if (m == 0) {
 #pragma unroll
@@ -220,92 +246,104 @@ __device__ __forceinline__ void trace_faces(const ApplyArgs<T>& a, const Tile& t
     }
     __syncthreads();
   }
-  // 3. interpolation to the shared face rule where it is finer (p-non-conforming faces)
-  if (fine) {
-    const int nfld = orth ? 2 : 4;
-    if constexpr (DIM == 2) {
-      for (int w = threadIdx.x; w < ne * NFB * nfld * qfm; w += blockDim.x) {
-        const int el = w / (NFB * nfld * qfm);
-        const int rem = w - el * NFB * nfld * qfm;
-        const int fb = rem / (nfld * qfm), r2 = rem - fb * nfld * qfm;
-        const int f = r2 / qfm, z = r2 - f * qfm;
-        const int qf = mt->slot[el * 2 * DIM + K0 + fb].qf;
-        if (qf == Q || z >= qf) continue;
-        const T* IT = tb + TabLayout::IT(N, qf);
-        T* fq = F0 + el * PER + fb * FB;
-        const T* src = fq + f * QF1;
-        T s = 0;
-#pragma unroll
-        for (int r = 0; r < Q; ++r) s = fma(IT[r * qf + z], src[r], s);
-        fq[4 * (QF1 + FT) + f * FMAX + z] = s;
-      }
-      __syncthreads();
-    } else {
-      for (int w = threadIdx.x; w < ne * NFB * nfld * Q * qfm; w += blockDim.x) {
-        const int el = w / (NFB * nfld * Q * qfm);
-        const int rem = w - el * NFB * nfld * Q * qfm;
-        const int fb = rem / (nfld * Q * qfm), r2 = rem - fb * nfld * Q * qfm;
-        const int f = r2 / (Q * qfm), r3 = r2 - f * Q * qfm;
-        const int j1 = r3 / qfm, z0 = r3 - j1 * qfm;
-        const int qf = mt->slot[el * 2 * DIM + K0 + fb].qf;
-        if (qf == Q || z0 >= qf) continue;
-        const T* IT = tb + TabLayout::IT(N, qf);
-        T* fq = F0 + el * PER + fb * FB;
-        const T* src = fq + f * QF1 + j1 * Q;
-        T s = 0;
-#pragma unroll
-        for (int r = 0; r < Q; ++r) s = fma(IT[r * qf + z0], src[r], s);
-        fq[4 * QF1 + f * FT + j1 * kQMax + z0] = s;
-      }
-      __syncthreads();
-      for (int w = threadIdx.x; w < ne * NFB * nfld * npm; w += blockDim.x) {
-        const int el = w / (NFB * nfld * npm);
-        const int rem = w - el * NFB * nfld * npm;
-        const int fb = rem / (nfld * npm), r2 = rem - fb * nfld * npm;
-        const int f = r2 / npm, zz = r2 - f * npm;
-        const int z1 = zz / qfm, z0 = zz - z1 * qfm;
-        const int qf = mt->slot[el * 2 * DIM + K0 + fb].qf;
-        if (qf == Q || z0 >= qf || z1 >= qf) continue;
-        const T* IT = tb + TabLayout::IT(N, qf);
-        T* fq = F0 + el * PER + fb * FB;
-        const T* src = fq + 4 * QF1 + f * FT + z0;
-        T s = 0;
-#pragma unroll
-        for (int r = 0; r < Q; ++r) s = fma(IT[r * qf + z1], src[r * kQMax], s);
-        fq[4 * (QF1 + FT) + f * FMAX + z0 + qf * z1] = s;
-      }
-      __syncthreads();
-    }
-  }
-  // 4. normal derivative c . grad_ref u, stored in canonical face order
-  for (int w = threadIdx.x; w < ne * NFB * npm; w += blockDim.x) {
-    const int el = w / (NFB * npm);
-    const int rem = w - el * NFB * npm;
-    const int fb = rem / npm, zz = rem - fb * npm;
-    const int z0 = zz % qfm, z1 = zz / qfm;
-    const int k = K0 + fb, ax = k >> 1;
+  // normal derivative c . grad_ref u and store at canonical point zc
+  auto emit = [&](int el, int k, const T* src, int fs, int z0, int z1) {
     const FaceSlot sl = mt->slot[el * 2 * DIM + k];
-    const int qf = sl.qf;
-    if (z0 >= qf || z1 >= qf) continue;
+    const int qf = sl.qf, ax = k >> 1;
     const int npts = DIM == 2 ? qf : qf * qf;
     const int z = z0 + qf * z1;
-    const bool fq_fine = qf != Q;
-    const T* fq = F0 + el * PER + fb * FB;
-    const T* src = fq_fine ? fq + 4 * (QF1 + FT) : fq;
-    const int fs = fq_fine ? FMAX : QF1;
     const int zc = canon(DIM, sl.side, sl.orient, qf, z0, z1);
-    const int64_t go = a.f_goff[sl.face];
-    const T* c = a.fgeo + go + (int64_t)(1 + sl.side * DIM) * npts + zc;
-    T g = c[(int64_t)ax * npts] * src[fs + z];
+    FaceGeo<T> fg{a.fgeo + a.f_goff[sl.face], npts, zc, sl.side, DIM, (sl.flags & kFaceAffine) != 0, T(0)};
+    T g = fg.c(ax) * src[fs + z];
     if (!orth) {
       int t0, t1;
       tang_axes<DIM>(ax, t0, t1);
-      g += c[(int64_t)t0 * npts] * src[2 * fs + z];
-      if constexpr (DIM == 3) g += c[(int64_t)t1 * npts] * src[3 * fs + z];
+      g += fg.c(t0) * src[2 * fs + z];
+      if constexpr (DIM == 3) g += fg.c(t1) * src[3 * fs + z];
     }
     T* tr = a.trace + rhs * a.trace_stride + 4 * a.f_troff[sl.face] + (int64_t)(2 * sl.side) * npts + zc;
     tr[0] = src[z];
     tr[npts] = g;
+  };
+  // 3. conforming faces, all at once
+  for (int w = threadIdx.x; w < ne * NFACE * QF1; w += blockDim.x) {
+    const int el = w / (NFACE * QF1);
+    const int rem = w - el * NFACE * QF1;
+    const int k = rem / QF1, j = rem - k * QF1;
+    if (mt->slot[el * 2 * DIM + k].qf != Q) continue;
+    emit(el, k, F0 + el * PER + k * 4 * QF1, QF1, j % Q, j / Q);
+  }
+  // 4. faces with a finer shared rule (p-non-conforming): NSC faces per round,
+  //    each in its own scratch slot
+  if (fine) {
+    constexpr int NSC = scratch_slots(DIM);
+    constexpr int SL = 4 * (FT + FMAX);  // one slot: Ft [4][FT], Ff [4][FMAX]
+    const int nfld = orth ? 2 : 4;
+    for (int k0 = 0; k0 < NFACE; k0 += NSC) {
+      if constexpr (DIM == 2) {
+        for (int w = threadIdx.x; w < ne * NSC * nfld * qfm; w += blockDim.x) {
+          const int el = w / (NSC * nfld * qfm);
+          const int rem = w - el * NSC * nfld * qfm;
+          const int kk = rem / (nfld * qfm), r2 = rem - kk * nfld * qfm;
+          const int f = r2 / qfm, z = r2 - f * qfm;
+          const int k = k0 + kk;
+          const int qf = mt->slot[el * 2 * DIM + k].qf;
+          if (qf == Q || z >= qf) continue;
+          const T* IT = tb + TabLayout::IT(N, qf);
+          const T* src = F0 + el * PER + k * 4 * QF1 + f * QF1;
+          T s = 0;
+#pragma unroll
+          for (int r = 0; r < Q; ++r) s = fma(IT[r * qf + z], src[r], s);
+          F0[el * PER + SC + kk * SL + 4 * FT + f * FMAX + z] = s;
+        }
+        __syncthreads();
+      } else {
+        for (int w = threadIdx.x; w < ne * NSC * nfld * Q * qfm; w += blockDim.x) {
+          const int el = w / (NSC * nfld * Q * qfm);
+          const int rem = w - el * NSC * nfld * Q * qfm;
+          const int kk = rem / (nfld * Q * qfm), r2 = rem - kk * nfld * Q * qfm;
+          const int f = r2 / (Q * qfm), r3 = r2 - f * Q * qfm;
+          const int j1 = r3 / qfm, z0 = r3 - j1 * qfm;
+          const int k = k0 + kk;
+          const int qf = mt->slot[el * 2 * DIM + k].qf;
+          if (qf == Q || z0 >= qf) continue;
+          const T* IT = tb + TabLayout::IT(N, qf);
+          const T* src = F0 + el * PER + k * 4 * QF1 + f * QF1 + j1 * Q;
+          T s = 0;
+#pragma unroll
+          for (int r = 0; r < Q; ++r) s = fma(IT[r * qf + z0], src[r], s);
+          F0[el * PER + SC + kk * SL + f * FT + j1 * kQMax + z0] = s;
+        }
+        __syncthreads();
+        for (int w = threadIdx.x; w < ne * NSC * nfld * npm; w += blockDim.x) {
+          const int el = w / (NSC * nfld * npm);
+          const int rem = w - el * NSC * nfld * npm;
+          const int kk = rem / (nfld * npm), r2 = rem - kk * nfld * npm;
+          const int f = r2 / npm, zz = r2 - f * npm;
+          const int z1 = zz / qfm, z0 = zz - z1 * qfm;
+          const int k = k0 + kk;
+          const int qf = mt->slot[el * 2 * DIM + k].qf;
+          if (qf == Q || z0 >= qf || z1 >= qf) continue;
+          const T* IT = tb + TabLayout::IT(N, qf);
+          const T* src = F0 + el * PER + SC + kk * SL + f * FT + z0;
+          T s = 0;
+#pragma unroll
+          for (int r = 0; r < Q; ++r) s = fma(IT[r * qf + z1], src[r * kQMax], s);
+          F0[el * PER + SC + kk * SL + 4 * FT + f * FMAX + z0 + qf * z1] = s;
+        }
+        __syncthreads();
+      }
+      for (int w = threadIdx.x; w < ne * NSC * npm; w += blockDim.x) {
+        const int el = w / (NSC * npm), r2 = w - el * NSC * npm;
+        const int kk = r2 / npm, zz = r2 - kk * npm;
+        const int z0 = zz % qfm, z1 = zz / qfm;
+        const int k = k0 + kk;
+        const int qf = mt->slot[el * 2 * DIM + k].qf;
+        if (qf == Q || z0 >= qf || z1 >= qf) continue;
+        emit(el, k, F0 + el * PER + SC + kk * SL + 4 * FT, FMAX, z0, z1);
+      }
+      __syncthreads();
+    }
   }
   __syncthreads();
 }
@@ -315,7 +353,7 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
   using S = Shape<DIM, N>;
   constexpr int PER = S::PER_TRACE;
   const int ne = t.count;
-  load_meta<DIM>(a.elist, a.slots, t, mt);
+  load_meta<DIM>(a.elist, a.slots, a.eaff, t, mt);
   load_tables<T, N>(tb);
   for (int w = threadIdx.x; w < ne * S::NV; w += blockDim.x) {
     const int el = w / S::NV, i = w - el * S::NV;
@@ -334,157 +372,174 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
       a.ug[rhs * a.nquad + a.quad_off[mt->eid[el]] + q] = U[el * PER + q];
     }
   }
-  if constexpr (DIM == 2) {
-    trace_faces<T, DIM, N, 0>(a, t, mt, rhs, tb, sm, U);
-  } else {
-    trace_faces<T, DIM, N, 0>(a, t, mt, rhs, tb, sm, U);
-    trace_faces<T, DIM, N, 1>(a, t, mt, rhs, tb, sm, U);
-    trace_faces<T, DIM, N, 2>(a, t, mt, rhs, tb, sm, U);
-    trace_faces<T, DIM, N, 3>(a, t, mt, rhs, tb, sm, U);
-    trace_faces<T, DIM, N, 4>(a, t, mt, rhs, tb, sm, U);
-    trace_faces<T, DIM, N, 5>(a, t, mt, rhs, tb, sm, U);
-  }
+  trace_all_faces<T, DIM, N>(a, t, mt, rhs, tb, sm, U);
 }
 
 // ============================================================ main kernel
-template <typename T, int DIM, int N, int K0>
-__device__ __forceinline__ void lift_faces(const ApplyArgs<T>& a, const Tile& t, const TileMeta* mt, int rhs,
-                                           const T* tb, T* sm) {
+// SIP flux of face k of element el at its shared point (z0, z1) (own order):
+// writes s and c_m t (m = 0..DIM-1; only c_a t where the tile is orthogonal) to
+// dst[f * fs + z0 + qf z1].
+template <typename T, int DIM, int N>
+__device__ __forceinline__ void face_flux(const ApplyArgs<T>& a, const TileMeta* mt, int rhs, const T* tb,
+                                          bool orth, int el, int k, int z0, int z1, T* dst, int fs) {
+  const FaceSlot sl = mt->slot[el * 2 * DIM + k];
+  const int qf = sl.qf, ax = k >> 1;
+  const int npts = DIM == 2 ? qf : qf * qf;
+  const int z = z0 + qf * z1;
+  const int zc = canon(DIM, sl.side, sl.orient, qf, z0, z1);
+  const T* tr = a.trace + rhs * a.trace_stride + 4 * a.f_troff[sl.face] + zc;
+  const bool faff = (sl.flags & kFaceAffine) != 0;
+  const T* GWf = tb + TabLayout::GW(N, qf);
+  const T wz = faff ? (DIM == 2 ? GWf[zc] : GWf[zc % qf] * GWf[zc / qf]) : T(0);
+  FaceGeo<T> fg{a.fgeo + a.f_goff[sl.face], npts, zc, sl.side, DIM, faff, wz};
+  const T W = fg.W();
+  const T tau = a.f_tau[sl.face];
+  const T uo = tr[(int64_t)(2 * sl.side) * npts];
+  const T go_ = tr[(int64_t)(2 * sl.side + 1) * npts];
+  T s, tt;
+  if (sl.flags & kFaceBnd) {
+    // Nitsche: -(grad v.n, u) - (v, grad u.n) + tau (v, u)
+    if (!a.transpose) { s = W * (tau * uo - go_); tt = -W * uo; }
+    else { s = W * tau * uo - W * go_; tt = -(W * uo); }
+  } else {
+    const int oth = 1 - sl.side;
+    const T un = tr[(int64_t)(2 * oth) * npts];
+    const T gn = tr[(int64_t)(2 * oth + 1) * npts];
+    if (!a.transpose) {
+      // rows of the per-point flux: s = W (tau [u] - {du/dn}), t = -W [u] / 2
+      const T jmp = uo - un;
+      const T avg = T(0.5) * (go_ - gn);
+      s = W * (tau * jmp - avg);
+      tt = T(-0.5) * W * jmp;
+    } else {
+      // columns of the same flux (trial and test roles exchanged)
+      s = W * tau * uo - W * tau * un - T(0.5) * W * go_ + T(0.5) * W * gn;
+      tt = T(0.5) * W * un - T(0.5) * W * uo;
+    }
+  }
+  dst[z] = s;
+#pragma unroll
+  for (int m = 0; m < DIM; ++m)
+    if (!orth || m == ax) dst[(1 + m) * fs + z] = fg.c(m) * tt;
+}
+
+// Flux of all 2 DIM faces, projected back to the element's own face points
+// (TraceIProduct), then one pass extruding every face along its normal with
+// l_r(+-1) into U (field s) and G_m (fields c_m t).
+template <typename T, int DIM, int N>
+__device__ __forceinline__ void lift_all_faces(const ApplyArgs<T>& a, const Tile& t, const TileMeta* mt, int rhs,
+                                               const T* tb, T* sm) {
   using S = Shape<DIM, N>;
-  constexpr int Q = S::Q, QV = S::QV, QF1 = S::QF1, FMAX = S::FMAX, FT = S::FT, NFB = S::NFB;
+  constexpr int Q = S::Q, QV = S::QV, QF1 = S::QF1, FMAX = S::FMAX, FT = S::FT, NFACE = S::NFACE;
   constexpr int PER = S::PER_MAIN, NF = 1 + DIM;  // fields: s, c_0 t, .., c_{d-1} t
-  constexpr int FB = NF * (QF1 + FT + FMAX);       // per face: Fq [NF][QF1], Ft [NF][FT], Ff [NF][FMAX]
   const int ne = t.count;
   const int qfm = t.flags & kTileQfMask;
   const bool fine = t.flags & kTileFine;
   const bool orth = t.flags & kTileOrth;  // only s and c_a t are non-zero
   const int npm = DIM == 2 ? qfm : qfm * qfm;
+  // per element: Fq [NFACE][NF][QF1], then scratch Ft [NF][FT], Ff [NF][FMAX]
   T* const F0 = sm + (1 + DIM) * QV;
-  // a. flux at the shared face points (own point order): s and c_m t
-  for (int w = threadIdx.x; w < ne * NFB * npm; w += blockDim.x) {
-    const int el = w / (NFB * npm);
-    const int rem = w - el * NFB * npm;
-    const int fb = rem / npm, zz = rem - fb * npm;
-    const int z0 = zz % qfm, z1 = zz / qfm;
-    const int k = K0 + fb, ax = k >> 1;
-    const FaceSlot sl = mt->slot[el * 2 * DIM + k];
-    const int qf = sl.qf;
-    if (z0 >= qf || z1 >= qf) continue;
-    const int npts = DIM == 2 ? qf : qf * qf;
-    const int z = z0 + qf * z1;
-    const int zc = canon(DIM, sl.side, sl.orient, qf, z0, z1);
-    const T* tr = a.trace + rhs * a.trace_stride + 4 * a.f_troff[sl.face] + zc;
-    const int64_t go = a.f_goff[sl.face];
-    const T W = a.fgeo[go + zc];
-    const T tau = a.f_tau[sl.face];
-    const T uo = tr[(int64_t)(2 * sl.side) * npts];
-    const T go_ = tr[(int64_t)(2 * sl.side + 1) * npts];
-    T s, tt;
-    if (sl.flags & kFaceBnd) {
-      // Nitsche: -(grad v.n, u) - (v, grad u.n) + tau (v, u)
-      if (!a.transpose) { s = W * (tau * uo - go_); tt = -W * uo; }
-      else { s = W * tau * uo - W * go_; tt = -(W * uo); }
-    } else {
-      const int oth = 1 - sl.side;
-      const T un = tr[(int64_t)(2 * oth) * npts];
-      const T gn = tr[(int64_t)(2 * oth + 1) * npts];
-      if (!a.transpose) {
-        // rows of the per-point flux: s = W (tau [u] - {du/dn}), t = -W [u] / 2
-        const T jmp = uo - un;
-        const T avg = T(0.5) * (go_ - gn);
-        s = W * (tau * jmp - avg);
-        tt = T(-0.5) * W * jmp;
+  constexpr int SC = NFACE * NF * QF1;
+  // a. conforming faces, all at once, straight into the face buffers
+  for (int w = threadIdx.x; w < ne * NFACE * QF1; w += blockDim.x) {
+    const int el = w / (NFACE * QF1);
+    const int rem = w - el * NFACE * QF1;
+    const int k = rem / QF1, j = rem - k * QF1;
+    if (mt->slot[el * 2 * DIM + k].qf != Q) continue;
+    face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
+  }
+  // b. faces with a finer shared rule, NSC faces per round in their own scratch
+  //    slots: flux at the shared points, then projection back to the own points
+  if (fine) {
+    constexpr int NSC = scratch_slots(DIM);
+    constexpr int SL = NF * (FT + FMAX);  // one slot: Ft [NF][FT], Ff [NF][FMAX]
+    for (int k0 = 0; k0 < NFACE; k0 += NSC) {
+      for (int w = threadIdx.x; w < ne * NSC * npm; w += blockDim.x) {
+        const int el = w / (NSC * npm), r2 = w - el * NSC * npm;
+        const int kk = r2 / npm, zz = r2 - kk * npm;
+        const int z0 = zz % qfm, z1 = zz / qfm;
+        const int k = k0 + kk;
+        const int qf = mt->slot[el * 2 * DIM + k].qf;
+        if (qf == Q || z0 >= qf || z1 >= qf) continue;
+        face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, z0, z1, F0 + el * PER + SC + kk * SL + NF * FT, FMAX);
+      }
+      __syncthreads();
+      if constexpr (DIM == 2) {
+        for (int w = threadIdx.x; w < ne * NSC * NF * Q; w += blockDim.x) {
+          const int el = w / (NSC * NF * Q);
+          const int rem = w - el * NSC * NF * Q;
+          const int kk = rem / (NF * Q), r2 = rem - kk * NF * Q;
+          const int f = r2 / Q, r = r2 - f * Q;
+          const int k = k0 + kk;
+          const int qf = mt->slot[el * 2 * DIM + k].qf;
+          if (qf == Q || (orth && f != 0 && f != 1 + (k >> 1))) continue;
+          const T* II = tb + TabLayout::II(N, qf);
+          const T* src = F0 + el * PER + SC + kk * SL + NF * FT + f * FMAX;
+          T s = 0;
+          for (int z = 0; z < qf; ++z) s = fma(II[z * Q + r], src[z], s);
+          F0[el * PER + k * NF * QF1 + f * QF1 + r] = s;
+        }
+        __syncthreads();
       } else {
-        // columns of the same flux (trial and test roles exchanged)
-        s = W * tau * uo - W * tau * un - T(0.5) * W * go_ + T(0.5) * W * gn;
-        tt = T(0.5) * W * un - T(0.5) * W * uo;
+        for (int w = threadIdx.x; w < ne * NSC * NF * qfm * Q; w += blockDim.x) {
+          const int el = w / (NSC * NF * qfm * Q);
+          const int rem = w - el * NSC * NF * qfm * Q;
+          const int kk = rem / (NF * qfm * Q), r2 = rem - kk * NF * qfm * Q;
+          const int f = r2 / (qfm * Q), r3 = r2 - f * qfm * Q;
+          const int z1 = r3 / Q, r0 = r3 - z1 * Q;
+          const int k = k0 + kk;
+          const int qf = mt->slot[el * 2 * DIM + k].qf;
+          if (qf == Q || z1 >= qf || (orth && f != 0 && f != 1 + (k >> 1))) continue;
+          const T* II = tb + TabLayout::II(N, qf);
+          const T* src = F0 + el * PER + SC + kk * SL + NF * FT + f * FMAX + qf * z1;
+          T s = 0;
+          for (int z0 = 0; z0 < qf; ++z0) s = fma(II[z0 * Q + r0], src[z0], s);
+          F0[el * PER + SC + kk * SL + f * FT + z1 * Q + r0] = s;
+        }
+        __syncthreads();
+        for (int w = threadIdx.x; w < ne * NSC * NF * QF1; w += blockDim.x) {
+          const int el = w / (NSC * NF * QF1);
+          const int rem = w - el * NSC * NF * QF1;
+          const int kk = rem / (NF * QF1), r2 = rem - kk * NF * QF1;
+          const int f = r2 / QF1, r = r2 - f * QF1;
+          const int r0 = r % Q, r1 = r / Q;
+          const int k = k0 + kk;
+          const int qf = mt->slot[el * 2 * DIM + k].qf;
+          if (qf == Q || (orth && f != 0 && f != 1 + (k >> 1))) continue;
+          const T* II = tb + TabLayout::II(N, qf);
+          const T* src = F0 + el * PER + SC + kk * SL + f * FT + r0;
+          T s = 0;
+          for (int z1 = 0; z1 < qf; ++z1) s = fma(II[z1 * Q + r1], src[z1 * Q], s);
+          F0[el * PER + k * NF * QF1 + f * QF1 + r] = s;
+        }
+        __syncthreads();
       }
     }
-    const bool ffine = qf != Q;
-    T* fq = F0 + el * PER + fb * FB;
-    T* dst = ffine ? fq + NF * (QF1 + FT) : fq;
-    const int fs = ffine ? FMAX : QF1;
-    dst[z] = s;
-    const T* c = a.fgeo + go + (int64_t)(1 + sl.side * DIM) * npts + zc;
-#pragma unroll
-    for (int m = 0; m < DIM; ++m)
-      if (!orth || m == ax) dst[(1 + m) * fs + z] = c[(int64_t)m * npts] * tt;
   }
   __syncthreads();
-  // b. projection from the shared rule back to the element's own Gauss points
-  if (fine) {
-    if constexpr (DIM == 2) {
-      for (int w = threadIdx.x; w < ne * NFB * NF * Q; w += blockDim.x) {
-        const int el = w / (NFB * NF * Q);
-        const int rem = w - el * NFB * NF * Q;
-        const int fb = rem / (NF * Q), r2 = rem - fb * NF * Q;
-        const int f = r2 / Q, r = r2 - f * Q;
-        const int qf = mt->slot[el * 2 * DIM + K0 + fb].qf;
-        if (qf == Q || (orth && f != 0 && f != 1 + ((K0 + fb) >> 1))) continue;
-        const T* II = tb + TabLayout::II(N, qf);
-        T* fq = F0 + el * PER + fb * FB;
-        const T* src = fq + NF * (QF1 + FT) + f * FMAX;
-        T s = 0;
-        for (int z = 0; z < qf; ++z) s = fma(II[z * Q + r], src[z], s);
-        fq[f * QF1 + r] = s;
-      }
-      __syncthreads();
-    } else {
-      for (int w = threadIdx.x; w < ne * NFB * NF * qfm * Q; w += blockDim.x) {
-        const int el = w / (NFB * NF * qfm * Q);
-        const int rem = w - el * NFB * NF * qfm * Q;
-        const int fb = rem / (NF * qfm * Q), r2 = rem - fb * NF * qfm * Q;
-        const int f = r2 / (qfm * Q), r3 = r2 - f * qfm * Q;
-        const int z1 = r3 / Q, r0 = r3 - z1 * Q;
-        const int qf = mt->slot[el * 2 * DIM + K0 + fb].qf;
-        if (qf == Q || z1 >= qf || (orth && f != 0 && f != 1 + ((K0 + fb) >> 1))) continue;
-        const T* II = tb + TabLayout::II(N, qf);
-        T* fq = F0 + el * PER + fb * FB;
-        const T* src = fq + NF * (QF1 + FT) + f * FMAX + qf * z1;
-        T s = 0;
-        for (int z0 = 0; z0 < qf; ++z0) s = fma(II[z0 * Q + r0], src[z0], s);
-        fq[NF * QF1 + f * FT + z1 * Q + r0] = s;
-      }
-      __syncthreads();
-      for (int w = threadIdx.x; w < ne * NFB * NF * QF1; w += blockDim.x) {
-        const int el = w / (NFB * NF * QF1);
-        const int rem = w - el * NFB * NF * QF1;
-        const int fb = rem / (NF * QF1), r2 = rem - fb * NF * QF1;
-        const int f = r2 / QF1, r = r2 - f * QF1;
-        const int r0 = r % Q, r1 = r / Q;
-        const int qf = mt->slot[el * 2 * DIM + K0 + fb].qf;
-        if (qf == Q || (orth && f != 0 && f != 1 + ((K0 + fb) >> 1))) continue;
-        const T* II = tb + TabLayout::II(N, qf);
-        T* fq = F0 + el * PER + fb * FB;
-        const T* src = fq + NF * QF1 + f * FT + r0;
-        T s = 0;
-        for (int z1 = 0; z1 < qf; ++z1) s = fma(II[z1 * Q + r1], src[z1 * Q], s);
-        fq[f * QF1 + r] = s;
-      }
-      __syncthreads();
-    }
-  }
-  // c. extrude along the normal with l_r(+-1) into U (field s) and G_m (fields c_m t)
+  // c. one extrusion pass over the Gauss points for all faces
   const T* LL = tb + TabLayout::LL(N);
   for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
     const int el = w / QV, q = w - el * QV;
+    const int qc[3] = {q % Q, (q / Q) % Q, DIM == 3 ? q / (Q * Q) : 0};
     T* base = sm + el * PER;
+    const T* fel = F0 + el * PER;
     T acc[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) acc[f] = base[f * QV + q];
 #pragma unroll
-    for (int fb = 0; fb < NFB; ++fb) {
-      const int k = K0 + fb, ax = k >> 1, sd = k & 1;
-      int t0, t1;
-      tang_axes<DIM>(ax, t0, t1);
-      const int qa = (q / qpow<Q>(ax)) % Q;
-      const int j = (q / qpow<Q>(t0)) % Q + (DIM == 3 ? Q * ((q / qpow<Q>(t1)) % Q) : 0);
-      const T l = LL[sd * Q + qa];
-      const T* fq = F0 + el * PER + fb * FB;
-      acc[0] = fma(l, fq[j], acc[0]);
+    for (int ax = 0; ax < DIM; ++ax) {
+      // tangential index of q on the faces normal to ax
+      const int j = DIM == 2 ? qc[1 - ax] : (ax == 0 ? qc[1] + Q * qc[2] : (ax == 1 ? qc[0] + Q * qc[2] : qc[0] + Q * qc[1]));
 #pragma unroll
-      for (int m = 0; m < DIM; ++m)
-        if (!orth || m == ax) acc[1 + m] = fma(l, fq[(1 + m) * QF1 + j], acc[1 + m]);
+      for (int sd = 0; sd < 2; ++sd) {
+        const T l = LL[sd * Q + qc[ax]];
+        const T* fq = fel + (2 * ax + sd) * NF * QF1 + j;
+        acc[0] = fma(l, fq[0], acc[0]);
+#pragma unroll
+        for (int m = 0; m < DIM; ++m)
+          if (!orth || m == ax) acc[1 + m] = fma(l, fq[(1 + m) * QF1], acc[1 + m]);
+      }
     }
 #pragma unroll
     for (int f = 0; f < NF; ++f) base[f * QV + q] = acc[f];
@@ -502,7 +557,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   T* G0 = sm + QV;
   T* G1 = sm + 2 * QV;
   T* G2 = sm + 3 * QV;
-  load_meta<DIM>(a.elist, a.slots, t, mt);
+  load_meta<DIM>(a.elist, a.slots, a.eaff, t, mt);
   load_tables<T, N>(tb);
   if (a.ug) {
     for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
@@ -559,19 +614,28 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
     const int el = w / QV, q = w - el * QV;
     const int e = mt->eid[el];
-    const T* geo = a.vgeo + a.vgoff[e] + q;
+    // deformed element: factors per point; affine element: constants times the weight
+    const bool eaf = mt->aff[el] != 0;
+    const T* geo = a.vgeo + a.vgoff[e] + (eaf ? 0 : q);
+    const int gs = eaf ? 1 : QV;
+    T wq = T(1);
+    if (eaf) {
+      const T* gw = tb + TabLayout::GW(N, Q);
+      wq = gw[q % Q] * gw[(q / Q) % Q];
+      if constexpr (DIM == 3) wq *= gw[q / (Q * Q)];
+    }
     const T kap = a.kappa ? a.kappa[a.quad_off[e] + q] : T(1);
     T* b = sm + el * PER;
     if constexpr (DIM == 2) {
       const T g0 = b[QV + q], g1 = b[2 * QV + q];
-      const T a00 = geo[0], a01 = geo[QV], a11 = geo[2 * QV], wj = geo[3 * QV];
+      const T a00 = wq * geo[0], a01 = wq * geo[gs], a11 = wq * geo[2 * gs], wj = wq * geo[3 * gs];
       b[QV + q] = kap * (a00 * g0 + a01 * g1);
       b[2 * QV + q] = kap * (a01 * g0 + a11 * g1);
       b[q] = a.lambda * wj * b[q];
     } else {
       const T g0 = b[QV + q], g1 = b[2 * QV + q], g2 = b[3 * QV + q];
-      const T a00 = geo[0], a01 = geo[QV], a02 = geo[2 * QV], a11 = geo[3 * QV], a12 = geo[4 * QV],
-              a22 = geo[5 * QV], wj = geo[6 * QV];
+      const T a00 = wq * geo[0], a01 = wq * geo[gs], a02 = wq * geo[2 * gs], a11 = wq * geo[3 * gs],
+              a12 = wq * geo[4 * gs], a22 = wq * geo[5 * gs], wj = wq * geo[6 * gs];
       b[QV + q] = kap * (a00 * g0 + a01 * g1 + a02 * g2);
       b[2 * QV + q] = kap * (a01 * g0 + a11 * g1 + a12 * g2);
       b[3 * QV + q] = kap * (a02 * g0 + a12 * g1 + a22 * g2);
@@ -580,16 +644,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   }
   __syncthreads();
   // faces: flux, projection, extrusion into U and G
-  if constexpr (DIM == 2) {
-    lift_faces<T, DIM, N, 0>(a, t, mt, rhs, tb, sm);
-  } else {
-    lift_faces<T, DIM, N, 0>(a, t, mt, rhs, tb, sm);
-    lift_faces<T, DIM, N, 1>(a, t, mt, rhs, tb, sm);
-    lift_faces<T, DIM, N, 2>(a, t, mt, rhs, tb, sm);
-    lift_faces<T, DIM, N, 3>(a, t, mt, rhs, tb, sm);
-    lift_faces<T, DIM, N, 4>(a, t, mt, rhs, tb, sm);
-    lift_faces<T, DIM, N, 5>(a, t, mt, rhs, tb, sm);
-  }
+  lift_all_faces<T, DIM, N>(a, t, mt, rhs, tb, sm);
   // U += sum_m D_m^T G_m
   if constexpr (line_mode<T, DIM>()) {
     contract<T, Q, Q, Q, 0, Q, tab_D(Q), true, true>(G0, U, PER, ne);

@@ -7,10 +7,15 @@
 
 #define SIP_DEFINE_APPLY_TU(SUFFIX, TYPE, DIM)                                                     \
   namespace sip {                                                                                 \
-  cudaError_t upload_tables_##SUFFIX(const double* tab_d, const float* tab_f, const int* ioff) {   \
+  cudaError_t upload_tables_##SUFFIX(const double* tab_d, const float* tab_f, const int* ioff,     \
+                                     const double* gw_d, const float* gw_f) {                     \
     cudaError_t e = cudaMemcpyToSymbol(c_tab_d, tab_d, sizeof(double) * kTabSize);                 \
     if (e != cudaSuccess) return e;                                                               \
     e = cudaMemcpyToSymbol(c_tab_f, tab_f, sizeof(float) * kTabSize);                             \
+    if (e != cudaSuccess) return e;                                                               \
+    e = cudaMemcpyToSymbol(c_gw_d, gw_d, sizeof(double) * (kQMax + 1) * kQMax);                   \
+    if (e != cudaSuccess) return e;                                                               \
+    e = cudaMemcpyToSymbol(c_gw_f, gw_f, sizeof(float) * (kQMax + 1) * kQMax);                    \
     if (e != cudaSuccess) return e;                                                               \
     return cudaMemcpyToSymbol(c_ioff, ioff, sizeof(int) * (kQMax + 1) * (kQMax + 1));             \
   }                                                                                               \

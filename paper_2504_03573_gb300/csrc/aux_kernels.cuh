@@ -14,6 +14,7 @@ struct AuxArgs {
   const double* vgeo;
   const int32_t* elist;
   const Tile* tiles;
+  const int8_t* eaff;
   const double* a;
   const double* b;
   double* out;
@@ -58,6 +59,18 @@ __device__ __forceinline__ void gauss_grad(const double* U, double* G0, double* 
   __syncthreads();
 }
 
+// volume factor comp (0..nG-1) of element e at Gauss point q (affine elements
+// store constants without the Gauss weight)
+template <int DIM, int Q>
+__device__ __forceinline__ double vfac(const AuxArgs& a, int e, int q, int comp) {
+  constexpr int QV = ipow(Q, DIM);
+  const double* g = a.vgeo + a.vgoff[e];
+  if (!a.eaff[e]) return g[comp * QV + q];
+  double w = c_gw_d[Q][q % Q] * c_gw_d[Q][(q / Q) % Q];
+  if (DIM == 3) w *= c_gw_d[Q][q / (Q * Q)];
+  return w * g[comp];
+}
+
 template <int DIM, int N>
 __device__ void aux_tile(const AuxArgs& a, const Tile& t, double* sm) {
   constexpr int Q = N + 1, QV = ipow(Q, DIM), NV = ipow(N, DIM);
@@ -75,16 +88,18 @@ __device__ void aux_tile(const AuxArgs& a, const Tile& t, double* sm) {
     for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
       const int el = w / QV, q = w - el * QV;
       const int e = a.elist[t.start + el];
-      const double* g = a.vgeo + a.vgoff[e] + q;
       const double* ga = Ga + el * PER + q;
       const double* gb = Gb + el * PER + q;
       double v;
       if constexpr (DIM == 2) {
-        v = g[0] * ga[0] * gb[0] + g[QV] * (ga[0] * gb[QV] + ga[QV] * gb[0]) + g[2 * QV] * ga[QV] * gb[QV];
+        v = vfac<DIM, Q>(a, e, q, 0) * ga[0] * gb[0] + vfac<DIM, Q>(a, e, q, 1) * (ga[0] * gb[QV] + ga[QV] * gb[0]) +
+            vfac<DIM, Q>(a, e, q, 2) * ga[QV] * gb[QV];
       } else {
-        v = g[0] * ga[0] * gb[0] + g[3 * QV] * ga[QV] * gb[QV] + g[5 * QV] * ga[2 * QV] * gb[2 * QV] +
-            g[QV] * (ga[0] * gb[QV] + ga[QV] * gb[0]) + g[2 * QV] * (ga[0] * gb[2 * QV] + ga[2 * QV] * gb[0]) +
-            g[4 * QV] * (ga[QV] * gb[2 * QV] + ga[2 * QV] * gb[QV]);
+        v = vfac<DIM, Q>(a, e, q, 0) * ga[0] * gb[0] + vfac<DIM, Q>(a, e, q, 3) * ga[QV] * gb[QV] +
+            vfac<DIM, Q>(a, e, q, 5) * ga[2 * QV] * gb[2 * QV] +
+            vfac<DIM, Q>(a, e, q, 1) * (ga[0] * gb[QV] + ga[QV] * gb[0]) +
+            vfac<DIM, Q>(a, e, q, 2) * (ga[0] * gb[2 * QV] + ga[2 * QV] * gb[0]) +
+            vfac<DIM, Q>(a, e, q, 4) * (ga[QV] * gb[2 * QV] + ga[2 * QV] * gb[QV]);
       }
       double* o = a.out + a.quad_off[e] + q;
       *o = a.accumulate ? *o + v : v;
@@ -97,7 +112,7 @@ __device__ void aux_tile(const AuxArgs& a, const Tile& t, double* sm) {
     for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
       const int el = w / QV, q = w - el * QV;
       const int e = a.elist[t.start + el];
-      s += a.vgeo[a.vgoff[e] + WJ * QV + q] * Ua[el * PER + q] * Ub[el * PER + q];
+      s += vfac<DIM, Q>(a, e, q, WJ) * Ua[el * PER + q] * Ub[el * PER + q];
     }
     // fixed-order block reduction (deterministic)
     __syncthreads();
@@ -114,7 +129,7 @@ __device__ void aux_tile(const AuxArgs& a, const Tile& t, double* sm) {
     for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
       const int el = w / QV, q = w - el * QV;
       const int e = a.elist[t.start + el];
-      Ua[el * PER + q] = a.vgeo[a.vgoff[e] + WJ * QV + q] * a.a[a.quad_off[e] + q];
+      Ua[el * PER + q] = vfac<DIM, Q>(a, e, q, WJ) * a.a[a.quad_off[e] + q];
     }
     __syncthreads();
     double* t1 = Ga;

@@ -41,10 +41,10 @@ int apply_epb(int dim, int n, int precision) {
   return std::max(1, std::min(std::min(epb, room), kMaxEpb));
 }
 
-cudaError_t upload_tables_2d_f64(const double*, const float*, const int*);
-cudaError_t upload_tables_2d_f32(const double*, const float*, const int*);
-cudaError_t upload_tables_3d_f64(const double*, const float*, const int*);
-cudaError_t upload_tables_3d_f32(const double*, const float*, const int*);
+cudaError_t upload_tables_2d_f64(const double*, const float*, const int*, const double*, const float*);
+cudaError_t upload_tables_2d_f32(const double*, const float*, const int*, const double*, const float*);
+cudaError_t upload_tables_3d_f64(const double*, const float*, const int*, const double*, const float*);
+cudaError_t upload_tables_3d_f32(const double*, const float*, const int*, const double*, const float*);
 cudaError_t prepare_2d_f64();
 cudaError_t prepare_2d_f32();
 cudaError_t prepare_3d_f64();
@@ -85,11 +85,18 @@ int ensure_tables(int dev) {
   int ioff[kQMax + 1][kQMax + 1];
   for (int q = 0; q <= kQMax; ++q)
     for (int f = 0; f <= kQMax; ++f) ioff[q][f] = (q >= kQMin && f > q) ? tab_I(q, f) : 0;
+  double gwd[kQMax + 1][kQMax] = {};
+  float gwf[kQMax + 1][kQMax] = {};
+  for (int q = 1; q <= kQMax; ++q) {
+    std::vector<double> gx, gw;
+    gauss_legendre(q, gx, gw);
+    for (int z = 0; z < q; ++z) { gwd[q][z] = gw[z]; gwf[q][z] = (float)gw[z]; }
+  }
   cudaError_t e;
-  if ((e = upload_tables_2d_f64(tab.data(), tabf.data(), &ioff[0][0])) != cudaSuccess) return cuda_fail(e, "tables");
-  if ((e = upload_tables_2d_f32(tab.data(), tabf.data(), &ioff[0][0])) != cudaSuccess) return cuda_fail(e, "tables");
-  if ((e = upload_tables_3d_f64(tab.data(), tabf.data(), &ioff[0][0])) != cudaSuccess) return cuda_fail(e, "tables");
-  if ((e = upload_tables_3d_f32(tab.data(), tabf.data(), &ioff[0][0])) != cudaSuccess) return cuda_fail(e, "tables");
+  if ((e = upload_tables_2d_f64(tab.data(), tabf.data(), &ioff[0][0], &gwd[0][0], &gwf[0][0])) != cudaSuccess) return cuda_fail(e, "tables");
+  if ((e = upload_tables_2d_f32(tab.data(), tabf.data(), &ioff[0][0], &gwd[0][0], &gwf[0][0])) != cudaSuccess) return cuda_fail(e, "tables");
+  if ((e = upload_tables_3d_f64(tab.data(), tabf.data(), &ioff[0][0], &gwd[0][0], &gwf[0][0])) != cudaSuccess) return cuda_fail(e, "tables");
+  if ((e = upload_tables_3d_f32(tab.data(), tabf.data(), &ioff[0][0], &gwd[0][0], &gwf[0][0])) != cudaSuccess) return cuda_fail(e, "tables");
   // dynamic shared-memory limits, set once per device (never during a stream capture)
   for (auto fn : {prepare_2d_f64, prepare_2d_f32, prepare_3d_f64, prepare_3d_f32, prepare_aux_2d, prepare_aux_3d})
     if ((e = fn()) != cudaSuccess) return cuda_fail(e, "kernel attributes");
@@ -180,6 +187,7 @@ ApplyArgs<T> make_args(sip_handle* h, const T* x, T* y, T* trace, T* ug, int tra
   a.f_tau = g.tau;
   a.fgeo = g.fgeo;
   a.elist = h->elist;
+  a.eaff = h->eaff;
   a.tiles = h->tiles_d[std::is_same<T, float>::value ? 1 : 0];
   a.x = x;
   a.y = y;
@@ -343,6 +351,7 @@ int sip_create(const sip_mesh* mesh, const int32_t* orders, double lambda, const
   UP(h->f_goff, p.f_goff);
   UP(h->slots, p.slots);
   UP(h->elist, p.elist);
+  UP(h->eaff, p.affine);
   UP(h->gd.vgeo, p.vgeo);
   UP(h->gd.fgeo, p.fgeo);
   UP(h->gd.tau, p.f_tau);

@@ -24,6 +24,7 @@ struct ApplyArgs {
   const T* fgeo;
   const int32_t* elist;
   const Tile* tiles;
+  const int8_t* eaff;      // per element: 1 if its volume geometry is stored as constants
   const T* x;
   T* y;
   T* trace;
@@ -42,6 +43,14 @@ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 static __constant__ double c_tab_d[kTabSize];
 static __constant__ float c_tab_f[kTabSize];
 static __constant__ int c_ioff[kQMax + 1][kQMax + 1];
+static __constant__ double c_gw_d[kQMax + 1][kQMax];  // Gauss weights of the q-point rule
+static __constant__ float c_gw_f[kQMax + 1][kQMax];
+
+template <typename T>
+__device__ __forceinline__ T cgw(int q, int z) {
+  if constexpr (std::is_same<T, double>::value) return c_gw_d[q][z];
+  else return c_gw_f[q][z];
+}
 
 template <typename T>
 __device__ __forceinline__ T ctab(int i) {

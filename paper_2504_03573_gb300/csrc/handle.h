@@ -54,6 +54,7 @@ struct sip_handle {
   int64_t* f_goff = nullptr;
   sip::FaceSlot* slots = nullptr;
   int32_t* elist = nullptr;
+  int8_t* eaff = nullptr;
   sip::Tile* tiles_d[2] = {nullptr, nullptr};   // per precision (FP64, FP32)
   std::vector<sip::Tile> tiles_h[2];
   int epb[2][sip::kNMax + 2] = {};                // elements per tile per order in use (0: default)

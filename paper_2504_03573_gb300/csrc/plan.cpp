@@ -412,6 +412,57 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
       for (int z = 0; z < npts; ++z) fg[z] = 0.0;
   }
 
+  // ---- regular (affine) elements and faces keep constants only (Sec. 5.1: regular
+  // vs deformed elements): the kernels multiply by the Gauss weights themselves
+  {
+    std::vector<double> wv, wq;
+    std::vector<int64_t> vnew(E + 1, 0);
+    for (int64_t e = 0; e < E; ++e)
+      vnew[e + 1] = vnew[e] + (p.affine[e] ? nG : p.vgoff[e + 1] - p.vgoff[e]);
+    std::vector<double> vg(vnew[E]);
+    for (int64_t e = 0; e < E; ++e) {
+      const int64_t nq = p.quad_off[e + 1] - p.quad_off[e];
+      const double* src = &p.vgeo[p.vgoff[e]];
+      if (p.affine[e]) {
+        gauss_legendre(p.P[e] + 2, wv, wq);
+        double w0 = 1.0;
+        for (int k = 0; k < dim; ++k) w0 *= wq[0];
+        for (int c = 0; c < nG; ++c) vg[vnew[e] + c] = src[c * nq] / w0;
+      } else {
+        std::copy(src, src + nG * nq, vg.begin() + vnew[e]);
+      }
+    }
+    p.vgeo.swap(vg);
+    p.vgoff.swap(vnew);
+    std::vector<int64_t> fnew(F + 1, 0);
+    std::vector<char> faff(F, 0);
+    for (int64_t f = 0; f < F; ++f) {
+      const bool aff = p.affine[p.f_em[f]] && (p.f_ep[f] < 0 || p.affine[p.f_ep[f]]);
+      faff[f] = aff;
+      const int ncomp = p.f_ep[f] >= 0 ? 1 + 2 * dim : 1 + dim;
+      fnew[f + 1] = fnew[f] + (aff ? ncomp : p.f_goff[f + 1] - p.f_goff[f]);
+    }
+    std::vector<double> fgn(fnew[F]);
+    for (int64_t f = 0; f < F; ++f) {
+      const double* src = &p.fgeo[p.f_goff[f]];
+      const int qf = p.f_qf[f];
+      const int npts = dim == 2 ? qf : qf * qf;
+      const int ncomp = p.f_ep[f] >= 0 ? 1 + 2 * dim : 1 + dim;
+      if (faff[f]) {
+        gauss_legendre(qf, wv, wq);
+        const double wz = dim == 2 ? wq[0] : wq[0] * wq[0];
+        fgn[fnew[f]] = src[0] / wz;
+        for (int c = 1; c < ncomp; ++c) fgn[fnew[f] + c] = src[c * npts];
+        p.slots[(size_t)p.f_em[f] * 2 * dim + p.f_km[f]].flags |= kFaceAffine;
+        if (p.f_ep[f] >= 0) p.slots[(size_t)p.f_ep[f] * 2 * dim + p.f_kp[f]].flags |= kFaceAffine;
+      } else {
+        std::copy(src, src + ncomp * npts, fgn.begin() + fnew[f]);
+      }
+    }
+    p.fgeo.swap(fgn);
+    p.f_goff.swap(fnew);
+  }
+
   // ---- elements sorted by order (the paper's element groups)
   p.elist.resize(E);
   std::iota(p.elist.begin(), p.elist.end(), 0);

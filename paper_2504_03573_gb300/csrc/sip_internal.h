@@ -65,6 +65,7 @@ constexpr int kTabSize = tab_I(kQMax + 1, kQMax + 2);
 //   DD [Q][Q]  D[q][r] at q*Q + r      transposed derivative
 //   LL [4][Q]  l(-1), l(+1), l'(-1), l'(+1)
 //   for F = Q+1 .. kQMax:  IT_F [Q][F] (I[z][r] at r*F + z), II_F [F][Q] (I[z][r] at z*Q + r)
+//   for F = Q .. kQMax:    GW_F [F] Gauss weights
 // ---------------------------------------------------------------------------
 struct TabLayout {
   static constexpr int BT(int) { return 0; }
@@ -78,18 +79,26 @@ struct TabLayout {
     return o;
   }
   static constexpr int II(int n, int f) { return IT(n, f) + f * (n + 1); }
-  static constexpr int size(int n) { return IT(n, kQMax + 1); }
+  // Gauss weights of the F-point rules, F = Q .. kQMax (affine geometry)
+  static constexpr int GW(int n, int f) {
+    int o = IT(n, kQMax + 1);
+    for (int g = n + 1; g < f; ++g) o += g;
+    return o;
+  }
+  static constexpr int size(int n) { return GW(n, kQMax + 1); }
 };
 
 constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * cpow(b, e - 1); }
 
-// faces processed together in one pass: all four in 2D, one at a time in 3D
-constexpr int faces_per_batch(int dim) { return dim == 2 ? 4 : 1; }
-
-// per-element shared memory (in elements of T) of the trace and main kernels
+// per-element shared memory (in elements of T) of the trace and main kernels:
+// face values of all 2*dim faces at the element's own face points
+// [2 dim][fields][Q^(dim-1)], plus scratch for faces with a finer shared rule,
+// [slots][fields][FT + kQMax^(dim-1)] (FT = kQMax Q in 3D, 0 in 2D): one slot per
+// face in 2D (all processed together), one slot in 3D (one face at a time)
+constexpr int scratch_slots(int dim) { return dim == 2 ? 4 : 1; }
 constexpr int face_buf(int dim, int n, int fields) {
-  return faces_per_batch(dim) * fields *
-         (cpow(n + 1, dim - 1) + (dim == 3 ? kQMax * (n + 1) : 0) + cpow(kQMax, dim - 1));
+  return 2 * dim * fields * cpow(n + 1, dim - 1) +
+         scratch_slots(dim) * fields * ((dim == 3 ? kQMax * (n + 1) : 0) + cpow(kQMax, dim - 1));
 }
 constexpr int per_elem_trace(int dim, int n) { return 2 * cpow(n + 1, dim) + face_buf(dim, n, 4); }
 constexpr int per_elem_main(int dim, int n) { return (1 + dim) * cpow(n + 1, dim) + face_buf(dim, n, 1 + dim); }
@@ -99,8 +108,9 @@ constexpr int table_block_bytes(int bytes_per, int n) { return ((TabLayout::size
 // ---------------------------------------------------------------------------
 // Per element local face slot (2*dim per element; local face k = 2*axis + side).
 // ---------------------------------------------------------------------------
-constexpr int kFaceBnd = 1;   // boundary face
-constexpr int kFaceOrth = 2;  // c = J^-1 n has no tangential component on either side
+constexpr int kFaceBnd = 1;     // boundary face
+constexpr int kFaceOrth = 2;    // c = J^-1 n has no tangential component on either side
+constexpr int kFaceAffine = 4;  // both sides affine: geometry stored as constants (W without the weight)
 
 struct FaceSlot {
   int32_t face;    // face id
@@ -122,8 +132,8 @@ struct Tile {
   int32_t flags;   // kTileQfMask | kTileFine | kTileOrth
 };
 
-// per-tile copy of element ids and face slots, after the table block
-constexpr int kMetaBytes = ((kMaxEpb * (4 + 6 * (int)sizeof(FaceSlot)) + 15) / 16) * 16;
+// per-tile copy of element ids, face slots and affine flags, after the table block
+constexpr int kMetaBytes = ((kMaxEpb * (4 + 6 * (int)sizeof(FaceSlot) + 1) + 15) / 16) * 16;
 
 // Host plan: everything the device needs, in FP64.
 struct Plan {
@@ -134,7 +144,8 @@ struct Plan {
   std::vector<int64_t> dof_off, quad_off;
   std::vector<int8_t> affine;
   // volume geometry: per element nG comps x Q^dim points, comp-major:
-  // 2D: G00 G01 G11 wJ, 3D: G00 G01 G02 G11 G12 G22 wJ with G = w|J| J^-1 J^-T
+  // 2D: G00 G01 G11 wJ, 3D: G00 G01 G02 G11 G12 G22 wJ with G = w|J| J^-1 J^-T;
+  // affine elements store the nG constants without the weight w (|J| J^-1 J^-T, |J|)
   std::vector<int64_t> vgoff;
   std::vector<double> vgeo;
   std::vector<double> xq;       // physical Gauss points [nquad][dim]
@@ -147,7 +158,8 @@ struct Plan {
   std::vector<double> f_tau;
   // face geometry, canonical point order (minus side's parametrisation):
   // interior: W, c-_0..c-_{d-1}, c+_0..c+_{d-1}; boundary: W, c_0..c_{d-1}
-  // each comp holds npts = qf^(dim-1) values; c = J^-1 n of that side
+  // each comp holds npts = qf^(dim-1) values; c = J^-1 n of that side;
+  // affine faces (kFaceAffine) store one value per comp, W without the weight w_z
   std::vector<double> fgeo;
   int64_t trace_points = 0;
   std::vector<FaceSlot> slots;   // [E][2 dim]

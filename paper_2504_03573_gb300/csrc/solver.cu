@@ -207,7 +207,7 @@ void sip_handle::release() {
   ck_x.clear(); ck_r.clear(); ck_p.clear();
   if (solve_stream) cudaStreamDestroy(solve_stream);
   cudaFree(dof_off); cudaFree(quad_off); cudaFree(vgoff); cudaFree(f_troff); cudaFree(f_goff);
-  cudaFree(slots); cudaFree(elist); cudaFree(tiles_d[0]); cudaFree(tiles_d[1]); cudaFree(xq);
+  cudaFree(slots); cudaFree(elist); cudaFree(eaff); cudaFree(tiles_d[0]); cudaFree(tiles_d[1]); cudaFree(xq);
   cudaFree(gd.vgeo); cudaFree(gd.fgeo); cudaFree(gd.tau); cudaFree(gd.kappa);
   cudaFree(gf.vgeo); cudaFree(gf.fgeo); cudaFree(gf.tau); cudaFree(gf.kappa);
   cudaFree(trace_d);
@@ -664,6 +664,7 @@ int launch_aux(sip_handle* h, AuxArgs& a, cudaStream_t s) {
   a.vgoff = h->vgoff;
   a.vgeo = h->gd.vgeo;
   a.elist = h->elist;
+  a.eaff = h->eaff;
   a.tiles = h->tiles_d[0];
   const int nt = (int)h->tiles_h[0].size();
   cudaError_t e = h->plan.dim == 2 ? launch_aux_2d(a, nt, aux_smem(h), s) : launch_aux_3d(a, nt, aux_smem(h), s);
