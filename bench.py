@@ -41,6 +41,10 @@ METRIC = "SIP apply GDoF/s (FP64 vs FP32-refined) and CG time to 1e-10 residual"
 FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
+# DRAM bytes (read + write) per launch of the FP64 main kernel, from one ncu capture
+# of that workload with the current kernels (profiles/apply_<workload>.md)
+NCU_MAIN_TRAFFIC = {"c2_2d_64x64_jitter_p2to6": 10.892544e6, "c3_3d_32cube_p4": 183.451392e6 + 23.756288e6}
+
 
 def peaks():
     p = {"hbm_gbs": 6800.0, "src": "fallback"}
@@ -247,7 +251,7 @@ def run_gb300(args):
     pk = peaks()
     ach = w64["flops_main"] / (main_ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": f"k_main<double,{mesh.dim}>",
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": NCU_MAIN_TRAFFIC.get(args.workload), "kernel": f"k_main<double,{mesh.dim}>",
             "peak_src": "FP64 vendor figure 1.25 TFLOP/s (dense)",
             "kernel_ms": main_ms, "trace_kernel_ms": trace_ms,
             "hbm_frac": (w64["bytes_x"] + w64["bytes_y"] + w64["bytes_geometry"] + w64["bytes_trace"])
