@@ -423,140 +423,100 @@ __device__ __forceinline__ void face_flux(const ApplyArgs<T>& a, const TileMeta*
     if (!orth || m == ax) dst[(1 + m) * fs + z] = fg.c(m) * tt;
 }
 
-// Flux of all 2 DIM faces, projected back to the element's own face points
-// (TraceIProduct), then one pass extruding every face along its normal with
-// l_r(+-1) into U (field s) and G_m (fields c_m t).
+// Flux of faces with a finer shared rule (p-non-conforming), SC slots per
+// round: flux at the shared points, then projection back to the element's own
+// face points (TraceIProduct) into the per-face buffers.
 template <typename T, int DIM, int N>
-__device__ __forceinline__ void lift_all_faces(const ApplyArgs<T>& a, const Tile& t, const TileMeta* mt, int rhs,
-                                               const T* tb, T* sm) {
+__device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Tile& t, const TileMeta* mt, int rhs,
+                                                const T* tb, T* F0, int per, bool orth) {
   using S = Shape<DIM, N>;
-  constexpr int Q = S::Q, QV = S::QV, QF1 = S::QF1, FMAX = S::FMAX, FT = S::FT, NFACE = S::NFACE;
-  constexpr int PER = S::PER_MAIN, NF = 1 + DIM;  // fields: s, c_0 t, .., c_{d-1} t
+  constexpr int Q = S::Q, QF1 = S::QF1, FMAX = S::FMAX, FT = S::FT, NFACE = S::NFACE, NF = 1 + DIM;
+  constexpr int SC = NFACE * NF * QF1;
+  constexpr int NSC = scratch_slots(DIM);
+  constexpr int SL = NF * (FT + FMAX);  // one slot: Ft [NF][FT], Ff [NF][FMAX]
   const int ne = t.count;
   const int qfm = t.flags & kTileQfMask;
-  const bool fine = t.flags & kTileFine;
-  const bool orth = t.flags & kTileOrth;  // only s and c_a t are non-zero
   const int npm = DIM == 2 ? qfm : qfm * qfm;
-  // per element: Fq [NFACE][NF][QF1], then scratch Ft [NF][FT], Ff [NF][FMAX]
-  T* const F0 = sm + (1 + DIM) * QV;
-  constexpr int SC = NFACE * NF * QF1;
-  // a. conforming faces, all at once, straight into the face buffers
-  for (int w = threadIdx.x; w < ne * NFACE * QF1; w += blockDim.x) {
-    const int el = w / (NFACE * QF1);
-    const int rem = w - el * NFACE * QF1;
-    const int k = rem / QF1, j = rem - k * QF1;
-    if (mt->slot[el * 2 * DIM + k].qf != Q) continue;
-    face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
-  }
-  // b. faces with a finer shared rule, NSC faces per round in their own scratch
-  //    slots: flux at the shared points, then projection back to the own points
-  if (fine) {
-    constexpr int NSC = scratch_slots(DIM);
-    constexpr int SL = NF * (FT + FMAX);  // one slot: Ft [NF][FT], Ff [NF][FMAX]
-    for (int k0 = 0; k0 < NFACE; k0 += NSC) {
-      for (int w = threadIdx.x; w < ne * NSC * npm; w += blockDim.x) {
-        const int el = w / (NSC * npm), r2 = w - el * NSC * npm;
-        const int kk = r2 / npm, zz = r2 - kk * npm;
-        const int z0 = zz % qfm, z1 = zz / qfm;
+  for (int k0 = 0; k0 < NFACE; k0 += NSC) {
+    for (int w = threadIdx.x; w < ne * NSC * npm; w += blockDim.x) {
+      const int el = w / (NSC * npm), r2 = w - el * NSC * npm;
+      const int kk = r2 / npm, zz = r2 - kk * npm;
+      const int z0 = zz % qfm, z1 = zz / qfm;
+      const int k = k0 + kk;
+      const int qf = mt->slot[el * 2 * DIM + k].qf;
+      if (qf == Q || z0 >= qf || z1 >= qf) continue;
+      face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, z0, z1, F0 + el * per + SC + kk * SL + NF * FT, FMAX);
+    }
+    __syncthreads();
+    if constexpr (DIM == 2) {
+      for (int w = threadIdx.x; w < ne * NSC * NF * Q; w += blockDim.x) {
+        const int el = w / (NSC * NF * Q);
+        const int rem = w - el * NSC * NF * Q;
+        const int kk = rem / (NF * Q), r2 = rem - kk * NF * Q;
+        const int f = r2 / Q, r = r2 - f * Q;
         const int k = k0 + kk;
         const int qf = mt->slot[el * 2 * DIM + k].qf;
-        if (qf == Q || z0 >= qf || z1 >= qf) continue;
-        face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, z0, z1, F0 + el * PER + SC + kk * SL + NF * FT, FMAX);
+        if (qf == Q || (orth && f != 0 && f != 1 + (k >> 1))) continue;
+        const T* II = tb + TabLayout::II(N, qf);
+        const T* src = F0 + el * per + SC + kk * SL + NF * FT + f * FMAX;
+        T s = 0;
+        for (int z = 0; z < qf; ++z) s = fma(II[z * Q + r], src[z], s);
+        F0[el * per + k * NF * QF1 + f * QF1 + r] = s;
       }
       __syncthreads();
-      if constexpr (DIM == 2) {
-        for (int w = threadIdx.x; w < ne * NSC * NF * Q; w += blockDim.x) {
-          const int el = w / (NSC * NF * Q);
-          const int rem = w - el * NSC * NF * Q;
-          const int kk = rem / (NF * Q), r2 = rem - kk * NF * Q;
-          const int f = r2 / Q, r = r2 - f * Q;
-          const int k = k0 + kk;
-          const int qf = mt->slot[el * 2 * DIM + k].qf;
-          if (qf == Q || (orth && f != 0 && f != 1 + (k >> 1))) continue;
-          const T* II = tb + TabLayout::II(N, qf);
-          const T* src = F0 + el * PER + SC + kk * SL + NF * FT + f * FMAX;
-          T s = 0;
-          for (int z = 0; z < qf; ++z) s = fma(II[z * Q + r], src[z], s);
-          F0[el * PER + k * NF * QF1 + f * QF1 + r] = s;
-        }
-        __syncthreads();
-      } else {
-        for (int w = threadIdx.x; w < ne * NSC * NF * qfm * Q; w += blockDim.x) {
-          const int el = w / (NSC * NF * qfm * Q);
-          const int rem = w - el * NSC * NF * qfm * Q;
-          const int kk = rem / (NF * qfm * Q), r2 = rem - kk * NF * qfm * Q;
-          const int f = r2 / (qfm * Q), r3 = r2 - f * qfm * Q;
-          const int z1 = r3 / Q, r0 = r3 - z1 * Q;
-          const int k = k0 + kk;
-          const int qf = mt->slot[el * 2 * DIM + k].qf;
-          if (qf == Q || z1 >= qf || (orth && f != 0 && f != 1 + (k >> 1))) continue;
-          const T* II = tb + TabLayout::II(N, qf);
-          const T* src = F0 + el * PER + SC + kk * SL + NF * FT + f * FMAX + qf * z1;
-          T s = 0;
-          for (int z0 = 0; z0 < qf; ++z0) s = fma(II[z0 * Q + r0], src[z0], s);
-          F0[el * PER + SC + kk * SL + f * FT + z1 * Q + r0] = s;
-        }
-        __syncthreads();
-        for (int w = threadIdx.x; w < ne * NSC * NF * QF1; w += blockDim.x) {
-          const int el = w / (NSC * NF * QF1);
-          const int rem = w - el * NSC * NF * QF1;
-          const int kk = rem / (NF * QF1), r2 = rem - kk * NF * QF1;
-          const int f = r2 / QF1, r = r2 - f * QF1;
-          const int r0 = r % Q, r1 = r / Q;
-          const int k = k0 + kk;
-          const int qf = mt->slot[el * 2 * DIM + k].qf;
-          if (qf == Q || (orth && f != 0 && f != 1 + (k >> 1))) continue;
-          const T* II = tb + TabLayout::II(N, qf);
-          const T* src = F0 + el * PER + SC + kk * SL + f * FT + r0;
-          T s = 0;
-          for (int z1 = 0; z1 < qf; ++z1) s = fma(II[z1 * Q + r1], src[z1 * Q], s);
-          F0[el * PER + k * NF * QF1 + f * QF1 + r] = s;
-        }
-        __syncthreads();
+    } else {
+      for (int w = threadIdx.x; w < ne * NSC * NF * qfm * Q; w += blockDim.x) {
+        const int el = w / (NSC * NF * qfm * Q);
+        const int rem = w - el * NSC * NF * qfm * Q;
+        const int kk = rem / (NF * qfm * Q), r2 = rem - kk * NF * qfm * Q;
+        const int f = r2 / (qfm * Q), r3 = r2 - f * qfm * Q;
+        const int z1 = r3 / Q, r0 = r3 - z1 * Q;
+        const int k = k0 + kk;
+        const int qf = mt->slot[el * 2 * DIM + k].qf;
+        if (qf == Q || z1 >= qf || (orth && f != 0 && f != 1 + (k >> 1))) continue;
+        const T* II = tb + TabLayout::II(N, qf);
+        const T* src = F0 + el * per + SC + kk * SL + NF * FT + f * FMAX + qf * z1;
+        T s = 0;
+        for (int z0 = 0; z0 < qf; ++z0) s = fma(II[z0 * Q + r0], src[z0], s);
+        F0[el * per + SC + kk * SL + f * FT + z1 * Q + r0] = s;
       }
+      __syncthreads();
+      for (int w = threadIdx.x; w < ne * NSC * NF * QF1; w += blockDim.x) {
+        const int el = w / (NSC * NF * QF1);
+        const int rem = w - el * NSC * NF * QF1;
+        const int kk = rem / (NF * QF1), r2 = rem - kk * NF * QF1;
+        const int f = r2 / QF1, r = r2 - f * QF1;
+        const int r0 = r % Q, r1 = r / Q;
+        const int k = k0 + kk;
+        const int qf = mt->slot[el * 2 * DIM + k].qf;
+        if (qf == Q || (orth && f != 0 && f != 1 + (k >> 1))) continue;
+        const T* II = tb + TabLayout::II(N, qf);
+        const T* src = F0 + el * per + SC + kk * SL + f * FT + r0;
+        T s = 0;
+        for (int z1 = 0; z1 < qf; ++z1) s = fma(II[z1 * Q + r1], src[z1 * Q], s);
+        F0[el * per + k * NF * QF1 + f * QF1 + r] = s;
+      }
+      __syncthreads();
     }
   }
-  __syncthreads();
-  // c. one extrusion pass over the Gauss points for all faces
-  const T* LL = tb + TabLayout::LL(N);
-  for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
-    const int el = w / QV, q = w - el * QV;
-    const int qc[3] = {q % Q, (q / Q) % Q, DIM == 3 ? q / (Q * Q) : 0};
-    T* base = sm + el * PER;
-    const T* fel = F0 + el * PER;
-    T acc[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) acc[f] = base[f * QV + q];
-#pragma unroll
-    for (int ax = 0; ax < DIM; ++ax) {
-      // tangential index of q on the faces normal to ax
-      const int j = DIM == 2 ? qc[1 - ax] : (ax == 0 ? qc[1] + Q * qc[2] : (ax == 1 ? qc[0] + Q * qc[2] : qc[0] + Q * qc[1]));
-#pragma unroll
-      for (int sd = 0; sd < 2; ++sd) {
-        const T l = LL[sd * Q + qc[ax]];
-        const T* fq = fel + (2 * ax + sd) * NF * QF1 + j;
-        acc[0] = fma(l, fq[0], acc[0]);
-#pragma unroll
-        for (int m = 0; m < DIM; ++m)
-          if (!orth || m == ax) acc[1 + m] = fma(l, fq[(1 + m) * QF1], acc[1 + m]);
-      }
-    }
-#pragma unroll
-    for (int f = 0; f < NF; ++f) base[f * QV + q] = acc[f];
-  }
-  __syncthreads();
 }
 
 template <typename T, int DIM, int N>
 __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, TileMeta* mt, T* sm) {
   using S = Shape<DIM, N>;
-  constexpr int Q = S::Q, QV = S::QV, NV = S::NV, PER = S::PER_MAIN;
+  constexpr int Q = S::Q, QV = S::QV, NV = S::NV, QF1 = S::QF1, NFACE = S::NFACE, PER = S::PER_MAIN;
+  constexpr int NF = 1 + DIM;
   const int ne = t.count;
-  // per element: U [QV], G_0..G_{DIM-1} [QV each], face buffers
+  const bool fine = t.flags & kTileFine;
+  const bool orth = t.flags & kTileOrth;
+  // per element: U [QV], G_0..G_{DIM-1} [QV each], R [QV], face buffers Fq
+  // [NFACE][NF][QF1] (fields s, c_0 t, .., c_{d-1} t) and scratch
   T* U = sm;
   T* G0 = sm + QV;
   T* G1 = sm + 2 * QV;
   T* G2 = sm + 3 * QV;
+  T* R = sm + (1 + DIM) * QV;
+  T* const F0 = sm + (2 + DIM) * QV;
   load_meta<DIM>(a.elist, a.slots, a.eaff, t, mt);
   load_tables<T, N>(tb);
   if (a.ug) {
@@ -592,60 +552,135 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
     }
     __syncthreads();
   }
-  // reference gradient by collocation
+  if constexpr (line_mode<T, DIM>()) {
+    // reference gradient, one line per thread
+    contract<T, Q, Q, Q, 0, Q, tab_D(Q), false, false>(U, G0, PER, ne);
+    contract<T, Q, Q, Q, 1, Q, tab_D(Q), false, false>(U, G1, PER, ne);
+    contract<T, Q, Q, Q, 2, Q, tab_D(Q), false, false>(U, G2, PER, ne);
+    __syncthreads();
+  }
+  // volume pointwise terms (with the collocation gradient computed in place in
+  // output-per-thread mode) and the flux of the conforming faces, in one pass:
+  //   G_m = kappa (G grad_ref u)_m,  R = lambda w|J| u,  Fq[k] = (s, c_m t)
   {
     const T* DT = tb + TabLayout::DT(N);
-    if constexpr (DIM == 2) {
-      cpt<T, Q, Q, 1, 0, Q, false>(U, G0, PER, ne, DT);
-      cpt<T, Q, Q, 1, 1, Q, false>(U, G1, PER, ne, DT);
-    } else if constexpr (!line_mode<T, DIM>()) {
-      cpt<T, Q, Q, Q, 0, Q, false>(U, G0, PER, ne, DT);
-      cpt<T, Q, Q, Q, 1, Q, false>(U, G1, PER, ne, DT);
-      cpt<T, Q, Q, Q, 2, Q, false>(U, G2, PER, ne, DT);
-    } else {
-      (void)DT;
-      contract<T, Q, Q, Q, 0, Q, tab_D(Q), false, false>(U, G0, PER, ne);
-      contract<T, Q, Q, Q, 1, Q, tab_D(Q), false, false>(U, G1, PER, ne);
-      contract<T, Q, Q, Q, 2, Q, tab_D(Q), false, false>(U, G2, PER, ne);
+    const int nvol = ne * QV;
+    for (int w = threadIdx.x; w < nvol + ne * NFACE * QF1; w += blockDim.x) {
+      if (w >= nvol) {
+        const int v = w - nvol;
+        const int el = v / (NFACE * QF1);
+        const int rem = v - el * NFACE * QF1;
+        const int k = rem / QF1, j = rem - k * QF1;
+        if (mt->slot[el * 2 * DIM + k].qf != Q) continue;
+        face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
+        continue;
+      }
+      const int el = w / QV, q = w - el * QV;
+      const int e = mt->eid[el];
+      T* b = sm + el * PER;
+      T g[DIM];
+      if constexpr (line_mode<T, DIM>()) {
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) g[m] = b[(1 + m) * QV + q];
+      } else {
+        const int qc[3] = {q % Q, (q / Q) % Q, DIM == 3 ? q / (Q * Q) : 0};
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) {
+          const int sm_ = m == 0 ? 1 : (m == 1 ? Q : Q * Q);
+          const T* u = b + q - qc[m] * sm_;
+          T acc = 0;
+#pragma unroll
+          for (int r = 0; r < Q; ++r) acc = fma(DT[r * Q + qc[m]], u[r * sm_], acc);
+          g[m] = acc;
+        }
+      }
+      // deformed element: factors per point; affine element: constants times the weight
+      const bool eaf = mt->aff[el] != 0;
+      const T* geo = a.vgeo + a.vgoff[e] + (eaf ? 0 : q);
+      const int gs = eaf ? 1 : QV;
+      T wq = T(1);
+      if (eaf) {
+        const T* gw = tb + TabLayout::GW(N, Q);
+        wq = gw[q % Q] * gw[(q / Q) % Q];
+        if constexpr (DIM == 3) wq *= gw[q / (Q * Q)];
+      }
+      const T kap = a.kappa ? a.kappa[a.quad_off[e] + q] : T(1);
+      if constexpr (DIM == 2) {
+        const T a00 = wq * geo[0], a01 = wq * geo[gs], a11 = wq * geo[2 * gs], wj = wq * geo[3 * gs];
+        b[QV + q] = kap * (a00 * g[0] + a01 * g[1]);
+        b[2 * QV + q] = kap * (a01 * g[0] + a11 * g[1]);
+        b[(1 + DIM) * QV + q] = a.lambda * wj * b[q];
+      } else {
+        const T a00 = wq * geo[0], a01 = wq * geo[gs], a02 = wq * geo[2 * gs], a11 = wq * geo[3 * gs],
+                a12 = wq * geo[4 * gs], a22 = wq * geo[5 * gs], wj = wq * geo[6 * gs];
+        b[QV + q] = kap * (a00 * g[0] + a01 * g[1] + a02 * g[2]);
+        b[2 * QV + q] = kap * (a01 * g[0] + a11 * g[1] + a12 * g[2]);
+        b[3 * QV + q] = kap * (a02 * g[0] + a12 * g[1] + a22 * g[2]);
+        b[(1 + DIM) * QV + q] = a.lambda * wj * b[q];
+      }
     }
   }
   __syncthreads();
-  // pointwise: q = kappa G grad_ref u, r = lambda w|J| u
-  for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
-    const int el = w / QV, q = w - el * QV;
-    const int e = mt->eid[el];
-    // deformed element: factors per point; affine element: constants times the weight
-    const bool eaf = mt->aff[el] != 0;
-    const T* geo = a.vgeo + a.vgoff[e] + (eaf ? 0 : q);
-    const int gs = eaf ? 1 : QV;
-    T wq = T(1);
-    if (eaf) {
-      const T* gw = tb + TabLayout::GW(N, Q);
-      wq = gw[q % Q] * gw[(q / Q) % Q];
-      if constexpr (DIM == 3) wq *= gw[q / (Q * Q)];
+  if (fine) lift_fine_faces<T, DIM, N>(a, t, mt, rhs, tb, F0, PER, orth);
+  // face field P = s + sum_{tangential m} D_m^T (c_m t) on the face (the
+  // tangential part of the lift after the transposed gradient); c_a t stays as
+  // is and is lifted with l'(+-1)
+  const T* DD = tb + TabLayout::DD(N);
+  if (!orth) {
+    for (int w = threadIdx.x; w < ne * NFACE * QF1; w += blockDim.x) {
+      const int el = w / (NFACE * QF1);
+      const int rem = w - el * NFACE * QF1;
+      const int k = rem / QF1, j = rem - k * QF1;
+      const int ax = k >> 1;
+      int t0, t1;
+      tang_axes<DIM>(ax, t0, t1);
+      const int j0 = j % Q, j1 = j / Q;
+      T* fq = F0 + el * PER + k * NF * QF1;
+      T p = fq[j];
+      const T* f0 = fq + (1 + t0) * QF1 + Q * j1;
+#pragma unroll
+      for (int r = 0; r < Q; ++r) p = fma(DD[r * Q + j0], f0[r], p);
+      if constexpr (DIM == 3) {
+        const T* f1 = fq + (1 + t1) * QF1 + j0;
+#pragma unroll
+        for (int r = 0; r < Q; ++r) p = fma(DD[r * Q + j1], f1[r * Q], p);
+      }
+      fq[j] = p;
     }
-    const T kap = a.kappa ? a.kappa[a.quad_off[e] + q] : T(1);
-    T* b = sm + el * PER;
-    if constexpr (DIM == 2) {
-      const T g0 = b[QV + q], g1 = b[2 * QV + q];
-      const T a00 = wq * geo[0], a01 = wq * geo[gs], a11 = wq * geo[2 * gs], wj = wq * geo[3 * gs];
-      b[QV + q] = kap * (a00 * g0 + a01 * g1);
-      b[2 * QV + q] = kap * (a01 * g0 + a11 * g1);
-      b[q] = a.lambda * wj * b[q];
-    } else {
-      const T g0 = b[QV + q], g1 = b[2 * QV + q], g2 = b[3 * QV + q];
-      const T a00 = wq * geo[0], a01 = wq * geo[gs], a02 = wq * geo[2 * gs], a11 = wq * geo[3 * gs],
-              a12 = wq * geo[4 * gs], a22 = wq * geo[5 * gs], wj = wq * geo[6 * gs];
-      b[QV + q] = kap * (a00 * g0 + a01 * g1 + a02 * g2);
-      b[2 * QV + q] = kap * (a01 * g0 + a11 * g1 + a12 * g2);
-      b[3 * QV + q] = kap * (a02 * g0 + a12 * g1 + a22 * g2);
-      b[q] = a.lambda * wj * b[q];
+    __syncthreads();
+  }
+  // H = R + sum_m D_m^T G_m + sum_faces [ l(+-1) P + l'(+-1) c_a t ] (into U)
+  {
+    const T* LL = tb + TabLayout::LL(N);
+    for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
+      const int el = w / QV, q = w - el * QV;
+      const int qc[3] = {q % Q, (q / Q) % Q, DIM == 3 ? q / (Q * Q) : 0};
+      const T* b = sm + el * PER;
+      const T* fel = F0 + el * PER;
+      T acc = b[(1 + DIM) * QV + q];
+      if constexpr (!line_mode<T, DIM>()) {
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) {
+          const int sm_ = m == 0 ? 1 : (m == 1 ? Q : Q * Q);
+          const T* g = b + (1 + m) * QV + q - qc[m] * sm_;
+#pragma unroll
+          for (int r = 0; r < Q; ++r) acc = fma(DD[r * Q + qc[m]], g[r * sm_], acc);
+        }
+      }
+#pragma unroll
+      for (int ax = 0; ax < DIM; ++ax) {
+        const int j = DIM == 2 ? qc[1 - ax] : (ax == 0 ? qc[1] + Q * qc[2] : (ax == 1 ? qc[0] + Q * qc[2] : qc[0] + Q * qc[1]));
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+          const T* fq = fel + (2 * ax + sd) * NF * QF1 + j;
+          acc = fma(LL[sd * Q + qc[ax]], fq[0], acc);
+          acc = fma(LL[(2 + sd) * Q + qc[ax]], fq[(1 + ax) * QF1], acc);
+        }
+      }
+      sm[el * PER + q] = acc;
     }
   }
   __syncthreads();
-  // faces: flux, projection, extrusion into U and G
-  lift_all_faces<T, DIM, N>(a, t, mt, rhs, tb, sm);
-  // U += sum_m D_m^T G_m
   if constexpr (line_mode<T, DIM>()) {
     contract<T, Q, Q, Q, 0, Q, tab_D(Q), true, true>(G0, U, PER, ne);
     __syncthreads();
@@ -653,30 +688,8 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
     __syncthreads();
     contract<T, Q, Q, Q, 2, Q, tab_D(Q), true, true>(G2, U, PER, ne);
     __syncthreads();
-  } else {
-    // one item per Gauss point reads all DIM fields
-    const T* DD = tb + TabLayout::DD(N);
-    for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
-      const int el = w / QV, q = w - el * QV;
-      const int q0 = q % Q, q1 = (q / Q) % Q, q2 = q / (Q * Q);
-      const T* b = sm + el * PER;
-      T acc = b[q];
-      const T* g0 = b + QV + q - q0;
-#pragma unroll
-      for (int r = 0; r < Q; ++r) acc = fma(DD[r * Q + q0], g0[r], acc);
-      const T* g1 = b + 2 * QV + q - q1 * Q;
-#pragma unroll
-      for (int r = 0; r < Q; ++r) acc = fma(DD[r * Q + q1], g1[r * Q], acc);
-      if constexpr (DIM == 3) {
-        const T* g2 = b + 3 * QV + q - q2 * Q * Q;
-#pragma unroll
-        for (int r = 0; r < Q; ++r) acc = fma(DD[r * Q + q2], g2[r * Q * Q], acc);
-      }
-      sm[el * PER + q] = acc;
-    }
-    __syncthreads();
   }
-  // y = (B^T x B^T (x B^T)) U
+  // y = (B^T x B^T (x B^T)) H
   const T* BB = tb + TabLayout::BB(N);
   T* res;
   if constexpr (DIM == 2) {

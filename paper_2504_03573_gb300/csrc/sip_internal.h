@@ -101,7 +101,7 @@ constexpr int face_buf(int dim, int n, int fields) {
          scratch_slots(dim) * fields * ((dim == 3 ? kQMax * (n + 1) : 0) + cpow(kQMax, dim - 1));
 }
 constexpr int per_elem_trace(int dim, int n) { return 2 * cpow(n + 1, dim) + face_buf(dim, n, 4); }
-constexpr int per_elem_main(int dim, int n) { return (1 + dim) * cpow(n + 1, dim) + face_buf(dim, n, 1 + dim); }
+constexpr int per_elem_main(int dim, int n) { return (2 + dim) * cpow(n + 1, dim) + face_buf(dim, n, 1 + dim); }
 // bytes of the CTA's table block (padded to 16) that precedes the element buffers
 constexpr int table_block_bytes(int bytes_per, int n) { return ((TabLayout::size(n) * bytes_per + 15) / 16) * 16; }
 

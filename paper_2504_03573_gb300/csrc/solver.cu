@@ -839,7 +839,9 @@ int sip_work_model(const sip_handle* h, int precision, sip_work* out) {
         interp_m = nfl_m * per_field;
       }
       ft += 2.0 * 2.0 * QF1 * Q + (orth ? 0.0 : 2.0 * (d - 1) * QF1 * Q) + interp_t + 2.0 * (orth ? 1.0 : d) * np;
-      fm += 12.0 * np + (orth ? 1.0 : d) * np + interp_m + 2.0 * nfl_m * QV;
+      // flux, projection, tangential transposed derivative on the face (P), and the
+      // lift l(+-1) P + l'(+-1) c_a t at every Gauss point
+      fm += 12.0 * np + (orth ? 1.0 : d) * np + interp_m + (orth ? 0.0 : 2.0 * (d - 1) * Q * QF1) + 2.0 * 2.0 * QV;
     }
   }
   out->flops_trace = ft;
