@@ -63,6 +63,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(t_local: float, world: int, device=None) -> float:
+    """Step time of the slowest rank (the job's time); plain value when world == 1."""
+    if world <= 1:
+        return float(t_local)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(units_per_rank: int, world: int, t_max: float) -> float:
+    """Whole-job units per second: every rank processes its own replica of the
+    workload (weak scaling), the job takes the slowest rank's time."""
+    return world * units_per_rank / t_max
+
+
 class ClockSampler:
     """nvidia-smi samples every 200 ms while the timed region runs."""
 
@@ -230,12 +247,8 @@ def run_gb300(args):
         ms, kt, wall = timed_applies(x, y, args.steps, args.warmup, kernel_times=True, label="timed_fp64")
     clocks = clk.summary()
     t_step = sum(ms) / len(ms) / 1e3
-    t_max = t_step
-    if world > 1:
-        tt = torch.tensor([t_step], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt)
-    value = world * n / t_max / 1e9
+    t_max = max_over_ranks(t_step, world, device="cuda")
+    value = job_throughput(n, world, t_max) / 1e9
 
     # ---- FP32 apply (same protocol)
     ms32, kt32, _ = timed_applies(x32, y32, args.steps, args.warmup, kernel_times=True, label="timed_fp32")

@@ -147,3 +147,21 @@ def test_precision_config_c3(pkg):
         assert float(torch.linalg.norm(r) / torch.linalg.norm(b)) <= 1e-10
     assert float(torch.linalg.norm(x64 - x32) / torch.linalg.norm(x64)) <= 1e-7
     assert s32["refinements"] >= 2
+
+
+def test_batched_rhs_c4_full_mesh(pkg):
+    """24^3 jittered hexes, orders 2..7, a batch of right-hand sides from the
+    seed-4 N(0,1) batch: FP64 CG and FP32-refined CG, all columns to 1e-10,
+    each column's residual checked with a separate FP64 apply."""
+    import torch
+    m = si.workload("c4_3d_24cube_jitter_p2to7")
+    op = pkg.SipOperator.from_mesh(m)
+    B = torch.tensor(si.random_rhs_batch(32, op.ndof, 4)[:4], device="cuda")
+    X32, s32 = op.cg_solve(B, mode=1, rtol=1e-10)
+    X64, s64 = op.cg_solve(B, mode=0, rtol=1e-10)
+    for X in (X32, X64):
+        R = B - op.apply(X)
+        rel = torch.linalg.norm(R, dim=1) / torch.linalg.norm(B, dim=1)
+        assert float(rel.max()) <= 1e-10
+    assert s32["converged"] == 1 and s64["converged"] == 1
+    assert float((torch.linalg.norm(X32 - X64, dim=1) / torch.linalg.norm(X64, dim=1)).max()) <= 1e-7
