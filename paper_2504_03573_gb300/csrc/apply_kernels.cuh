@@ -82,12 +82,12 @@ __device__ __forceinline__ void load_tables(T* tb) {
   __syncthreads();
 }
 
-// out[el][o] (+)= sum_j M[j][k(o)] in[el][line(o) + j SI], one work item per
-// output o of every element; in and out are [E2][E1][E0] arrays (E0 fastest)
-// whose AX extent is NIN (in) and NOUT (out).  M is a [NIN][NOUT] shared table.
-template <typename T, int E0, int E1, int E2, int AX, int NOUT, bool ACC>
-__device__ __forceinline__ void cpt(const T* __restrict__ in, T* __restrict__ out, int stride, int ne,
-                                    const T* __restrict__ M) {
+// out(el)[o] (+)= sum_j M[j][k(o)] in(el)[line(o) + j SI], one work item per
+// output o of every element; in(el) and out(el) give the element's [E2][E1][E0]
+// arrays (E0 fastest; shared or global memory) whose AX extent is NIN (in) and
+// NOUT (out).  M is a [NIN][NOUT] shared table.
+template <typename T, int E0, int E1, int E2, int AX, int NOUT, bool ACC, typename InF, typename OutF>
+__device__ __forceinline__ void cpt_io(InF in, OutF out, int ne, const T* __restrict__ M) {
   constexpr int NIN = AX == 0 ? E0 : (AX == 1 ? E1 : E2);
   constexpr int O0 = AX == 0 ? NOUT : E0;
   constexpr int O1 = AX == 1 ? NOUT : E1;
@@ -102,12 +102,20 @@ __device__ __forceinline__ void cpt(const T* __restrict__ in, T* __restrict__ ou
     if (AX == 0) { k = o0; bi = o1 * E0 + o2 * E0 * E1; }
     else if (AX == 1) { k = o1; bi = o0 + o2 * E0 * E1; }
     else { k = o2; bi = o0 + o1 * E0; }
-    const T* src = in + el * stride + bi;
-    T acc = ACC ? out[el * stride + o] : T(0);
+    const T* src = in(el) + bi;
+    T* dst = out(el);
+    T acc = ACC ? dst[o] : T(0);
 #pragma unroll
     for (int j = 0; j < NIN; ++j) acc = fma(M[j * NOUT + k], src[j * SI], acc);
-    out[el * stride + o] = acc;
+    dst[o] = acc;
   }
+}
+
+template <typename T, int E0, int E1, int E2, int AX, int NOUT, bool ACC>
+__device__ __forceinline__ void cpt(const T* __restrict__ in, T* __restrict__ out, int stride, int ne,
+                                    const T* __restrict__ M) {
+  cpt_io<T, E0, E1, E2, AX, NOUT, ACC>([&](int el) { return in + el * stride; },
+                                       [&](int el) { return out + el * stride; }, ne, M);
 }
 
 // GLL coefficients in bA (N^DIM) -> Gauss values (Q^DIM); bB scratch.  Returns
@@ -198,9 +206,34 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
   // per element: Fq [NFACE][4][QF1] (u, du/dn_ref, two tangential derivatives), then scratch
   T* const F0 = sm + 2 * S::QV;
   constexpr int SC = NFACE * 4 * QF1;  // scratch offset from F0: Ft [4][FT], Ff [4][FMAX]
+  // normal derivative c . grad_ref u from (u, du/dn_ref, tangential derivatives)
+  // and store both at canonical point zc
+  auto emit_vals = [&](int el, int k, int z0, int z1, T uv, T dn, T d0, T d1) {
+    const FaceSlot sl = mt->slot[el * 2 * DIM + k];
+    const int qf = sl.qf, ax = k >> 1;
+    const int npts = DIM == 2 ? qf : qf * qf;
+    const int zc = canon(DIM, sl.side, sl.orient, qf, z0, z1);
+    FaceGeo<T> fg{a.fgeo + a.f_goff[sl.face], npts, zc, sl.side, DIM, (sl.flags & kFaceAffine) != 0, T(0)};
+    T g = fg.c(ax) * dn;
+    if (!orth) {
+      int t0, t1;
+      tang_axes<DIM>(ax, t0, t1);
+      g += fg.c(t0) * d0;
+      if constexpr (DIM == 3) g += fg.c(t1) * d1;
+    }
+    T* tr = a.trace + rhs * a.trace_stride + 4 * a.f_troff[sl.face] + (int64_t)(2 * sl.side) * npts + zc;
+    tr[0] = uv;
+    tr[npts] = g;
+  };
+  auto emit = [&](int el, int k, const T* src, int fs, int z0, int z1) {
+    const int z = z0 + mt->slot[el * 2 * DIM + k].qf * z1;
+    emit_vals(el, k, z0, z1, src[z], src[fs + z], orth ? T(0) : src[2 * fs + z],
+              (DIM == 3 && !orth) ? src[3 * fs + z] : T(0));
+  };
   const T* LL = tb + TabLayout::LL(N);
   const T* DT = tb + TabLayout::DT(N);
   // 1. value and reference normal derivative at the element's own face points
+  //    (orthogonal conforming faces need nothing else and are stored at once)
   for (int w = threadIdx.x; w < ne * NFACE * QF1; w += blockDim.x) {
     const int el = w / (NFACE * QF1);
     const int rem = w - el * NFACE * QF1;
@@ -217,6 +250,10 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
       const T v = u[r * sa];
       uf = fma(LL[sd * Q + r], v, uf);
       dn = fma(LL[(2 + sd) * Q + r], v, dn);
+    }
+    if (orth && mt->slot[el * 2 * DIM + k].qf == Q) {
+      emit_vals(el, k, j0, j1, uf, dn, T(0), T(0));
+      continue;
     }
     T* fq = F0 + el * PER + k * 4 * QF1;
     fq[j] = uf;
@@ -246,27 +283,8 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
     }
     __syncthreads();
   }
-  // normal derivative c . grad_ref u and store at canonical point zc
-  auto emit = [&](int el, int k, const T* src, int fs, int z0, int z1) {
-    const FaceSlot sl = mt->slot[el * 2 * DIM + k];
-    const int qf = sl.qf, ax = k >> 1;
-    const int npts = DIM == 2 ? qf : qf * qf;
-    const int z = z0 + qf * z1;
-    const int zc = canon(DIM, sl.side, sl.orient, qf, z0, z1);
-    FaceGeo<T> fg{a.fgeo + a.f_goff[sl.face], npts, zc, sl.side, DIM, (sl.flags & kFaceAffine) != 0, T(0)};
-    T g = fg.c(ax) * src[fs + z];
-    if (!orth) {
-      int t0, t1;
-      tang_axes<DIM>(ax, t0, t1);
-      g += fg.c(t0) * src[2 * fs + z];
-      if constexpr (DIM == 3) g += fg.c(t1) * src[3 * fs + z];
-    }
-    T* tr = a.trace + rhs * a.trace_stride + 4 * a.f_troff[sl.face] + (int64_t)(2 * sl.side) * npts + zc;
-    tr[0] = src[z];
-    tr[npts] = g;
-  };
-  // 3. conforming faces, all at once
-  for (int w = threadIdx.x; w < ne * NFACE * QF1; w += blockDim.x) {
+  // 3. conforming faces, all at once (orthogonal ones were stored in step 1)
+  for (int w = threadIdx.x; w < (orth ? 0 : ne * NFACE * QF1); w += blockDim.x) {
     const int el = w / (NFACE * QF1);
     const int rem = w - el * NFACE * QF1;
     const int k = rem / QF1, j = rem - k * QF1;
@@ -355,17 +373,40 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
   const int ne = t.count;
   load_meta<DIM>(a.elist, a.slots, a.eaff, t, mt);
   load_tables<T, N>(tb);
-  for (int w = threadIdx.x; w < ne * S::NV; w += blockDim.x) {
-    const int el = w / S::NV, i = w - el * S::NV;
-    sm[el * PER + i] = a.x[rhs * a.ndof + a.dof_off[mt->eid[el]] + i];
-  }
-  __syncthreads();
   // one output per thread (2D, and FP64 in 3D: more parallel work for the narrow
   // FP64 pipe) or one line per thread with the matrices as constant-bank operands
   // (FP32 in 3D: fewer instructions per FMA)
   T* U;
-  if constexpr (!line_mode<T, DIM>()) U = interp_to_gauss<T, DIM, N>(sm, sm + S::QV, PER, ne, tb);
-  else U = to_gauss<T, DIM, N>(sm, sm + S::QV, PER, ne);
+  if constexpr (!line_mode<T, DIM>()) {
+    // first contraction reads the coefficients straight from global memory
+    constexpr int Q = S::Q;
+    const T* BT = tb + TabLayout::BT(N);
+    T* bA = sm;
+    T* bB = sm + S::QV;
+    auto gx = [&](int el) { return a.x + rhs * a.ndof + a.dof_off[mt->eid[el]]; };
+    if constexpr (DIM == 2) {
+      cpt_io<T, N, N, 1, 0, Q, false>(gx, [&](int el) { return bB + el * PER; }, ne, BT);
+      __syncthreads();
+      cpt<T, Q, N, 1, 1, Q, false>(bB, bA, PER, ne, BT);
+      __syncthreads();
+      U = bA;
+    } else {
+      cpt_io<T, N, N, N, 0, Q, false>(gx, [&](int el) { return bB + el * PER; }, ne, BT);
+      __syncthreads();
+      cpt<T, Q, N, N, 1, Q, false>(bB, bA, PER, ne, BT);
+      __syncthreads();
+      cpt<T, Q, Q, N, 2, Q, false>(bA, bB, PER, ne, BT);
+      __syncthreads();
+      U = bB;
+    }
+  } else {
+    for (int w = threadIdx.x; w < ne * S::NV; w += blockDim.x) {
+      const int el = w / S::NV, i = w - el * S::NV;
+      sm[el * PER + i] = a.x[rhs * a.ndof + a.dof_off[mt->eid[el]] + i];
+    }
+    __syncthreads();
+    U = to_gauss<T, DIM, N>(sm, sm + S::QV, PER, ne);
+  }
   if (a.ug) {
     for (int w = threadIdx.x; w < ne * S::QV; w += blockDim.x) {
       const int el = w / S::QV, q = w - el * S::QV;
@@ -689,21 +730,20 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
     contract<T, Q, Q, Q, 2, Q, tab_D(Q), true, true>(G2, U, PER, ne);
     __syncthreads();
   }
-  // y = (B^T x B^T (x B^T)) H
+  // y = (B^T x B^T (x B^T)) H; the last contraction writes y in global memory
   const T* BB = tb + TabLayout::BB(N);
-  T* res;
+  auto gy = [&](int el) { return a.y + rhs * a.ndof + a.dof_off[mt->eid[el]]; };
+  T* res = nullptr;
   if constexpr (DIM == 2) {
     cpt<T, Q, Q, 1, 0, N, false>(U, G0, PER, ne, BB);
     __syncthreads();
-    cpt<T, N, Q, 1, 1, N, false>(G0, G1, PER, ne, BB);
-    res = G1;
+    cpt_io<T, N, Q, 1, 1, N, false>([&](int el) { return G0 + el * PER; }, gy, ne, BB);
   } else if constexpr (!line_mode<T, DIM>()) {
     cpt<T, Q, Q, Q, 0, N, false>(U, G0, PER, ne, BB);
     __syncthreads();
     cpt<T, N, Q, Q, 1, N, false>(G0, G1, PER, ne, BB);
     __syncthreads();
-    cpt<T, N, N, Q, 2, N, false>(G1, G2, PER, ne, BB);
-    res = G2;
+    cpt_io<T, N, N, Q, 2, N, false>([&](int el) { return G1 + el * PER; }, gy, ne, BB);
   } else {
     (void)BB;
     contract<T, Q, Q, Q, 0, N, tab_B(N), true, false>(U, G0, PER, ne);
@@ -713,10 +753,15 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
     contract<T, N, N, Q, 2, N, tab_B(N), true, false>(G1, G2, PER, ne);
     res = G2;
   }
-  __syncthreads();
-  for (int w = threadIdx.x; w < ne * NV; w += blockDim.x) {
-    const int el = w / NV, i = w - el * NV;
-    a.y[rhs * a.ndof + a.dof_off[mt->eid[el]] + i] = res[el * PER + i];
+  if constexpr (line_mode<T, DIM>()) {
+    __syncthreads();
+    for (int w = threadIdx.x; w < ne * NV; w += blockDim.x) {
+      const int el = w / NV, i = w - el * NV;
+      a.y[rhs * a.ndof + a.dof_off[mt->eid[el]] + i] = res[el * PER + i];
+    }
+  } else {
+    (void)res;
+    (void)NV;
   }
 }
 
