@@ -210,13 +210,19 @@ typedef struct sip_work {
 } sip_work;
 int  sip_work_model(const sip_handle* h, int precision, sip_work* out);
 
-/* Autotuner of the tile shape (elements per CTA for each polynomial order):
- * coordinate descent over the orders present, timing the whole apply (best of
- * three batches of reps launches) for a few candidate tile sizes of one order
- * at a time, and installs the fastest for this precision.
- * Set-up call: allocates temporaries and synchronises the stream.  The paper
- * picks a kernel configuration per order (Sec. 5.1); this chooses it by
- * measurement on the current GPU. */
+/* Launch schedule.  Elements are grouped in tiles of one order, one CTA per
+ * tile and right-hand side, at most a set number of elements per tile for each
+ * order.  Where that gives fewer tiles than CTAs resident at once, tiles are
+ * split further so that there are about (CTAs per SM) x SMs of them, each with
+ * the same share of the apply's flops: one wave of equal CTAs keeps every SM
+ * busy to the end of the launch, whichever SM each CTA lands on.
+ *
+ * Autotuner: coordinate descent over the orders present, timing the whole
+ * apply (best of three batches of reps launches) for a few candidate tile sizes
+ * of one order at a time, then over the CTAs per SM; installs the fastest for
+ * this precision.  Set-up call: allocates temporaries and synchronises the
+ * stream.  The paper picks a kernel configuration per order (Sec. 5.1); this
+ * chooses it by measurement on the current GPU. */
 int  sip_autotune(sip_handle* h, int precision, int reps, void* stream);
 
 /* Current tiling: epb_out[P] = largest number of elements per tile used for
@@ -224,6 +230,20 @@ int  sip_autotune(sip_handle* h, int precision, int reps, void* stream);
  * per apply (may be NULL). */
 int  sip_get_tiling(const sip_handle* h, int precision, int32_t* epb_out /* [SIP_MAX_ORDER+1] */,
                     int64_t* ntiles_out);
+
+/* Current launch grid: *nctas_out CTAs (tiles) per right-hand side, balanced
+ * for *ctas_per_sm_out resident CTAs per SM. */
+int  sip_get_grid(const sip_handle* h, int precision, int32_t* nctas_out, int32_t* ctas_per_sm_out);
+
+/* Install a tiling by hand: epb[P] = elements per tile for order P (0: the
+ * default; at most 32), P = 0..SIP_MAX_ORDER, or epb = NULL for all defaults;
+ * ctas_per_sm = resident CTAs per SM to balance for (0: as many as fit, capped
+ * at the number of tiles per SM that epb gives; larger values are capped at the
+ * occupancy).  Set-up call: synchronises the device.  Errors: SIP_ERR_ARG for an
+ * out-of-range value or a tile too large for shared memory (the previous tiling
+ * stays). */
+int  sip_set_tiling(sip_handle* h, int precision, const int32_t* epb /* [SIP_MAX_ORDER+1] */,
+                    int32_t ctas_per_sm);
 
 /* Device time of the last apply's kernels, per phase, measured with CUDA events
  * on the apply's stream when timing is enabled (sip_set_timing(h, 1)); ms. */

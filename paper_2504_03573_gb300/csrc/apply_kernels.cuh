@@ -635,30 +635,37 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
           g[m] = acc;
         }
       }
-      // deformed element: factors per point; affine element: constants times the weight
+      // deformed element: factors per point; affine element: constants times the
+      // Gauss weight.  The gradient is scaled first (kappa, weight), so that each
+      // multiply that is 1 is skipped.
       const bool eaf = mt->aff[el] != 0;
       const T* geo = a.vgeo + a.vgoff[e] + (eaf ? 0 : q);
       const int gs = eaf ? 1 : QV;
-      T wq = T(1);
-      if (eaf) {
-        const T* gw = tb + TabLayout::GW(N, Q);
-        wq = gw[q % Q] * gw[(q / Q) % Q];
-        if constexpr (DIM == 3) wq *= gw[q / (Q * Q)];
+      T lwj = a.lambda * geo[DIM == 2 ? 3 * gs : 6 * gs];
+      if (eaf || a.kappa) {
+        T wk = T(1);
+        if (eaf) {
+          const T* gw = tb + TabLayout::GW(N, Q);
+          T wq = gw[q % Q] * gw[(q / Q) % Q];
+          if constexpr (DIM == 3) wq *= gw[q / (Q * Q)];
+          lwj *= wq;
+          wk = wq;
+        }
+        if (a.kappa) wk = eaf ? wk * a.kappa[a.quad_off[e] + q] : a.kappa[a.quad_off[e] + q];
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) g[m] *= wk;
       }
-      const T kap = a.kappa ? a.kappa[a.quad_off[e] + q] : T(1);
       if constexpr (DIM == 2) {
-        const T a00 = wq * geo[0], a01 = wq * geo[gs], a11 = wq * geo[2 * gs], wj = wq * geo[3 * gs];
-        b[QV + q] = kap * (a00 * g[0] + a01 * g[1]);
-        b[2 * QV + q] = kap * (a01 * g[0] + a11 * g[1]);
-        b[(1 + DIM) * QV + q] = a.lambda * wj * b[q];
+        b[QV + q] = geo[0] * g[0] + geo[gs] * g[1];
+        b[2 * QV + q] = geo[gs] * g[0] + geo[2 * gs] * g[1];
       } else {
-        const T a00 = wq * geo[0], a01 = wq * geo[gs], a02 = wq * geo[2 * gs], a11 = wq * geo[3 * gs],
-                a12 = wq * geo[4 * gs], a22 = wq * geo[5 * gs], wj = wq * geo[6 * gs];
-        b[QV + q] = kap * (a00 * g[0] + a01 * g[1] + a02 * g[2]);
-        b[2 * QV + q] = kap * (a01 * g[0] + a11 * g[1] + a12 * g[2]);
-        b[3 * QV + q] = kap * (a02 * g[0] + a12 * g[1] + a22 * g[2]);
-        b[(1 + DIM) * QV + q] = a.lambda * wj * b[q];
+        const T a00 = geo[0], a01 = geo[gs], a02 = geo[2 * gs], a11 = geo[3 * gs], a12 = geo[4 * gs],
+                a22 = geo[5 * gs];
+        b[QV + q] = a00 * g[0] + a01 * g[1] + a02 * g[2];
+        b[2 * QV + q] = a01 * g[0] + a11 * g[1] + a12 * g[2];
+        b[3 * QV + q] = a02 * g[0] + a12 * g[1] + a22 * g[2];
       }
+      b[(1 + DIM) * QV + q] = lwj * b[q];
     }
   }
   __syncthreads();

@@ -51,29 +51,25 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
   for (int n : orders) cur[n] = apply_epb(p.dim, n, precision);
   const bool timing = h->timing;
   h->timing = false;
-  auto time_full = [&](const int* epb, float* ms_out) -> int {
-    std::vector<Tile> t;
-    build_tiles(p, precision, epb, t);
-    size_t st = 0, sm = 0;
-    for (const Tile& tt : t) {
-      const size_t fixed = (size_t)table_block_bytes(es, tt.n) + kMetaBytes;
-      st = std::max(st, fixed + (size_t)tt.count * per_elem_trace(p.dim, tt.n) * es);
-      sm = std::max(sm, fixed + (size_t)tt.count * per_elem_main(p.dim, tt.n) * es);
-    }
-    if (st > 200 * 1024 || sm > 200 * 1024) { *ms_out = 1e30f; return SIP_OK; }
+  auto time_full = [&](const int* epb, int per_sm, float* ms_out, int* per_sm_out) -> int {
+    Schedule sc;
+    int r2 = make_schedule(h, precision, epb, per_sm, sc);
+    if (r2 == SIP_ERR_ARG) { *ms_out = 1e30f; return SIP_OK; }  // tile too large for shared memory
+    if (r2) return r2;
+    if (per_sm_out) *per_sm_out = sc.per_sm;
     Tile* td = nullptr;
-    cudaError_t ee = cudaMalloc((void**)&td, t.size() * sizeof(Tile));
-    if (ee == cudaSuccess) ee = cudaMemcpy(td, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+    cudaError_t ee = cudaMalloc((void**)&td, std::max<size_t>(16, sc.tiles.size() * sizeof(Tile)));
+    if (ee == cudaSuccess) ee = cudaMemcpy(td, sc.tiles.data(), sc.tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
     if (ee != cudaSuccess) { cudaFree(td); return cuda_fail(ee, "autotune tiles"); }
-    int r2 = SIP_OK;
-    for (int w = 0; w < 2 && r2 == SIP_OK; ++w)
-      r2 = apply_tiles(h, precision, td, (int)t.size(), st, sm, x, y, 1, s, 0, nullptr);
+    auto run = [&]() {
+      return apply_tiles(h, precision, td, (int)sc.tiles.size(), sc.smem_t, sc.smem_m, x, y, 1, s, 0, nullptr);
+    };
+    for (int w = 0; w < 2 && r2 == SIP_OK; ++w) r2 = run();
     // best of three batches of reps launches
     float best = 1e30f;
     for (int batch = 0; batch < 3 && r2 == SIP_OK; ++batch) {
       cudaEventRecord(a, s);
-      for (int r = 0; r < reps && r2 == SIP_OK; ++r)
-        r2 = apply_tiles(h, precision, td, (int)t.size(), st, sm, x, y, 1, s, 0, nullptr);
+      for (int r = 0; r < reps && r2 == SIP_OK; ++r) r2 = run();
       cudaEventRecord(b, s);
       ee = cudaEventSynchronize(b);
       if (ee != cudaSuccess) { r2 = cuda_fail(ee, "autotune timing"); break; }
@@ -86,7 +82,8 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
     return r2;
   };
   float cur_ms = 1e30f;
-  rc = time_full(cur, &cur_ms);
+  int cur_per_sm = 0, auto_per_sm = 0;
+  rc = time_full(cur, 0, &cur_ms, &auto_per_sm);
   for (int n : orders) {
     if (rc) break;
     const int base = cur[n];
@@ -100,12 +97,24 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
       std::memcpy(trial, cur, sizeof(trial));
       trial[n] = c;
       float ms = 0.0f;
-      rc = time_full(trial, &ms);
+      rc = time_full(trial, 0, &ms, nullptr);
       if (rc) break;
       if (ms < 0.97f * cur_ms) {  // keep a change only for a clear gain
         cur_ms = ms;
         cur[n] = c;
       }
+    }
+  }
+  // then the number of resident CTAs per SM the schedule is balanced for
+  for (int ps = 1; ps <= 8 && rc == SIP_OK; ++ps) {
+    if (ps == auto_per_sm) continue;
+    float ms = 0.0f;
+    int got = 0;
+    rc = time_full(cur, ps, &ms, &got);
+    if (rc || got != ps) break;  // beyond the occupancy
+    if (ms < 0.97f * cur_ms) {
+      cur_ms = ms;
+      cur_per_sm = ps;
     }
   }
   int* best = cur;
@@ -115,9 +124,9 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
   cudaFree(x);
   cudaFree(y);
   if (rc) return rc;
-  rc = set_tiles(h, precision, best);
+  rc = set_tiles(h, precision, best, cur_per_sm);
   if (rc) return rc;
-  std::memcpy(h->epb[pi], best, sizeof(best));
+  std::memcpy(h->epb[pi], best, sizeof(cur));
   return SIP_OK;
 }
 
@@ -127,5 +136,31 @@ extern "C" int sip_get_tiling(const sip_handle* h, int precision, int32_t* epb_o
   for (int n = 0; n <= kNMax; ++n) epb_out[n] = 0;
   for (const Tile& t : h->tiles_h[pi]) epb_out[t.n - 1] = std::max(epb_out[t.n - 1], (int32_t)t.count);
   if (ntiles_out) *ntiles_out = (int64_t)h->tiles_h[pi].size();
+  return SIP_OK;
+}
+
+extern "C" int sip_get_grid(const sip_handle* h, int precision, int32_t* nctas_out, int32_t* ctas_per_sm_out) {
+  if (!h || !nctas_out || !ctas_per_sm_out) return fail(SIP_ERR_ARG, "null argument");
+  if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
+  const int pi = precision == SIP_FP32 ? 1 : 0;
+  *nctas_out = (int32_t)h->tiles_h[pi].size();
+  *ctas_per_sm_out = h->ctas_per_sm[pi];
+  return SIP_OK;
+}
+
+extern "C" int sip_set_tiling(sip_handle* h, int precision, const int32_t* epb, int32_t ctas_per_sm) {
+  if (!h) return fail(SIP_ERR_ARG, "null handle");
+  if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
+  if (ctas_per_sm < 0) return fail(SIP_ERR_ARG, "ctas_per_sm must be >= 0");
+  int e[kNMax + 2] = {};
+  if (epb)
+    for (int P = 0; P <= kNMax - 1; ++P) {
+      if (epb[P] < 0 || epb[P] > kMaxEpb) return fail(SIP_ERR_ARG, "elements per tile must be in 0..32");
+      e[P + 1] = epb[P];
+    }
+  const int pi = precision == SIP_FP32 ? 1 : 0;
+  int rc = set_tiles(h, precision, e, ctas_per_sm);
+  if (rc) return rc;
+  std::memcpy(h->epb[pi], e, sizeof(e));
   return SIP_OK;
 }

@@ -51,6 +51,10 @@ cudaError_t prepare_3d_f64();
 cudaError_t prepare_3d_f32();
 cudaError_t prepare_aux_2d();
 cudaError_t prepare_aux_3d();
+cudaError_t occupancy_2d_f64(size_t, size_t, int*);
+cudaError_t occupancy_2d_f32(size_t, size_t, int*);
+cudaError_t occupancy_3d_f64(size_t, size_t, int*);
+cudaError_t occupancy_3d_f32(size_t, size_t, int*);
 cudaError_t launch_apply_2d_f64(const ApplyArgs<double>&, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
 cudaError_t launch_apply_3d_f64(const ApplyArgs<double>&, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
 cudaError_t launch_apply_2d_f32(const ApplyArgs<float>&, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
@@ -137,24 +141,54 @@ size_t apply_scratch_bytes(const sip_handle* h, int precision, int nrhs, size_t*
   return precision == SIP_FP64 ? tr + (size_t)nrhs * (size_t)h->plan.nquad * es : tr;
 }
 
-// (Re)build the tiles of one precision (epb_by_n[n] > 0 overrides the default
-// elements per tile for order n - 1), upload them and size the shared memory.
-int set_tiles(sip_handle* h, int precision, const int* epb_by_n) {
-  const int pi = precision == SIP_FP32 ? 1 : 0;
-  std::vector<Tile> tiles;
-  build_tiles(h->plan, precision, epb_by_n, tiles);
+int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_per_sm, Schedule& s) {
+  const Plan& p = h->plan;
   const int es = precision == SIP_FP32 ? 4 : 8;
-  size_t st = 0, sm = 0;
-  for (const Tile& t : tiles) {
-    const size_t fixed = (size_t)table_block_bytes(es, t.n) + kMetaBytes;
-    st = std::max(st, fixed + (size_t)t.count * per_elem_trace(h->plan.dim, t.n) * es);
-    sm = std::max(sm, fixed + (size_t)t.count * per_elem_main(h->plan.dim, t.n) * es);
-  }
-  if (st > 200 * 1024 || sm > 200 * 1024) return fail(SIP_ERR_ARG, "tile too large for shared memory");
+  auto size_smem = [&]() {
+    s.smem_t = s.smem_m = 0;
+    for (const Tile& t : s.tiles) {
+      const size_t fixed = (size_t)table_block_bytes(es, t.n) + kMetaBytes;
+      s.smem_t = std::max(s.smem_t, fixed + (size_t)t.count * per_elem_trace(p.dim, t.n) * es);
+      s.smem_m = std::max(s.smem_m, fixed + (size_t)t.count * per_elem_main(p.dim, t.n) * es);
+    }
+  };
+  // tiles of the largest size epb allows: their count and shared memory bound the rest
+  build_tiles(p, precision, epb, 0, s.tiles);
+  size_smem();
+  s.per_sm = 1;
+  if (s.smem_t > 200 * 1024 || s.smem_m > 200 * 1024) return fail(SIP_ERR_ARG, "tile too large for shared memory");
+  const int64_t ntile = (int64_t)s.tiles.size();
+  if (ntile == 0) return SIP_OK;
+  int occ = 0, nsm = 0;
+  cudaError_t e;
+  if (p.dim == 2) e = precision == SIP_FP64 ? occupancy_2d_f64(s.smem_t, s.smem_m, &occ) : occupancy_2d_f32(s.smem_t, s.smem_m, &occ);
+  else e = precision == SIP_FP64 ? occupancy_3d_f64(s.smem_t, s.smem_m, &occ) : occupancy_3d_f32(s.smem_t, s.smem_m, &occ);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+  occ = std::max(1, occ);
+  nsm = std::max(1, nsm);
+  // at least per_sm x SMs tiles of equal flops (tiles only get smaller than the
+  // bound above, so the shared memory and the occupancy hold)
+  const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ)
+                                     : (int)std::min<int64_t>(occ, std::max<int64_t>(1, ntile / nsm));
+  build_tiles(p, precision, epb, nsm * per_sm, s.tiles);
+  size_smem();
+  s.per_sm = per_sm;
+  return SIP_OK;
+}
+
+// (Re)build the tiles of one precision (epb_by_n[n] > 0 overrides the default
+// elements per tile for order n - 1; ctas_per_sm > 0 fixes the resident CTAs per
+// SM the tiles are balanced for), upload them and size the shared memory.
+int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm) {
+  const int pi = precision == SIP_FP32 ? 1 : 0;
+  Schedule sc;
+  int rc = make_schedule(h, precision, epb_by_n, ctas_per_sm, sc);
+  if (rc) return rc;
   Tile* d = nullptr;
-  cudaError_t e = cudaMalloc((void**)&d, std::max<size_t>(16, tiles.size() * sizeof(Tile)));
-  if (e == cudaSuccess && !tiles.empty())
-    e = cudaMemcpy(d, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMalloc((void**)&d, std::max<size_t>(16, sc.tiles.size() * sizeof(Tile)));
+  if (e == cudaSuccess && !sc.tiles.empty())
+    e = cudaMemcpy(d, sc.tiles.data(), sc.tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(d);
     return cuda_fail(e, "tiles");
@@ -164,9 +198,10 @@ int set_tiles(sip_handle* h, int precision, const int* epb_by_n) {
     cudaFree(h->tiles_d[pi]);
   }
   h->tiles_d[pi] = d;
-  h->tiles_h[pi] = std::move(tiles);
-  h->smem_trace[pi] = st;
-  h->smem_main[pi] = sm;
+  h->tiles_h[pi] = std::move(sc.tiles);
+  h->ctas_per_sm[pi] = sc.per_sm;
+  h->smem_trace[pi] = sc.smem_t;
+  h->smem_main[pi] = sc.smem_m;
   for (auto* W : {&h->cg64, &h->cg32})
     if (W->graph) { cudaGraphExecDestroy(W->graph); W->graph = nullptr; }
   return SIP_OK;
@@ -370,7 +405,7 @@ int sip_create(const sip_mesh* mesh, const int32_t* orders, double lambda, const
     return rc;
   }
   for (int prec : {SIP_FP64, SIP_FP32}) {
-    rc = set_tiles(h, prec, nullptr);
+    rc = set_tiles(h, prec, nullptr, 0);
     if (rc) { sip_destroy(h); return rc; }
   }
   rc = handle_grow_trace(h, 1);

@@ -58,6 +58,7 @@ struct sip_handle {
   sip::Tile* tiles_d[2] = {nullptr, nullptr};   // per precision (FP64, FP32)
   std::vector<sip::Tile> tiles_h[2];
   int epb[2][sip::kNMax + 2] = {};                // elements per tile per order in use (0: default)
+  int ctas_per_sm[2] = {0, 0};                    // resident CTAs per SM the tiles are balanced for
   double* xq = nullptr;
   sip::DevGeom<double> gd;
   sip::DevGeom<float> gf;
@@ -98,6 +99,16 @@ template <>
 inline const sip::DevGeom<float>& sip_handle::geom<float>() const { return gf; }
 
 namespace sip {
+// Tiles of one precision (one CTA each) with the shared memory of the two
+// kernels.  per_sm: resident CTAs per SM the tile sizes were balanced for.
+struct Schedule {
+  std::vector<Tile> tiles;
+  size_t smem_t = 0, smem_m = 0;
+  int per_sm = 0;
+};
+// epb: elements per tile by order (nullptr or 0 entries: default); ctas_per_sm <= 0:
+// as many as fit, capped at the number of default-sized tiles per SM
+int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_per_sm, Schedule& s);
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* where);
 // scratch_override: caller-provided scratch holding the trace buffer followed by
@@ -107,6 +118,6 @@ int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cu
 size_t apply_scratch_bytes(const sip_handle* h, int precision, int nrhs, size_t* ug_offset);
 int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, int ntiles, size_t smem_t, size_t smem_m,
                 const void* x, void* y, int nrhs, cudaStream_t s, int transpose, void* scratch_override);
-int set_tiles(sip_handle* h, int precision, const int* epb_by_n);
+int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm);
 int handle_grow_trace(sip_handle* h, int nrhs);
 }  // namespace sip

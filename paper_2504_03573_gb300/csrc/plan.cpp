@@ -471,32 +471,83 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
   return SIP_OK;
 }
 
-// Tiles of at most epb(n) elements of one order, cut from the order-sorted list.
-void build_tiles(const Plan& p, int precision, const int* epb_override, std::vector<Tile>& tiles) {
+// Flops (FMA = 2) of one element in the trace and main kernels: the work model
+// of the apply and the cost that the CTA schedule balances.
+void element_flops(const Plan& p, int64_t e, double& ft, double& fm) {
+  const int d = p.dim;
+  const double N = p.P[e] + 1, Q = N + 1;
+  const double QV = d == 2 ? Q * Q : Q * Q * Q;
+  const double QF1 = d == 2 ? Q : Q * Q;
+  // one sum-factorised interpolation GLL -> Gauss
+  const double interp = 2.0 * (d == 2 ? (N * N * Q + N * Q * Q) : (N * N * N * Q + N * N * Q * Q + N * Q * Q * Q));
+  const double grad = 2.0 * d * QV * Q;
+  ft = interp;
+  fm = grad + (2.0 * d * d + d + 2.0) * QV + grad + interp;  // gradient, pointwise, D^T, B^T
+  for (int k = 0; k < 2 * d; ++k) {
+    const FaceSlot& sl = p.slots[(size_t)e * 2 * d + k];
+    const bool orth = sl.flags & kFaceOrth;  // tangential terms vanish identically
+    const double qf = sl.qf;
+    const double np = d == 2 ? qf : qf * qf;
+    const double nfl_t = orth ? 2.0 : 4.0, nfl_m = orth ? 2.0 : 1.0 + d;
+    double interp_t = 0.0, interp_m = 0.0;
+    if (sl.qf != (int)Q) {
+      const double per_field = 2.0 * (d == 2 ? qf * Q : (Q * qf * Q + qf * qf * Q));
+      interp_t = nfl_t * per_field;
+      interp_m = nfl_m * per_field;
+    }
+    ft += 2.0 * 2.0 * QF1 * Q + (orth ? 0.0 : 2.0 * (d - 1) * QF1 * Q) + interp_t + 2.0 * (orth ? 1.0 : d) * np;
+    // flux, projection, tangential transposed derivative on the face (P), and the
+    // lift l(+-1) P + l'(+-1) c_a t at every Gauss point
+    fm += 12.0 * np + (orth ? 1.0 : d) * np + interp_m + (orth ? 0.0 : 2.0 * (d - 1) * Q * QF1) + 2.0 * 2.0 * QV;
+  }
+}
+
+namespace {
+
+Tile make_tile(const Plan& p, int n, int64_t s0, int64_t s1) {
+  int qfm = n + 1;
+  bool orth = true;
+  for (int64_t s = s0; s < s1; ++s)
+    for (int f = 0; f < 2 * p.dim; ++f) {
+      const FaceSlot& sl = p.slots[(size_t)p.elist[s] * 2 * p.dim + f];
+      qfm = std::max(qfm, (int)sl.qf);
+      orth = orth && (sl.flags & kFaceOrth);
+    }
+  const int flags = qfm | (qfm > n + 1 ? kTileFine : 0) | (orth ? kTileOrth : 0);
+  return Tile{n, (int32_t)s0, (int32_t)(s1 - s0), flags};
+}
+
+}  // namespace
+
+// Tiles of one order each, cut from the order-sorted element list: a run of cnt
+// elements of order n - 1 (flops C_n of the apply's C in all) is spread evenly
+// over k_n = max(ceil(cnt / epb(n)), round(ntarget C_n / C)) tiles, at most cnt.
+// With ntarget = the CTAs resident at once, every tile that is not capped by
+// epb carries the same flops, so one wave of CTAs keeps every SM busy to the end.
+void build_tiles(const Plan& p, int precision, const int* epb_override, int ntarget, std::vector<Tile>& tiles) {
   tiles.clear();
   const int64_t E = p.E;
+  double C = 0.0;
+  std::vector<double> ce(E);
+  for (int64_t i = 0; i < E; ++i) {
+    double ft = 0.0, fm = 0.0;
+    element_flops(p, p.elist[i], ft, fm);
+    ce[i] = ft + fm;
+    C += ce[i];
+  }
   for (int64_t i = 0; i < E;) {
     const int n = p.P[p.elist[i]] + 1;
     int64_t j = i;
-    while (j < E && p.P[p.elist[j]] + 1 == n) ++j;
+    double Cn = 0.0;
+    while (j < E && p.P[p.elist[j]] + 1 == n) Cn += ce[j++];
     int epb = epb_override && epb_override[n] > 0 ? epb_override[n] : apply_epb(p.dim, n, precision);
     epb = std::max(1, std::min(epb, kMaxEpb));
-    // spread the bucket evenly over ceil(count / epb) tiles
     const int64_t cnt = j - i;
-    const int64_t ntile = (cnt + epb - 1) / epb;
-    for (int64_t k = 0; k < ntile; ++k) {
-      const int64_t s0 = i + (cnt * k) / ntile, s1 = i + (cnt * (k + 1)) / ntile;
-      int qfm = n + 1;
-      bool orth = true;
-      for (int64_t s = s0; s < s1; ++s)
-        for (int f = 0; f < 2 * p.dim; ++f) {
-          const FaceSlot& sl = p.slots[(size_t)p.elist[s] * 2 * p.dim + f];
-          qfm = std::max(qfm, (int)sl.qf);
-          orth = orth && (sl.flags & kFaceOrth);
-        }
-      const int flags = qfm | (qfm > n + 1 ? kTileFine : 0) | (orth ? kTileOrth : 0);
-      tiles.push_back(Tile{n, (int32_t)s0, (int32_t)(s1 - s0), flags});
-    }
+    int64_t ntile = (cnt + epb - 1) / epb;
+    if (ntarget > 0 && C > 0.0) ntile = std::max<int64_t>(ntile, std::llround(ntarget * Cn / C));
+    ntile = std::min(ntile, cnt);
+    for (int64_t k = 0; k < ntile; ++k)
+      tiles.push_back(make_tile(p, n, i + (cnt * k) / ntile, i + (cnt * (k + 1)) / ntile));
     i = j;
   }
 }

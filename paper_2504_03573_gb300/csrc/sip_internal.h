@@ -178,8 +178,10 @@ double lagrange(const std::vector<double>& nodes, int j, double x);
 double lagrange_deriv(const std::vector<double>& nodes, int j, double x);
 void fill_tables(std::vector<double>& tab);
 
-// elements per tile for the apply kernels (host choice), and the tiles for it
+// elements per tile for the apply kernels (host choice), per-element flops, and
+// the tiles (at least about ntarget of them, of equal flops, where ntarget > 0)
 int apply_epb(int dim, int n, int precision);
-void build_tiles(const Plan& p, int precision, const int* epb_override, std::vector<Tile>& tiles);
+void element_flops(const Plan& p, int64_t e, double& ft, double& fm);
+void build_tiles(const Plan& p, int precision, const int* epb_override, int ntarget, std::vector<Tile>& tiles);
 
 }  // namespace sip

@@ -814,35 +814,13 @@ int sip_quad_points(sip_handle* h, double* xq, void* stream) {
 int sip_work_model(const sip_handle* h, int precision, sip_work* out) {
   if (!h || !out) return fail(SIP_ERR_ARG, "null argument");
   const Plan& p = h->plan;
-  const int d = p.dim;
   const double es = precision == SIP_FP32 ? 4.0 : 8.0;
   double ft = 0.0, fm = 0.0;
   for (int64_t e = 0; e < p.E; ++e) {
-    const double N = p.P[e] + 1, Q = N + 1;
-    const double QV = d == 2 ? Q * Q : Q * Q * Q;
-    const double QF1 = d == 2 ? Q : Q * Q;
-    // one sum-factorised interpolation GLL -> Gauss (FMA = 2 flops)
-    const double interp = 2.0 * (d == 2 ? (N * N * Q + N * Q * Q) : (N * N * N * Q + N * N * Q * Q + N * Q * Q * Q));
-    const double grad = 2.0 * d * QV * Q;
-    ft += interp;
-    fm += grad + (2.0 * d * d + d + 2.0) * QV + grad + interp;  // gradient, pointwise, D^T, B^T
-    for (int k = 0; k < 2 * d; ++k) {
-      const FaceSlot& sl = p.slots[(size_t)e * 2 * d + k];
-      const bool orth = sl.flags & kFaceOrth;  // tangential terms vanish identically
-      const double qf = sl.qf;
-      const double np = d == 2 ? qf : qf * qf;
-      const double nfl_t = orth ? 2.0 : 4.0, nfl_m = orth ? 2.0 : 1.0 + d;
-      double interp_t = 0.0, interp_m = 0.0;
-      if (sl.qf != (int)Q) {
-        const double per_field = 2.0 * (d == 2 ? qf * Q : (Q * qf * Q + qf * qf * Q));
-        interp_t = nfl_t * per_field;
-        interp_m = nfl_m * per_field;
-      }
-      ft += 2.0 * 2.0 * QF1 * Q + (orth ? 0.0 : 2.0 * (d - 1) * QF1 * Q) + interp_t + 2.0 * (orth ? 1.0 : d) * np;
-      // flux, projection, tangential transposed derivative on the face (P), and the
-      // lift l(+-1) P + l'(+-1) c_a t at every Gauss point
-      fm += 12.0 * np + (orth ? 1.0 : d) * np + interp_m + (orth ? 0.0 : 2.0 * (d - 1) * Q * QF1) + 2.0 * 2.0 * QV;
-    }
+    double a = 0.0, b = 0.0;
+    element_flops(p, e, a, b);
+    ft += a;
+    fm += b;
   }
   out->flops_trace = ft;
   out->flops_main = fm;

@@ -180,3 +180,48 @@ def test_autotuned_tiles_keep_parity(pkg, name):
         assert [b > 0 for b in before["epb_by_order"]] == [a > 0 for a in after["epb_by_order"]]
         y = op.apply(torch.tensor(x, device="cuda", dtype=dt)).double().cpu().numpy()
         assert rel(y, A @ x) <= tol
+
+
+@pytest.mark.parametrize("name", ["2d_rot_jitter_p1to8", "3d_rot_jitter_p1to5", "c2_2d_64x64_jitter_p2to6"])
+def test_tilings_give_identical_results(pkg, name):
+    """Each element's arithmetic does not depend on how elements are grouped in
+    tiles: every tiling gives the same bits (and, on the small meshes, parity)."""
+    import torch
+    small = name in MESHES
+    m = MESHES[name] if small else si.workload(name)
+    A = SipOracle(m).assemble() if small else None
+    op = pkg.SipOperator.from_mesh(m)
+    x = si.random_vector(op.ndof, 0)
+    P1 = pkg._lib.SIP_MAX_ORDER + 1
+    for prec, dt, tol in ((pkg.SIP_FP64, torch.float64, TOL64), (pkg.SIP_FP32, torch.float32, TOL32)):
+        xt = torch.tensor(x, device="cuda", dtype=dt)
+        ref = op.apply(xt)
+        if small:
+            assert rel(ref.double().cpu().numpy(), A @ x) <= tol
+        ntiles = set()
+        big = 32 if m.dim == 2 else 4
+        for epb, per_sm in (([1] * P1, 0), ([big] * P1, 0), ([big] * P1, 1), (None, 1), (None, 3), ([2] * P1, 8)):
+            info = op.set_tiling(prec, epb, per_sm)
+            assert 1 <= info["nctas"] <= len(m.orders) and info["ctas_per_sm"] >= 1
+            if epb is not None and epb[0] == 1:
+                assert info["ntiles"] == len(m.orders)
+            ntiles.add(info["ntiles"])
+            assert torch.equal(op.apply(xt), ref), (epb, per_sm, info)
+        if not small:
+            assert len(ntiles) >= 3
+        op.set_tiling(prec)  # back to the defaults
+        assert torch.equal(op.apply(xt), ref)
+
+
+def test_set_tiling_rejects_bad_values(pkg):
+    m = MESHES["2d_rot_jitter_p1to8"]
+    op = pkg.SipOperator.from_mesh(m)
+    before = op.tiling(pkg.SIP_FP64)
+    P1 = pkg._lib.SIP_MAX_ORDER + 1
+    with pytest.raises(pkg.SipError):
+        op.set_tiling(pkg.SIP_FP64, [33] * P1, 0)
+    with pytest.raises(pkg.SipError):
+        op.set_tiling(pkg.SIP_FP64, None, -1)
+    with pytest.raises(ValueError):
+        op.set_tiling(pkg.SIP_FP64, [1, 2], 0)
+    assert op.tiling(pkg.SIP_FP64) == before
