@@ -210,19 +210,25 @@ typedef struct sip_work {
 } sip_work;
 int  sip_work_model(const sip_handle* h, int precision, sip_work* out);
 
-/* Launch schedule.  Elements are grouped in tiles of one order, one CTA per
- * tile and right-hand side, at most a set number of elements per tile for each
- * order.  Where that gives fewer tiles than CTAs resident at once, tiles are
- * split further so that there are about (CTAs per SM) x SMs of them, each with
- * the same share of the apply's flops: one wave of equal CTAs keeps every SM
- * busy to the end of the launch, whichever SM each CTA lands on.
+/* Launch schedule.  Elements are grouped in tiles of one order (at most a set
+ * number of elements per tile for each order) and each CTA runs a list of tiles
+ * of one order.  The schedule is balanced for (CTAs per SM) x SMs CTAs resident
+ * at once, using per-element flop counts (sip_work_model's):
+ *  - one tile per CTA: where the tile sizes give fewer tiles than that, tiles are
+ *    split further so that there are about that many, each with the same share
+ *    of the apply's flops: one wave of equal CTAs keeps every SM busy to the end
+ *    of the launch whichever SM each CTA lands on; more tiles run in waves that
+ *    the hardware balances;
+ *  - persistent: exactly that many CTAs (about), each with an equal share of the
+ *    flops cut into tiles that it runs one after the other, the order's tables
+ *    loaded once.
  *
  * Autotuner: coordinate descent over the orders present, timing the whole
  * apply (best of three batches of reps launches) for a few candidate tile sizes
- * of one order at a time, then over the CTAs per SM; installs the fastest for
- * this precision.  Set-up call: allocates temporaries and synchronises the
- * stream.  The paper picks a kernel configuration per order (Sec. 5.1); this
- * chooses it by measurement on the current GPU. */
+ * of one order at a time, then over the CTAs per SM in both modes; installs the
+ * fastest for this precision.  Set-up call: allocates temporaries and
+ * synchronises the stream.  The paper picks a kernel configuration per order
+ * (Sec. 5.1); this chooses it by measurement on the current GPU. */
 int  sip_autotune(sip_handle* h, int precision, int reps, void* stream);
 
 /* Current tiling: epb_out[P] = largest number of elements per tile used for
@@ -231,19 +237,22 @@ int  sip_autotune(sip_handle* h, int precision, int reps, void* stream);
 int  sip_get_tiling(const sip_handle* h, int precision, int32_t* epb_out /* [SIP_MAX_ORDER+1] */,
                     int64_t* ntiles_out);
 
-/* Current launch grid: *nctas_out CTAs (tiles) per right-hand side, balanced
- * for *ctas_per_sm_out resident CTAs per SM. */
-int  sip_get_grid(const sip_handle* h, int precision, int32_t* nctas_out, int32_t* ctas_per_sm_out);
+/* Current launch grid: *nctas_out CTAs per right-hand side, balanced for
+ * *ctas_per_sm_out resident CTAs per SM, *persistent_out = 1 if CTAs run several
+ * tiles each. */
+int  sip_get_grid(const sip_handle* h, int precision, int32_t* nctas_out, int32_t* ctas_per_sm_out,
+                  int32_t* persistent_out);
 
 /* Install a tiling by hand: epb[P] = elements per tile for order P (0: the
  * default; at most 32), P = 0..SIP_MAX_ORDER, or epb = NULL for all defaults;
  * ctas_per_sm = resident CTAs per SM to balance for (0: as many as fit, capped
  * at the number of tiles per SM that epb gives; larger values are capped at the
- * occupancy).  Set-up call: synchronises the device.  Errors: SIP_ERR_ARG for an
+ * occupancy); persistent != 0 selects persistent CTAs.  Set-up call:
+ * synchronises the device.  Errors: SIP_ERR_ARG for an
  * out-of-range value or a tile too large for shared memory (the previous tiling
  * stays). */
 int  sip_set_tiling(sip_handle* h, int precision, const int32_t* epb /* [SIP_MAX_ORDER+1] */,
-                    int32_t ctas_per_sm);
+                    int32_t ctas_per_sm, int32_t persistent);
 
 /* Device time of the last apply's kernels, per phase, measured with CUDA events
  * on the apply's stream when timing is enabled (sip_set_timing(h, 1)); ms. */

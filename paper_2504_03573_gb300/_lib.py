@@ -116,8 +116,8 @@ SIGNATURES = {
     "sip_last_kernel_ms": (_I, [_H, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "sip_autotune": (_I, [_H, _I, _I, _P]),
     "sip_get_tiling": (_I, [_H, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
-    "sip_get_grid": (_I, [_H, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
-    "sip_set_tiling": (_I, [_H, _I, C.POINTER(C.c_int32), C.c_int32]),
+    "sip_get_grid": (_I, [_H, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "sip_set_tiling": (_I, [_H, _I, C.POINTER(C.c_int32), C.c_int32, C.c_int32]),
     "sip_apply_static_scratch": (_I, [_H, _I, _P, _P, _I, _P]),
     "sip_last_error": (C.c_char_p, []),
 }

@@ -372,7 +372,7 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
   constexpr int PER = S::PER_TRACE;
   const int ne = t.count;
   load_meta<DIM>(a.elist, a.slots, a.eaff, t, mt);
-  load_tables<T, N>(tb);
+  __syncthreads();
   // one output per thread (2D, and FP64 in 3D: more parallel work for the narrow
   // FP64 pipe) or one line per thread with the matrices as constant-bank operands
   // (FP32 in 3D: fewer instructions per FMA)
@@ -559,7 +559,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   T* R = sm + (1 + DIM) * QV;
   T* const F0 = sm + (2 + DIM) * QV;
   load_meta<DIM>(a.elist, a.slots, a.eaff, t, mt);
-  load_tables<T, N>(tb);
+  __syncthreads();
   if (a.ug) {
     for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
       const int el = w / QV, q = w - el * QV;
@@ -773,7 +773,9 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
 }
 
 // Shared memory of a CTA: [table block of its order (table_block_bytes)][TileMeta
-// (kMetaBytes)][elements].
+// (kMetaBytes)][elements].  A CTA runs a list of tiles of one order (its share
+// of the launch, tiles cta_off[b] .. cta_off[b+1]-1) one after the other, with the
+// order's tables loaded once.
 #define SIP_ORDER_SWITCH(FN) \
   switch (t.n) {             \
     case 2: FN(2); break;    \
@@ -787,15 +789,27 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
     default: break;          \
   }
 
+template <typename T, int DIM, int N, bool MAIN>
+__device__ __forceinline__ void run_tiles(const ApplyArgs<T>& a, int ti0, int ti1, int rhs, unsigned char* smem_raw) {
+  T* tb = reinterpret_cast<T*>(smem_raw);
+  TileMeta* mt = reinterpret_cast<TileMeta*>(smem_raw + table_block_bytes(sizeof(T), N));
+  T* sm = reinterpret_cast<T*>(smem_raw + table_block_bytes(sizeof(T), N) + kMetaBytes);
+  load_tables<T, N>(tb);
+  for (int ti = ti0; ti < ti1; ++ti) {
+    if (ti > ti0) __syncthreads();  // the previous tile's last stage still reads shared memory
+    const Tile t = a.tiles[ti];
+    if constexpr (MAIN) main_tile<T, DIM, N>(a, t, rhs, tb, mt, sm);
+    else trace_tile<T, DIM, N>(a, t, rhs, tb, mt, sm);
+  }
+}
+
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_trace(ApplyArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Tile t = a.tiles[blockIdx.x];
-  const int rhs = blockIdx.y;
-  T* tb = reinterpret_cast<T*>(smem_raw);
-#define SIP_TRACE_CASE(NN)                                                                              \
-  trace_tile<T, DIM, NN>(a, t, rhs, tb, reinterpret_cast<TileMeta*>(smem_raw + table_block_bytes(sizeof(T), NN)), \
-                         reinterpret_cast<T*>(smem_raw + table_block_bytes(sizeof(T), NN) + kMetaBytes))
+  const int ti0 = a.cta_off[blockIdx.x], ti1 = a.cta_off[blockIdx.x + 1];
+  if (ti0 >= ti1) return;
+  const Tile t = a.tiles[ti0];  // every tile of the CTA has this order
+#define SIP_TRACE_CASE(NN) run_tiles<T, DIM, NN, false>(a, ti0, ti1, blockIdx.y, smem_raw)
   SIP_ORDER_SWITCH(SIP_TRACE_CASE)
 #undef SIP_TRACE_CASE
 }
@@ -803,12 +817,10 @@ __global__ void __launch_bounds__(256) k_trace(ApplyArgs<T> a) {
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_main(ApplyArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Tile t = a.tiles[blockIdx.x];
-  const int rhs = blockIdx.y;
-  T* tb = reinterpret_cast<T*>(smem_raw);
-#define SIP_MAIN_CASE(NN)                                                                              \
-  main_tile<T, DIM, NN>(a, t, rhs, tb, reinterpret_cast<TileMeta*>(smem_raw + table_block_bytes(sizeof(T), NN)), \
-                        reinterpret_cast<T*>(smem_raw + table_block_bytes(sizeof(T), NN) + kMetaBytes))
+  const int ti0 = a.cta_off[blockIdx.x], ti1 = a.cta_off[blockIdx.x + 1];
+  if (ti0 >= ti1) return;
+  const Tile t = a.tiles[ti0];
+#define SIP_MAIN_CASE(NN) run_tiles<T, DIM, NN, true>(a, ti0, ti1, blockIdx.y, smem_raw)
   SIP_ORDER_SWITCH(SIP_MAIN_CASE)
 #undef SIP_MAIN_CASE
 }

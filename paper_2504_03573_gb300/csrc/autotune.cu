@@ -51,18 +51,21 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
   for (int n : orders) cur[n] = apply_epb(p.dim, n, precision);
   const bool timing = h->timing;
   h->timing = false;
-  auto time_full = [&](const int* epb, int per_sm, float* ms_out, int* per_sm_out) -> int {
+  auto time_full = [&](const int* epb, int per_sm, bool pers, float* ms_out, int* per_sm_out) -> int {
     Schedule sc;
-    int r2 = make_schedule(h, precision, epb, per_sm, sc);
+    int r2 = make_schedule(h, precision, epb, per_sm, pers, sc);
     if (r2 == SIP_ERR_ARG) { *ms_out = 1e30f; return SIP_OK; }  // tile too large for shared memory
     if (r2) return r2;
     if (per_sm_out) *per_sm_out = sc.per_sm;
     Tile* td = nullptr;
+    int32_t* cd = nullptr;
     cudaError_t ee = cudaMalloc((void**)&td, std::max<size_t>(16, sc.tiles.size() * sizeof(Tile)));
+    if (ee == cudaSuccess) ee = cudaMalloc((void**)&cd, sc.cta_off.size() * sizeof(int32_t));
     if (ee == cudaSuccess) ee = cudaMemcpy(td, sc.tiles.data(), sc.tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
-    if (ee != cudaSuccess) { cudaFree(td); return cuda_fail(ee, "autotune tiles"); }
+    if (ee == cudaSuccess) ee = cudaMemcpy(cd, sc.cta_off.data(), sc.cta_off.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (ee != cudaSuccess) { cudaFree(td); cudaFree(cd); return cuda_fail(ee, "autotune tiles"); }
     auto run = [&]() {
-      return apply_tiles(h, precision, td, (int)sc.tiles.size(), sc.smem_t, sc.smem_m, x, y, 1, s, 0, nullptr);
+      return apply_tiles(h, precision, td, cd, sc.nctas(), sc.smem_t, sc.smem_m, x, y, 1, s, 0, nullptr);
     };
     for (int w = 0; w < 2 && r2 == SIP_OK; ++w) r2 = run();
     // best of three batches of reps launches
@@ -78,12 +81,14 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
       best = std::min(best, ms);
     }
     cudaFree(td);
+    cudaFree(cd);
     *ms_out = best;
     return r2;
   };
   float cur_ms = 1e30f;
   int cur_per_sm = 0, auto_per_sm = 0;
-  rc = time_full(cur, 0, &cur_ms, &auto_per_sm);
+  bool cur_pers = false;
+  rc = time_full(cur, 0, false, &cur_ms, &auto_per_sm);
   for (int n : orders) {
     if (rc) break;
     const int base = cur[n];
@@ -97,7 +102,7 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
       std::memcpy(trial, cur, sizeof(trial));
       trial[n] = c;
       float ms = 0.0f;
-      rc = time_full(trial, 0, &ms, nullptr);
+      rc = time_full(trial, 0, false, &ms, nullptr);
       if (rc) break;
       if (ms < 0.97f * cur_ms) {  // keep a change only for a clear gain
         cur_ms = ms;
@@ -105,18 +110,21 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
       }
     }
   }
-  // then the number of resident CTAs per SM the schedule is balanced for
-  for (int ps = 1; ps <= 8 && rc == SIP_OK; ++ps) {
-    if (ps == auto_per_sm) continue;
-    float ms = 0.0f;
-    int got = 0;
-    rc = time_full(cur, ps, &ms, &got);
-    if (rc || got != ps) break;  // beyond the occupancy
-    if (ms < 0.97f * cur_ms) {
-      cur_ms = ms;
-      cur_per_sm = ps;
+  // then the resident CTAs per SM the schedule is balanced for, with one tile
+  // per CTA or with persistent CTAs
+  for (int pers = 0; pers < 2 && rc == SIP_OK; ++pers)
+    for (int ps = 1; ps <= 8 && rc == SIP_OK; ++ps) {
+      if (!pers && ps == auto_per_sm) continue;
+      float ms = 0.0f;
+      int got = 0;
+      rc = time_full(cur, ps, pers != 0, &ms, &got);
+      if (rc || got != ps) break;  // beyond the occupancy
+      if (ms < 0.97f * cur_ms) {
+        cur_ms = ms;
+        cur_per_sm = ps;
+        cur_pers = pers != 0;
+      }
     }
-  }
   int* best = cur;
   h->timing = timing;
   cudaEventDestroy(a);
@@ -124,7 +132,7 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
   cudaFree(x);
   cudaFree(y);
   if (rc) return rc;
-  rc = set_tiles(h, precision, best, cur_per_sm);
+  rc = set_tiles(h, precision, best, cur_per_sm, cur_pers);
   if (rc) return rc;
   std::memcpy(h->epb[pi], best, sizeof(cur));
   return SIP_OK;
@@ -139,16 +147,19 @@ extern "C" int sip_get_tiling(const sip_handle* h, int precision, int32_t* epb_o
   return SIP_OK;
 }
 
-extern "C" int sip_get_grid(const sip_handle* h, int precision, int32_t* nctas_out, int32_t* ctas_per_sm_out) {
-  if (!h || !nctas_out || !ctas_per_sm_out) return fail(SIP_ERR_ARG, "null argument");
+extern "C" int sip_get_grid(const sip_handle* h, int precision, int32_t* nctas_out, int32_t* ctas_per_sm_out,
+                            int32_t* persistent_out) {
+  if (!h || !nctas_out || !ctas_per_sm_out || !persistent_out) return fail(SIP_ERR_ARG, "null argument");
   if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
   const int pi = precision == SIP_FP32 ? 1 : 0;
-  *nctas_out = (int32_t)h->tiles_h[pi].size();
+  *nctas_out = (int32_t)h->cta_h[pi].size() - 1;
   *ctas_per_sm_out = h->ctas_per_sm[pi];
+  *persistent_out = h->persistent[pi];
   return SIP_OK;
 }
 
-extern "C" int sip_set_tiling(sip_handle* h, int precision, const int32_t* epb, int32_t ctas_per_sm) {
+extern "C" int sip_set_tiling(sip_handle* h, int precision, const int32_t* epb, int32_t ctas_per_sm,
+                              int32_t persistent) {
   if (!h) return fail(SIP_ERR_ARG, "null handle");
   if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
   if (ctas_per_sm < 0) return fail(SIP_ERR_ARG, "ctas_per_sm must be >= 0");
@@ -159,7 +170,7 @@ extern "C" int sip_set_tiling(sip_handle* h, int precision, const int32_t* epb, 
       e[P + 1] = epb[P];
     }
   const int pi = precision == SIP_FP32 ? 1 : 0;
-  int rc = set_tiles(h, precision, e, ctas_per_sm);
+  int rc = set_tiles(h, precision, e, ctas_per_sm, persistent != 0);
   if (rc) return rc;
   std::memcpy(h->epb[pi], e, sizeof(e));
   return SIP_OK;

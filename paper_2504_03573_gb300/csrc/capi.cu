@@ -141,7 +141,7 @@ size_t apply_scratch_bytes(const sip_handle* h, int precision, int nrhs, size_t*
   return precision == SIP_FP64 ? tr + (size_t)nrhs * (size_t)h->plan.nquad * es : tr;
 }
 
-int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_per_sm, Schedule& s) {
+int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_per_sm, bool persistent, Schedule& s) {
   const Plan& p = h->plan;
   const int es = precision == SIP_FP32 ? 4 : 8;
   auto size_smem = [&]() {
@@ -152,10 +152,12 @@ int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_p
       s.smem_m = std::max(s.smem_m, fixed + (size_t)t.count * per_elem_main(p.dim, t.n) * es);
     }
   };
-  // tiles of the largest size epb allows: their count and shared memory bound the rest
-  build_tiles(p, precision, epb, 0, s.tiles);
+  // one CTA per tile of the largest size epb allows: the tile count and shared
+  // memory bound the rest (a CTA's tiles are never larger)
+  build_tiles(p, precision, epb, 0, false, s.tiles, s.cta_off);
   size_smem();
   s.per_sm = 1;
+  s.persistent = persistent;
   if (s.smem_t > 200 * 1024 || s.smem_m > 200 * 1024) return fail(SIP_ERR_ARG, "tile too large for shared memory");
   const int64_t ntile = (int64_t)s.tiles.size();
   if (ntile == 0) return SIP_OK;
@@ -167,39 +169,46 @@ int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_p
   if (e != cudaSuccess) return cuda_fail(e, "occupancy");
   occ = std::max(1, occ);
   nsm = std::max(1, nsm);
-  // at least per_sm x SMs tiles of equal flops (tiles only get smaller than the
-  // bound above, so the shared memory and the occupancy hold)
+  // per_sm x SMs CTAs of equal flops, all resident at once
   const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ)
                                      : (int)std::min<int64_t>(occ, std::max<int64_t>(1, ntile / nsm));
-  build_tiles(p, precision, epb, nsm * per_sm, s.tiles);
+  build_tiles(p, precision, epb, nsm * per_sm, persistent, s.tiles, s.cta_off);
   size_smem();
   s.per_sm = per_sm;
   return SIP_OK;
 }
 
-// (Re)build the tiles of one precision (epb_by_n[n] > 0 overrides the default
+// (Re)build the schedule of one precision (epb_by_n[n] > 0 overrides the default
 // elements per tile for order n - 1; ctas_per_sm > 0 fixes the resident CTAs per
-// SM the tiles are balanced for), upload them and size the shared memory.
-int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm) {
+// SM it is balanced for), upload it and size the shared memory.
+int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm, bool persistent) {
   const int pi = precision == SIP_FP32 ? 1 : 0;
   Schedule sc;
-  int rc = make_schedule(h, precision, epb_by_n, ctas_per_sm, sc);
+  int rc = make_schedule(h, precision, epb_by_n, ctas_per_sm, persistent, sc);
   if (rc) return rc;
   Tile* d = nullptr;
+  int32_t* c = nullptr;
   cudaError_t e = cudaMalloc((void**)&d, std::max<size_t>(16, sc.tiles.size() * sizeof(Tile)));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c, sc.cta_off.size() * sizeof(int32_t));
   if (e == cudaSuccess && !sc.tiles.empty())
     e = cudaMemcpy(d, sc.tiles.data(), sc.tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c, sc.cta_off.data(), sc.cta_off.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(d);
+    cudaFree(c);
     return cuda_fail(e, "tiles");
   }
-  if (h->tiles_d[pi]) {
-    cudaDeviceSynchronize();  // earlier launches may still read the old tiles
+  if (h->tiles_d[pi] || h->cta_d[pi]) {
+    cudaDeviceSynchronize();  // earlier launches may still read the old schedule
     cudaFree(h->tiles_d[pi]);
+    cudaFree(h->cta_d[pi]);
   }
   h->tiles_d[pi] = d;
+  h->cta_d[pi] = c;
   h->tiles_h[pi] = std::move(sc.tiles);
+  h->cta_h[pi] = std::move(sc.cta_off);
   h->ctas_per_sm[pi] = sc.per_sm;
+  h->persistent[pi] = sc.persistent ? 1 : 0;
   h->smem_trace[pi] = sc.smem_t;
   h->smem_main[pi] = sc.smem_m;
   for (auto* W : {&h->cg64, &h->cg32})
@@ -224,6 +233,7 @@ ApplyArgs<T> make_args(sip_handle* h, const T* x, T* y, T* trace, T* ug, int tra
   a.elist = h->elist;
   a.eaff = h->eaff;
   a.tiles = h->tiles_d[std::is_same<T, float>::value ? 1 : 0];
+  a.cta_off = h->cta_d[std::is_same<T, float>::value ? 1 : 0];
   a.x = x;
   a.y = y;
   a.trace = trace;
@@ -236,8 +246,9 @@ ApplyArgs<T> make_args(sip_handle* h, const T* x, T* y, T* trace, T* ug, int tra
   return a;
 }
 
-int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, int ntiles, size_t smem_t, size_t smem_m,
-                const void* x, void* y, int nrhs, cudaStream_t s, int transpose, void* scratch_override) {
+int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t* cta_d, int nctas, size_t smem_t,
+                size_t smem_m, const void* x, void* y, int nrhs, cudaStream_t s, int transpose,
+                void* scratch_override) {
   size_t ug_off = 0;
   apply_scratch_bytes(h, precision, nrhs, &ug_off);
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
@@ -248,14 +259,16 @@ int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, int ntiles, s
     double* ug = scratch_override ? (double*)((char*)scratch_override + ug_off) : h->ug_d;
     auto a = make_args<double>(h, (const double*)x, (double*)y, tr, ug, transpose);
     a.tiles = tiles_d;
-    e = h->plan.dim == 2 ? launch_apply_2d_f64(a, ntiles, nrhs, smem_t, smem_m, s, e0, e1, e2)
-                         : launch_apply_3d_f64(a, ntiles, nrhs, smem_t, smem_m, s, e0, e1, e2);
+    a.cta_off = cta_d;
+    e = h->plan.dim == 2 ? launch_apply_2d_f64(a, nctas, nrhs, smem_t, smem_m, s, e0, e1, e2)
+                         : launch_apply_3d_f64(a, nctas, nrhs, smem_t, smem_m, s, e0, e1, e2);
   } else {
     float* tr = scratch_override ? (float*)scratch_override : (float*)h->trace_d;
     auto a = make_args<float>(h, (const float*)x, (float*)y, tr, nullptr, transpose);
     a.tiles = tiles_d;
-    e = h->plan.dim == 2 ? launch_apply_2d_f32(a, ntiles, nrhs, smem_t, smem_m, s, e0, e1, e2)
-                         : launch_apply_3d_f32(a, ntiles, nrhs, smem_t, smem_m, s, e0, e1, e2);
+    a.cta_off = cta_d;
+    e = h->plan.dim == 2 ? launch_apply_2d_f32(a, nctas, nrhs, smem_t, smem_m, s, e0, e1, e2)
+                         : launch_apply_3d_f32(a, nctas, nrhs, smem_t, smem_m, s, e0, e1, e2);
   }
   if (e != cudaSuccess) return cuda_fail(e, "apply launch");
   h->timed_pending = h->timing;
@@ -272,8 +285,8 @@ int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cu
     if (rc) return rc;
   }
   const int pi = precision == SIP_FP32 ? 1 : 0;
-  return apply_tiles(h, precision, h->tiles_d[pi], (int)h->tiles_h[pi].size(), h->smem_trace[pi], h->smem_main[pi],
-                     x, y, nrhs, s, transpose, scratch_override);
+  return apply_tiles(h, precision, h->tiles_d[pi], h->cta_d[pi], (int)h->cta_h[pi].size() - 1, h->smem_trace[pi],
+                     h->smem_main[pi], x, y, nrhs, s, transpose, scratch_override);
 }
 
 }  // namespace sip
@@ -405,7 +418,7 @@ int sip_create(const sip_mesh* mesh, const int32_t* orders, double lambda, const
     return rc;
   }
   for (int prec : {SIP_FP64, SIP_FP32}) {
-    rc = set_tiles(h, prec, nullptr, 0);
+    rc = set_tiles(h, prec, nullptr, 0, false);
     if (rc) { sip_destroy(h); return rc; }
   }
   rc = handle_grow_trace(h, 1);

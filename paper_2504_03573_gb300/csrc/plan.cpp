@@ -519,13 +519,20 @@ Tile make_tile(const Plan& p, int n, int64_t s0, int64_t s1) {
 
 }  // namespace
 
-// Tiles of one order each, cut from the order-sorted element list: a run of cnt
-// elements of order n - 1 (flops C_n of the apply's C in all) is spread evenly
-// over k_n = max(ceil(cnt / epb(n)), round(ntarget C_n / C)) tiles, at most cnt.
-// With ntarget = the CTAs resident at once, every tile that is not capped by
-// epb carries the same flops, so one wave of CTAs keeps every SM busy to the end.
-void build_tiles(const Plan& p, int precision, const int* epb_override, int ntarget, std::vector<Tile>& tiles) {
+// Tiles cut from the order-sorted element list, and the CTA that runs each.  A
+// run of cnt elements of one order, whose flops are C_n of the apply's C:
+//  * nctas <= 0: ceil(cnt / epb) tiles of equal size, one CTA each;
+//  * persistent = false: max(ceil(cnt / epb), round(nctas C_n / C)) tiles, one CTA
+//    each: with nctas = the CTAs resident at once, every tile not capped by epb
+//    carries the same flops, so one wave of CTAs keeps every SM busy to the end
+//    (larger meshes get more tiles than that and the hardware balances the waves);
+//  * persistent = true: k_n = round(nctas C_n / C) CTAs (1 .. cnt), each an equal
+//    share of the run cut into tiles of at most epb elements and run one after
+//    the other.
+void build_tiles(const Plan& p, int precision, const int* epb_override, int nctas, bool persistent,
+                 std::vector<Tile>& tiles, std::vector<int32_t>& cta_off) {
   tiles.clear();
+  cta_off.assign(1, 0);
   const int64_t E = p.E;
   double C = 0.0;
   std::vector<double> ce(E);
@@ -543,11 +550,17 @@ void build_tiles(const Plan& p, int precision, const int* epb_override, int ntar
     int epb = epb_override && epb_override[n] > 0 ? epb_override[n] : apply_epb(p.dim, n, precision);
     epb = std::max(1, std::min(epb, kMaxEpb));
     const int64_t cnt = j - i;
-    int64_t ntile = (cnt + epb - 1) / epb;
-    if (ntarget > 0 && C > 0.0) ntile = std::max<int64_t>(ntile, std::llround(ntarget * Cn / C));
-    ntile = std::min(ntile, cnt);
-    for (int64_t k = 0; k < ntile; ++k)
-      tiles.push_back(make_tile(p, n, i + (cnt * k) / ntile, i + (cnt * (k + 1)) / ntile));
+    const int64_t share = nctas > 0 ? std::max<int64_t>(1, std::llround(nctas * Cn / C)) : 0;
+    // CTAs of this run and tiles per CTA
+    int64_t kc = (cnt + epb - 1) / epb;
+    if (nctas > 0) kc = persistent ? share : std::max(kc, share);
+    kc = std::min(kc, cnt);
+    for (int64_t c = 0; c < kc; ++c) {
+      const int64_t r0 = i + (cnt * c) / kc, r1 = i + (cnt * (c + 1)) / kc;
+      const int64_t m = r1 - r0, nt = (m + epb - 1) / epb;
+      for (int64_t k = 0; k < nt; ++k) tiles.push_back(make_tile(p, n, r0 + (m * k) / nt, r0 + (m * (k + 1)) / nt));
+      cta_off.push_back((int32_t)tiles.size());
+    }
     i = j;
   }
 }

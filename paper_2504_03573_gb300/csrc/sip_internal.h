@@ -179,9 +179,11 @@ double lagrange_deriv(const std::vector<double>& nodes, int j, double x);
 void fill_tables(std::vector<double>& tab);
 
 // elements per tile for the apply kernels (host choice), per-element flops, and
-// the tiles (at least about ntarget of them, of equal flops, where ntarget > 0)
+// the tiles with the CTA that runs each (tiles cta_off[b] .. cta_off[b+1]-1, one
+// order per CTA)
 int apply_epb(int dim, int n, int precision);
 void element_flops(const Plan& p, int64_t e, double& ft, double& fm);
-void build_tiles(const Plan& p, int precision, const int* epb_override, int ntarget, std::vector<Tile>& tiles);
+void build_tiles(const Plan& p, int precision, const int* epb_override, int nctas, bool persistent,
+                 std::vector<Tile>& tiles, std::vector<int32_t>& cta_off);
 
 }  // namespace sip

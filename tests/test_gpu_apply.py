@@ -200,13 +200,17 @@ def test_tilings_give_identical_results(pkg, name):
             assert rel(ref.double().cpu().numpy(), A @ x) <= tol
         ntiles = set()
         big = 32 if m.dim == 2 else 4
-        for epb, per_sm in (([1] * P1, 0), ([big] * P1, 0), ([big] * P1, 1), (None, 1), (None, 3), ([2] * P1, 8)):
-            info = op.set_tiling(prec, epb, per_sm)
+        for epb, per_sm, pers in (([1] * P1, 0, False), ([big] * P1, 0, False), ([big] * P1, 1, True), (None, 1, False),
+                                  (None, 3, True), ([2] * P1, 8, True), ([2] * P1, 8, False)):
+            info = op.set_tiling(prec, epb, per_sm, pers)
+            assert info["persistent"] == pers
             assert 1 <= info["nctas"] <= len(m.orders) and info["ctas_per_sm"] >= 1
             if epb is not None and epb[0] == 1:
                 assert info["ntiles"] == len(m.orders)
+            if not pers:
+                assert info["nctas"] == info["ntiles"]
             ntiles.add(info["ntiles"])
-            assert torch.equal(op.apply(xt), ref), (epb, per_sm, info)
+            assert torch.equal(op.apply(xt), ref), (epb, per_sm, pers, info)
         if not small:
             assert len(ntiles) >= 3
         op.set_tiling(prec)  # back to the defaults
