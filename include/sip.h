@@ -225,34 +225,33 @@ int  sip_work_model(const sip_handle* h, int precision, sip_work* out);
  *
  * Autotuner: coordinate descent over the orders present, timing the whole
  * apply (best of three batches of reps launches) for a few candidate tile sizes
- * of one order at a time, then over the CTAs per SM in both modes; installs the
- * fastest for this precision.  Set-up call: allocates temporaries and
+ * of one order at a time, then over the threads per CTA and the CTAs per SM in
+ * both modes; installs the fastest for this precision.  Set-up call: allocates temporaries and
  * synchronises the stream.  The paper picks a kernel configuration per order
  * (Sec. 5.1); this chooses it by measurement on the current GPU. */
 int  sip_autotune(sip_handle* h, int precision, int reps, void* stream);
 
-/* Current tiling: epb_out[P] = largest number of elements per tile used for
- * order P (0 if the order is absent), P = 0..SIP_MAX_ORDER; *ntiles_out = tiles
- * per apply (may be NULL). */
-int  sip_get_tiling(const sip_handle* h, int precision, int32_t* epb_out /* [SIP_MAX_ORDER+1] */,
-                    int64_t* ntiles_out);
+/* A launch schedule of the apply kernels. */
+typedef struct sip_tiling {
+    int32_t epb[SIP_MAX_ORDER + 1]; /* largest elements per tile for order P, P = 0..SIP_MAX_ORDER
+                                       (set: 0 = the default for the order, at most 32;
+                                       get: 0 where the order is absent) */
+    int32_t ctas_per_sm;            /* resident CTAs per SM balanced for (set: 0 = as many as
+                                       fit, at most the tiles per SM that epb gives; larger
+                                       values are capped at the occupancy) */
+    int32_t persistent;             /* 1: each CTA runs several tiles */
+    int32_t threads;                /* threads per CTA: 64, 128 or 256 (set: 0 = 256) */
+    int64_t ntiles, nctas;          /* get only: tiles and CTAs per right-hand side */
+} sip_tiling;
 
-/* Current launch grid: *nctas_out CTAs per right-hand side, balanced for
- * *ctas_per_sm_out resident CTAs per SM, *persistent_out = 1 if CTAs run several
- * tiles each. */
-int  sip_get_grid(const sip_handle* h, int precision, int32_t* nctas_out, int32_t* ctas_per_sm_out,
-                  int32_t* persistent_out);
+/* Current schedule of one precision. */
+int  sip_get_tiling(const sip_handle* h, int precision, sip_tiling* out);
 
-/* Install a tiling by hand: epb[P] = elements per tile for order P (0: the
- * default; at most 32), P = 0..SIP_MAX_ORDER, or epb = NULL for all defaults;
- * ctas_per_sm = resident CTAs per SM to balance for (0: as many as fit, capped
- * at the number of tiles per SM that epb gives; larger values are capped at the
- * occupancy); persistent != 0 selects persistent CTAs.  Set-up call:
- * synchronises the device.  Errors: SIP_ERR_ARG for an
- * out-of-range value or a tile too large for shared memory (the previous tiling
- * stays). */
-int  sip_set_tiling(sip_handle* h, int precision, const int32_t* epb /* [SIP_MAX_ORDER+1] */,
-                    int32_t ctas_per_sm, int32_t persistent);
+/* Install a schedule by hand (t = NULL: all defaults); ntiles and nctas are
+ * ignored.  Set-up call: synchronises the device.  Errors: SIP_ERR_ARG for an
+ * out-of-range value or a tile too large for shared memory (the previous
+ * schedule stays). */
+int  sip_set_tiling(sip_handle* h, int precision, const sip_tiling* t);
 
 /* Device time of the last apply's kernels, per phase, measured with CUDA events
  * on the apply's stream when timing is enabled (sip_set_timing(h, 1)); ms. */

@@ -223,24 +223,25 @@ class SipOperator:
         return self.tiling(precision)
 
     def tiling(self, precision=SIP_FP64):
-        epb = (C.c_int32 * (_lib.SIP_MAX_ORDER + 1))()
-        nt = C.c_int64()
-        check(lib.sip_get_tiling(self._h, precision, epb, C.byref(nt)))
-        nc, ps, pe = C.c_int32(), C.c_int32(), C.c_int32()
-        check(lib.sip_get_grid(self._h, precision, C.byref(nc), C.byref(ps), C.byref(pe)))
-        return {"epb_by_order": list(epb), "ntiles": nt.value, "nctas": nc.value, "ctas_per_sm": ps.value,
-                "persistent": bool(pe.value)}
+        t = _lib.sip_tiling()
+        check(lib.sip_get_tiling(self._h, precision, C.byref(t)))
+        return {"epb_by_order": list(t.epb), "ntiles": t.ntiles, "nctas": t.nctas, "ctas_per_sm": t.ctas_per_sm,
+                "persistent": bool(t.persistent), "threads": t.threads}
 
-    def set_tiling(self, precision=SIP_FP64, epb_by_order=None, ctas_per_sm=0, persistent=False):
+    def set_tiling(self, precision=SIP_FP64, epb_by_order=None, ctas_per_sm=0, persistent=False, threads=256):
         """Install elements per tile by order (None or 0 entries: default), the
-        CTAs per SM the schedule is balanced for (0: automatic) and whether CTAs
-        run several tiles each."""
-        arr = None
+        CTAs per SM the schedule is balanced for (0: automatic), whether CTAs run
+        several tiles each, and the threads per CTA (64, 128 or 256)."""
+        t = _lib.sip_tiling()
         if epb_by_order is not None:
             if len(epb_by_order) != _lib.SIP_MAX_ORDER + 1:
                 raise ValueError("epb_by_order needs one entry per order 0..%d" % _lib.SIP_MAX_ORDER)
-            arr = (C.c_int32 * (_lib.SIP_MAX_ORDER + 1))(*[int(v) for v in epb_by_order])
-        check(lib.sip_set_tiling(self._h, precision, arr, int(ctas_per_sm), int(bool(persistent))))
+            for i, v in enumerate(epb_by_order):
+                t.epb[i] = int(v)
+        t.ctas_per_sm = int(ctas_per_sm)
+        t.persistent = int(bool(persistent))
+        t.threads = int(threads)
+        check(lib.sip_set_tiling(self._h, precision, C.byref(t)))
         return self.tiling(precision)
 
     # ---- timing of the apply kernels

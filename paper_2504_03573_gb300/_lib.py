@@ -72,6 +72,11 @@ class sip_plan_info(C.Structure):
         return d
 
 
+class sip_tiling(C.Structure):
+    _fields_ = [("epb", C.c_int32 * (SIP_MAX_ORDER + 1)), ("ctas_per_sm", C.c_int32), ("persistent", C.c_int32),
+                ("threads", C.c_int32), ("ntiles", C.c_int64), ("nctas", C.c_int64)]
+
+
 class sip_work(C.Structure):
     _fields_ = [("flops_trace", C.c_double), ("flops_main", C.c_double), ("bytes_x", C.c_double),
                 ("bytes_y", C.c_double), ("bytes_geometry", C.c_double), ("bytes_trace", C.c_double)]
@@ -115,9 +120,8 @@ SIGNATURES = {
     "sip_set_timing": (_I, [_H, _I]),
     "sip_last_kernel_ms": (_I, [_H, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "sip_autotune": (_I, [_H, _I, _I, _P]),
-    "sip_get_tiling": (_I, [_H, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
-    "sip_get_grid": (_I, [_H, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
-    "sip_set_tiling": (_I, [_H, _I, C.POINTER(C.c_int32), C.c_int32, C.c_int32]),
+    "sip_get_tiling": (_I, [_H, _I, C.POINTER(sip_tiling)]),
+    "sip_set_tiling": (_I, [_H, _I, C.POINTER(sip_tiling)]),
     "sip_apply_static_scratch": (_I, [_H, _I, _P, _P, _I, _P]),
     "sip_last_error": (C.c_char_p, []),
 }

@@ -26,24 +26,24 @@
     return cudaFuncSetAttribute(k_main<TYPE, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                 200 * 1024);                                                      \
   }                                                                                               \
-  cudaError_t occupancy_##SUFFIX(size_t smem_trace, size_t smem_main, int* blocks) {              \
+  cudaError_t occupancy_##SUFFIX(int threads, size_t smem_trace, size_t smem_main, int* blocks) { \
     int bt = 0, bm = 0;                                                                           \
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bt, k_trace<TYPE, DIM>, 256,   \
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bt, k_trace<TYPE, DIM>, threads, \
                                                                   smem_trace);                    \
     if (e != cudaSuccess) return e;                                                               \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, k_main<TYPE, DIM>, 256, smem_main);    \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, k_main<TYPE, DIM>, threads, smem_main); \
     *blocks = bt < bm ? bt : bm;                                                                  \
     return e;                                                                                     \
   }                                                                                               \
-  cudaError_t launch_apply_##SUFFIX(const ApplyArgs<TYPE>& a, int nctas, int nrhs,                \
+  cudaError_t launch_apply_##SUFFIX(const ApplyArgs<TYPE>& a, int nctas, int nrhs, int threads,   \
                                     size_t smem_trace, size_t smem_main, cudaStream_t s,          \
                                     cudaEvent_t ev0, cudaEvent_t ev1, cudaEvent_t ev2) {          \
     if (nctas == 0) return cudaSuccess;                                                           \
     dim3 grid(nctas, nrhs);                                                                       \
     if (ev0) cudaEventRecord(ev0, s);                                                             \
-    k_trace<TYPE, DIM><<<grid, 256, smem_trace, s>>>(a);                                          \
+    k_trace<TYPE, DIM><<<grid, threads, smem_trace, s>>>(a);                                      \
     if (ev1) cudaEventRecord(ev1, s);                                                             \
-    k_main<TYPE, DIM><<<grid, 256, smem_main, s>>>(a);                                            \
+    k_main<TYPE, DIM><<<grid, threads, smem_main, s>>>(a);                                        \
     if (ev2) cudaEventRecord(ev2, s);                                                             \
     return cudaGetLastError();                                                                    \
   }                                                                                               \

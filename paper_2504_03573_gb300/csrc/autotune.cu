@@ -48,12 +48,12 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
   // coordinate descent over the orders, each candidate timed on the full apply
   // (all buckets in one launch, as the solver runs it)
   int cur[kNMax + 2] = {};
-  for (int n : orders) cur[n] = apply_epb(p.dim, n, precision);
+  for (int n : orders) cur[n] = apply_epb(p.dim, n, precision, 256);
   const bool timing = h->timing;
   h->timing = false;
-  auto time_full = [&](const int* epb, int per_sm, bool pers, float* ms_out, int* per_sm_out) -> int {
+  auto time_full = [&](const int* epb, int per_sm, bool pers, int threads, float* ms_out, int* per_sm_out) -> int {
     Schedule sc;
-    int r2 = make_schedule(h, precision, epb, per_sm, pers, sc);
+    int r2 = make_schedule(h, precision, epb, per_sm, pers, threads, sc);
     if (r2 == SIP_ERR_ARG) { *ms_out = 1e30f; return SIP_OK; }  // tile too large for shared memory
     if (r2) return r2;
     if (per_sm_out) *per_sm_out = sc.per_sm;
@@ -65,7 +65,7 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
     if (ee == cudaSuccess) ee = cudaMemcpy(cd, sc.cta_off.data(), sc.cta_off.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (ee != cudaSuccess) { cudaFree(td); cudaFree(cd); return cuda_fail(ee, "autotune tiles"); }
     auto run = [&]() {
-      return apply_tiles(h, precision, td, cd, sc.nctas(), sc.smem_t, sc.smem_m, x, y, 1, s, 0, nullptr);
+      return apply_tiles(h, precision, td, cd, sc.nctas(), sc.threads, sc.smem_t, sc.smem_m, x, y, 1, s, 0, nullptr);
     };
     for (int w = 0; w < 2 && r2 == SIP_OK; ++w) r2 = run();
     // best of three batches of reps launches
@@ -86,9 +86,10 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
     return r2;
   };
   float cur_ms = 1e30f;
-  int cur_per_sm = 0, auto_per_sm = 0;
+  int cur_per_sm = 0, auto_per_sm = 0, cur_threads = 256;
   bool cur_pers = false;
-  rc = time_full(cur, 0, false, &cur_ms, &auto_per_sm);
+  rc = time_full(cur, 0, false, 256, &cur_ms, &auto_per_sm);
+  // 1. elements per tile, one order at a time (256 threads, default grid)
   for (int n : orders) {
     if (rc) break;
     const int base = cur[n];
@@ -102,7 +103,7 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
       std::memcpy(trial, cur, sizeof(trial));
       trial[n] = c;
       float ms = 0.0f;
-      rc = time_full(trial, 0, false, &ms, nullptr);
+      rc = time_full(trial, 0, false, 256, &ms, nullptr);
       if (rc) break;
       if (ms < 0.97f * cur_ms) {  // keep a change only for a clear gain
         cur_ms = ms;
@@ -110,67 +111,76 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
       }
     }
   }
-  // then the resident CTAs per SM the schedule is balanced for, with one tile
-  // per CTA or with persistent CTAs
-  for (int pers = 0; pers < 2 && rc == SIP_OK; ++pers)
-    for (int ps = 1; ps <= 8 && rc == SIP_OK; ++ps) {
-      if (!pers && ps == auto_per_sm) continue;
-      float ms = 0.0f;
-      int got = 0;
-      rc = time_full(cur, ps, pers != 0, &ms, &got);
-      if (rc || got != ps) break;  // beyond the occupancy
-      if (ms < 0.97f * cur_ms) {
-        cur_ms = ms;
-        cur_per_sm = ps;
-        cur_pers = pers != 0;
+  // 2. threads per CTA (tiles scaled with them), then the resident CTAs per SM
+  //    the schedule is balanced for, with one tile per CTA or persistent CTAs
+  int best_epb[kNMax + 2];
+  std::memcpy(best_epb, cur, sizeof(cur));
+  for (int threads : {256, 128, 64}) {
+    int scaled[kNMax + 2] = {};
+    for (int n : orders) scaled[n] = std::max(1, cur[n] * threads / 256);
+    for (int pers = 0; pers < 2 && rc == SIP_OK; ++pers)
+      for (int ps = 0; ps <= 32 && rc == SIP_OK; ++ps) {
+        if (ps == 0 && (pers || threads == 256)) continue;  // the default grid was timed above
+        if (ps > 0 && threads == 256 && !pers && ps == auto_per_sm) continue;
+        float ms = 0.0f;
+        int got = 0;
+        rc = time_full(scaled, ps, pers != 0, threads, &ms, &got);
+        if (rc || (ps > 0 && got != ps)) break;  // beyond the occupancy
+        if (ms < 0.97f * cur_ms) {
+          cur_ms = ms;
+          cur_per_sm = ps;
+          cur_pers = pers != 0;
+          cur_threads = threads;
+          std::memcpy(best_epb, scaled, sizeof(scaled));
+        }
       }
-    }
-  int* best = cur;
+    if (rc) break;
+  }
   h->timing = timing;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaFree(x);
   cudaFree(y);
   if (rc) return rc;
-  rc = set_tiles(h, precision, best, cur_per_sm, cur_pers);
+  rc = set_tiles(h, precision, best_epb, cur_per_sm, cur_pers, cur_threads);
   if (rc) return rc;
-  std::memcpy(h->epb[pi], best, sizeof(cur));
+  std::memcpy(h->epb[pi], best_epb, sizeof(best_epb));
   return SIP_OK;
 }
 
-extern "C" int sip_get_tiling(const sip_handle* h, int precision, int32_t* epb_out, int64_t* ntiles_out) {
-  if (!h || !epb_out) return fail(SIP_ERR_ARG, "null argument");
-  const int pi = precision == SIP_FP32 ? 1 : 0;
-  for (int n = 0; n <= kNMax; ++n) epb_out[n] = 0;
-  for (const Tile& t : h->tiles_h[pi]) epb_out[t.n - 1] = std::max(epb_out[t.n - 1], (int32_t)t.count);
-  if (ntiles_out) *ntiles_out = (int64_t)h->tiles_h[pi].size();
-  return SIP_OK;
-}
-
-extern "C" int sip_get_grid(const sip_handle* h, int precision, int32_t* nctas_out, int32_t* ctas_per_sm_out,
-                            int32_t* persistent_out) {
-  if (!h || !nctas_out || !ctas_per_sm_out || !persistent_out) return fail(SIP_ERR_ARG, "null argument");
+extern "C" int sip_get_tiling(const sip_handle* h, int precision, sip_tiling* out) {
+  if (!h || !out) return fail(SIP_ERR_ARG, "null argument");
   if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
   const int pi = precision == SIP_FP32 ? 1 : 0;
-  *nctas_out = (int32_t)h->cta_h[pi].size() - 1;
-  *ctas_per_sm_out = h->ctas_per_sm[pi];
-  *persistent_out = h->persistent[pi];
+  std::memset(out, 0, sizeof(*out));
+  for (const Tile& t : h->tiles_h[pi]) out->epb[t.n - 1] = std::max(out->epb[t.n - 1], (int32_t)t.count);
+  out->ctas_per_sm = h->ctas_per_sm[pi];
+  out->persistent = h->persistent[pi];
+  out->threads = h->threads[pi];
+  out->ntiles = (int64_t)h->tiles_h[pi].size();
+  out->nctas = (int64_t)h->cta_h[pi].size() - 1;
   return SIP_OK;
 }
 
-extern "C" int sip_set_tiling(sip_handle* h, int precision, const int32_t* epb, int32_t ctas_per_sm,
-                              int32_t persistent) {
+extern "C" int sip_set_tiling(sip_handle* h, int precision, const sip_tiling* t) {
   if (!h) return fail(SIP_ERR_ARG, "null handle");
   if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
-  if (ctas_per_sm < 0) return fail(SIP_ERR_ARG, "ctas_per_sm must be >= 0");
   int e[kNMax + 2] = {};
-  if (epb)
-    for (int P = 0; P <= kNMax - 1; ++P) {
-      if (epb[P] < 0 || epb[P] > kMaxEpb) return fail(SIP_ERR_ARG, "elements per tile must be in 0..32");
-      e[P + 1] = epb[P];
+  int per_sm = 0, threads = 256;
+  bool pers = false;
+  if (t) {
+    for (int P = 0; P <= kMaxOrder; ++P) {
+      if (t->epb[P] < 0 || t->epb[P] > kMaxEpb) return fail(SIP_ERR_ARG, "elements per tile must be in 0..32");
+      e[P + 1] = t->epb[P];
     }
+    if (t->ctas_per_sm < 0) return fail(SIP_ERR_ARG, "ctas_per_sm must be >= 0");
+    if (t->persistent != 0 && t->persistent != 1) return fail(SIP_ERR_ARG, "persistent must be 0 or 1");
+    per_sm = t->ctas_per_sm;
+    pers = t->persistent != 0;
+    threads = t->threads == 0 ? 256 : t->threads;
+  }
   const int pi = precision == SIP_FP32 ? 1 : 0;
-  int rc = set_tiles(h, precision, e, ctas_per_sm, persistent != 0);
+  int rc = set_tiles(h, precision, e, per_sm, pers, threads);
   if (rc) return rc;
   std::memcpy(h->epb[pi], e, sizeof(e));
   return SIP_OK;

@@ -26,15 +26,15 @@ int cuda_fail(cudaError_t e, const char* where) {
   return e == cudaErrorMemoryAllocation ? SIP_ERR_OOM : SIP_ERR_CUDA;
 }
 
-// Elements per tile: enough work items per CTA to keep 256 threads busy in every
+// Elements per tile: enough work items per CTA to keep its threads busy in every
 // stage (Gauss points in 2D, lines of Gauss points in 3D), within 64 KB of
 // shared memory.
-int apply_epb(int dim, int n, int precision) {
+int apply_epb(int dim, int n, int precision, int threads) {
   const int q = n + 1;
   // one Gauss point per work item (2D; FP64 in 3D) or one line of Q points (FP32 in 3D)
   const bool lines = dim == 3 && precision == SIP_FP32;
   const int items = lines ? q * q : (dim == 2 ? q * q : q * q * q);
-  int epb = std::max(1, (dim == 3 && !lines ? 384 : 256) / items);
+  int epb = std::max(1, (dim == 3 && !lines ? 3 * threads / 2 : threads) / items);
   const int es = precision == SIP_FP32 ? 4 : 8;
   const int per = std::max(per_elem_trace(dim, n), per_elem_main(dim, n)) * es;
   const int room = (64 * 1024 - table_block_bytes(es, n) - kMetaBytes) / per;
@@ -51,14 +51,14 @@ cudaError_t prepare_3d_f64();
 cudaError_t prepare_3d_f32();
 cudaError_t prepare_aux_2d();
 cudaError_t prepare_aux_3d();
-cudaError_t occupancy_2d_f64(size_t, size_t, int*);
-cudaError_t occupancy_2d_f32(size_t, size_t, int*);
-cudaError_t occupancy_3d_f64(size_t, size_t, int*);
-cudaError_t occupancy_3d_f32(size_t, size_t, int*);
-cudaError_t launch_apply_2d_f64(const ApplyArgs<double>&, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
-cudaError_t launch_apply_3d_f64(const ApplyArgs<double>&, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
-cudaError_t launch_apply_2d_f32(const ApplyArgs<float>&, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
-cudaError_t launch_apply_3d_f32(const ApplyArgs<float>&, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
+cudaError_t occupancy_2d_f64(int, size_t, size_t, int*);
+cudaError_t occupancy_2d_f32(int, size_t, size_t, int*);
+cudaError_t occupancy_3d_f64(int, size_t, size_t, int*);
+cudaError_t occupancy_3d_f32(int, size_t, size_t, int*);
+cudaError_t launch_apply_2d_f64(const ApplyArgs<double>&, int, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
+cudaError_t launch_apply_3d_f64(const ApplyArgs<double>&, int, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
+cudaError_t launch_apply_2d_f32(const ApplyArgs<float>&, int, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
+cudaError_t launch_apply_3d_f32(const ApplyArgs<float>&, int, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
 
 namespace {
 
@@ -141,7 +141,8 @@ size_t apply_scratch_bytes(const sip_handle* h, int precision, int nrhs, size_t*
   return precision == SIP_FP64 ? tr + (size_t)nrhs * (size_t)h->plan.nquad * es : tr;
 }
 
-int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_per_sm, bool persistent, Schedule& s) {
+int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_per_sm, bool persistent, int threads,
+                  Schedule& s) {
   const Plan& p = h->plan;
   const int es = precision == SIP_FP32 ? 4 : 8;
   auto size_smem = [&]() {
@@ -154,17 +155,23 @@ int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_p
   };
   // one CTA per tile of the largest size epb allows: the tile count and shared
   // memory bound the rest (a CTA's tiles are never larger)
-  build_tiles(p, precision, epb, 0, false, s.tiles, s.cta_off);
+  if (threads != 64 && threads != 128 && threads != 256) return fail(SIP_ERR_ARG, "threads per CTA must be 64, 128 or 256");
+  build_tiles(p, precision, epb, threads, 0, false, s.tiles, s.cta_off);
   size_smem();
   s.per_sm = 1;
   s.persistent = persistent;
+  s.threads = threads;
   if (s.smem_t > 200 * 1024 || s.smem_m > 200 * 1024) return fail(SIP_ERR_ARG, "tile too large for shared memory");
   const int64_t ntile = (int64_t)s.tiles.size();
   if (ntile == 0) return SIP_OK;
   int occ = 0, nsm = 0;
   cudaError_t e;
-  if (p.dim == 2) e = precision == SIP_FP64 ? occupancy_2d_f64(s.smem_t, s.smem_m, &occ) : occupancy_2d_f32(s.smem_t, s.smem_m, &occ);
-  else e = precision == SIP_FP64 ? occupancy_3d_f64(s.smem_t, s.smem_m, &occ) : occupancy_3d_f32(s.smem_t, s.smem_m, &occ);
+  if (p.dim == 2)
+    e = precision == SIP_FP64 ? occupancy_2d_f64(threads, s.smem_t, s.smem_m, &occ)
+                              : occupancy_2d_f32(threads, s.smem_t, s.smem_m, &occ);
+  else
+    e = precision == SIP_FP64 ? occupancy_3d_f64(threads, s.smem_t, s.smem_m, &occ)
+                              : occupancy_3d_f32(threads, s.smem_t, s.smem_m, &occ);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy");
   occ = std::max(1, occ);
@@ -172,7 +179,7 @@ int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_p
   // per_sm x SMs CTAs of equal flops, all resident at once
   const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ)
                                      : (int)std::min<int64_t>(occ, std::max<int64_t>(1, ntile / nsm));
-  build_tiles(p, precision, epb, nsm * per_sm, persistent, s.tiles, s.cta_off);
+  build_tiles(p, precision, epb, threads, nsm * per_sm, persistent, s.tiles, s.cta_off);
   size_smem();
   s.per_sm = per_sm;
   return SIP_OK;
@@ -181,10 +188,10 @@ int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_p
 // (Re)build the schedule of one precision (epb_by_n[n] > 0 overrides the default
 // elements per tile for order n - 1; ctas_per_sm > 0 fixes the resident CTAs per
 // SM it is balanced for), upload it and size the shared memory.
-int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm, bool persistent) {
+int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm, bool persistent, int threads) {
   const int pi = precision == SIP_FP32 ? 1 : 0;
   Schedule sc;
-  int rc = make_schedule(h, precision, epb_by_n, ctas_per_sm, persistent, sc);
+  int rc = make_schedule(h, precision, epb_by_n, ctas_per_sm, persistent, threads, sc);
   if (rc) return rc;
   Tile* d = nullptr;
   int32_t* c = nullptr;
@@ -209,6 +216,7 @@ int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm
   h->cta_h[pi] = std::move(sc.cta_off);
   h->ctas_per_sm[pi] = sc.per_sm;
   h->persistent[pi] = sc.persistent ? 1 : 0;
+  h->threads[pi] = sc.threads;
   h->smem_trace[pi] = sc.smem_t;
   h->smem_main[pi] = sc.smem_m;
   for (auto* W : {&h->cg64, &h->cg32})
@@ -246,8 +254,8 @@ ApplyArgs<T> make_args(sip_handle* h, const T* x, T* y, T* trace, T* ug, int tra
   return a;
 }
 
-int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t* cta_d, int nctas, size_t smem_t,
-                size_t smem_m, const void* x, void* y, int nrhs, cudaStream_t s, int transpose,
+int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t* cta_d, int nctas, int threads,
+                size_t smem_t, size_t smem_m, const void* x, void* y, int nrhs, cudaStream_t s, int transpose,
                 void* scratch_override) {
   size_t ug_off = 0;
   apply_scratch_bytes(h, precision, nrhs, &ug_off);
@@ -260,15 +268,15 @@ int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t
     auto a = make_args<double>(h, (const double*)x, (double*)y, tr, ug, transpose);
     a.tiles = tiles_d;
     a.cta_off = cta_d;
-    e = h->plan.dim == 2 ? launch_apply_2d_f64(a, nctas, nrhs, smem_t, smem_m, s, e0, e1, e2)
-                         : launch_apply_3d_f64(a, nctas, nrhs, smem_t, smem_m, s, e0, e1, e2);
+    e = h->plan.dim == 2 ? launch_apply_2d_f64(a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2)
+                         : launch_apply_3d_f64(a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2);
   } else {
     float* tr = scratch_override ? (float*)scratch_override : (float*)h->trace_d;
     auto a = make_args<float>(h, (const float*)x, (float*)y, tr, nullptr, transpose);
     a.tiles = tiles_d;
     a.cta_off = cta_d;
-    e = h->plan.dim == 2 ? launch_apply_2d_f32(a, nctas, nrhs, smem_t, smem_m, s, e0, e1, e2)
-                         : launch_apply_3d_f32(a, nctas, nrhs, smem_t, smem_m, s, e0, e1, e2);
+    e = h->plan.dim == 2 ? launch_apply_2d_f32(a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2)
+                         : launch_apply_3d_f32(a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2);
   }
   if (e != cudaSuccess) return cuda_fail(e, "apply launch");
   h->timed_pending = h->timing;
@@ -285,8 +293,8 @@ int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cu
     if (rc) return rc;
   }
   const int pi = precision == SIP_FP32 ? 1 : 0;
-  return apply_tiles(h, precision, h->tiles_d[pi], h->cta_d[pi], (int)h->cta_h[pi].size() - 1, h->smem_trace[pi],
-                     h->smem_main[pi], x, y, nrhs, s, transpose, scratch_override);
+  return apply_tiles(h, precision, h->tiles_d[pi], h->cta_d[pi], (int)h->cta_h[pi].size() - 1, h->threads[pi],
+                     h->smem_trace[pi], h->smem_main[pi], x, y, nrhs, s, transpose, scratch_override);
 }
 
 }  // namespace sip
@@ -418,7 +426,7 @@ int sip_create(const sip_mesh* mesh, const int32_t* orders, double lambda, const
     return rc;
   }
   for (int prec : {SIP_FP64, SIP_FP32}) {
-    rc = set_tiles(h, prec, nullptr, 0, false);
+    rc = set_tiles(h, prec, nullptr, 0, false, 256);
     if (rc) { sip_destroy(h); return rc; }
   }
   rc = handle_grow_trace(h, 1);

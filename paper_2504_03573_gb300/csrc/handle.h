@@ -62,6 +62,7 @@ struct sip_handle {
   int epb[2][sip::kNMax + 2] = {};                // elements per tile per order in use (0: default)
   int ctas_per_sm[2] = {0, 0};                    // resident CTAs per SM the schedule is balanced for
   int persistent[2] = {0, 0};                     // CTAs run several tiles each
+  int threads[2] = {256, 256};                    // threads per CTA
   double* xq = nullptr;
   sip::DevGeom<double> gd;
   sip::DevGeom<float> gf;
@@ -110,12 +111,14 @@ struct Schedule {
   size_t smem_t = 0, smem_m = 0;
   int per_sm = 0;
   bool persistent = false;
+  int threads = 256;
   int nctas() const { return (int)cta_off.size() - 1; }
 };
 // epb: elements per tile by order (nullptr or 0 entries: default); ctas_per_sm <= 0:
 // as many as fit, capped at the number of default-sized tiles per SM; persistent:
 // per_sm x SMs CTAs with several tiles each (build_tiles)
-int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_per_sm, bool persistent, Schedule& s);
+int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_per_sm, bool persistent, int threads,
+                  Schedule& s);
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* where);
 // scratch_override: caller-provided scratch holding the trace buffer followed by
@@ -123,9 +126,9 @@ int cuda_fail(cudaError_t e, const char* where);
 int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cudaStream_t s,
               int transpose, void* scratch_override);
 size_t apply_scratch_bytes(const sip_handle* h, int precision, int nrhs, size_t* ug_offset);
-int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t* cta_d, int nctas, size_t smem_t,
-                size_t smem_m, const void* x, void* y, int nrhs, cudaStream_t s, int transpose,
+int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t* cta_d, int nctas, int threads,
+                size_t smem_t, size_t smem_m, const void* x, void* y, int nrhs, cudaStream_t s, int transpose,
                 void* scratch_override);
-int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm, bool persistent);
+int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm, bool persistent, int threads);
 int handle_grow_trace(sip_handle* h, int nrhs);
 }  // namespace sip

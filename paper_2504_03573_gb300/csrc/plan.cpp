@@ -529,7 +529,7 @@ Tile make_tile(const Plan& p, int n, int64_t s0, int64_t s1) {
 //  * persistent = true: k_n = round(nctas C_n / C) CTAs (1 .. cnt), each an equal
 //    share of the run cut into tiles of at most epb elements and run one after
 //    the other.
-void build_tiles(const Plan& p, int precision, const int* epb_override, int nctas, bool persistent,
+void build_tiles(const Plan& p, int precision, const int* epb_override, int threads, int nctas, bool persistent,
                  std::vector<Tile>& tiles, std::vector<int32_t>& cta_off) {
   tiles.clear();
   cta_off.assign(1, 0);
@@ -547,7 +547,7 @@ void build_tiles(const Plan& p, int precision, const int* epb_override, int ncta
     int64_t j = i;
     double Cn = 0.0;
     while (j < E && p.P[p.elist[j]] + 1 == n) Cn += ce[j++];
-    int epb = epb_override && epb_override[n] > 0 ? epb_override[n] : apply_epb(p.dim, n, precision);
+    int epb = epb_override && epb_override[n] > 0 ? epb_override[n] : apply_epb(p.dim, n, precision, threads);
     epb = std::max(1, std::min(epb, kMaxEpb));
     const int64_t cnt = j - i;
     const int64_t share = nctas > 0 ? std::max<int64_t>(1, std::llround(nctas * Cn / C)) : 0;

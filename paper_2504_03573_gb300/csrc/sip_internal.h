@@ -181,9 +181,9 @@ void fill_tables(std::vector<double>& tab);
 // elements per tile for the apply kernels (host choice), per-element flops, and
 // the tiles with the CTA that runs each (tiles cta_off[b] .. cta_off[b+1]-1, one
 // order per CTA)
-int apply_epb(int dim, int n, int precision);
+int apply_epb(int dim, int n, int precision, int threads);
 void element_flops(const Plan& p, int64_t e, double& ft, double& fm);
-void build_tiles(const Plan& p, int precision, const int* epb_override, int nctas, bool persistent,
+void build_tiles(const Plan& p, int precision, const int* epb_override, int threads, int nctas, bool persistent,
                  std::vector<Tile>& tiles, std::vector<int32_t>& cta_off);
 
 }  // namespace sip

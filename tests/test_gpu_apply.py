@@ -200,17 +200,18 @@ def test_tilings_give_identical_results(pkg, name):
             assert rel(ref.double().cpu().numpy(), A @ x) <= tol
         ntiles = set()
         big = 32 if m.dim == 2 else 4
-        for epb, per_sm, pers in (([1] * P1, 0, False), ([big] * P1, 0, False), ([big] * P1, 1, True), (None, 1, False),
-                                  (None, 3, True), ([2] * P1, 8, True), ([2] * P1, 8, False)):
-            info = op.set_tiling(prec, epb, per_sm, pers)
-            assert info["persistent"] == pers
+        for epb, per_sm, pers, thr in (([1] * P1, 0, False, 256), ([big] * P1, 0, False, 256), ([big] * P1, 1, True, 256),
+                                       (None, 1, False, 128), (None, 3, True, 64), ([2] * P1, 8, True, 128),
+                                       ([2] * P1, 8, False, 64)):
+            info = op.set_tiling(prec, epb, per_sm, pers, thr)
+            assert info["persistent"] == pers and info["threads"] == thr
             assert 1 <= info["nctas"] <= len(m.orders) and info["ctas_per_sm"] >= 1
             if epb is not None and epb[0] == 1:
                 assert info["ntiles"] == len(m.orders)
             if not pers:
                 assert info["nctas"] == info["ntiles"]
             ntiles.add(info["ntiles"])
-            assert torch.equal(op.apply(xt), ref), (epb, per_sm, pers, info)
+            assert torch.equal(op.apply(xt), ref), (epb, per_sm, pers, thr, info)
         if not small:
             assert len(ntiles) >= 3
         op.set_tiling(prec)  # back to the defaults
@@ -226,6 +227,8 @@ def test_set_tiling_rejects_bad_values(pkg):
         op.set_tiling(pkg.SIP_FP64, [33] * P1, 0)
     with pytest.raises(pkg.SipError):
         op.set_tiling(pkg.SIP_FP64, None, -1)
+    with pytest.raises(pkg.SipError):
+        op.set_tiling(pkg.SIP_FP64, None, 0, False, 96)
     with pytest.raises(ValueError):
         op.set_tiling(pkg.SIP_FP64, [1, 2], 0)
     assert op.tiling(pkg.SIP_FP64) == before
