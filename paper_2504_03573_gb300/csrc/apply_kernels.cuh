@@ -153,17 +153,19 @@ template <int Q>
 __device__ __forceinline__ int qpow(int e) { return e == 0 ? 1 : (e == 1 ? Q : Q * Q); }
 
 // ============================================================ trace kernel
-// Per-tile copy of the element ids and face slots (kMetaBytes, after the table block).
+// Per-tile copy of the element ids, face slots and face list (kMetaBytes, after
+// the table block).
 struct TileMeta {
   int32_t eid[kMaxEpb];
   FaceSlot slot[kMaxEpb * 6];
   int8_t aff[kMaxEpb];
+  uint16_t fl[kFaceListMax];
 };
 static_assert(sizeof(TileMeta) <= kMetaBytes, "TileMeta exceeds its shared-memory block");
 
 template <int DIM>
 __device__ __forceinline__ void load_meta(const int32_t* elist, const FaceSlot* slots, const int8_t* eaff,
-                                          const Tile& t, TileMeta* mt) {
+                                          const uint16_t* flists, const Tile& t, TileMeta* mt) {
   for (int w = threadIdx.x; w < t.count * 2 * DIM; w += blockDim.x) {
     const int el = w / (2 * DIM), k = w - el * 2 * DIM;
     const int e = elist[t.start + el];
@@ -173,7 +175,45 @@ __device__ __forceinline__ void load_meta(const int32_t* elist, const FaceSlot* 
     }
     mt->slot[el * 2 * DIM + k] = slots[(int64_t)e * 2 * DIM + k];
   }
+  const uint16_t* fl = flists + t.flist;
+  const int len = 3 + 2 * fl[2] + fl[0] + fl[1];
+  for (int w = threadIdx.x; w < len; w += blockDim.x) mt->fl[w] = fl[w];
 }
+
+// The tile's faces as dense work lists: the conforming ones, and the ones with
+// a finer shared rule grouped by that rule (entries fl_el / fl_k / fl_qf).
+struct FaceList {
+  const uint16_t* r;
+  __device__ __forceinline__ int nconf() const { return r[0]; }
+  __device__ __forceinline__ int nfine() const { return r[1]; }
+  __device__ __forceinline__ int conf(int i) const { return r[3 + 2 * r[2] + i]; }
+  __device__ __forceinline__ int fine(int i) const { return r[3 + 2 * r[2] + r[0] + i]; }
+  // work items of all fine faces, items(qf) per face
+  template <typename F>
+  __device__ __forceinline__ int fine_items(F items) const {
+    int n = 0;
+    for (int g = 0; g < r[2]; ++g) n += r[4 + 2 * g] * items(r[3 + 2 * g]);
+    return n;
+  }
+  // fine face j and its item u for work item w < fine_items(items)
+  template <typename F>
+  __device__ __forceinline__ void fine_at(F items, int w, int& j, int& u) const {
+    int j0 = 0;
+    for (int g = 0; g < r[2]; ++g) {
+      const int per = items(r[3 + 2 * g]), cnt = r[4 + 2 * g];
+      if (w < cnt * per) {
+        const int q = w / per;
+        j = j0 + q;
+        u = w - q * per;
+        return;
+      }
+      w -= cnt * per;
+      j0 += cnt;
+    }
+    j = 0;
+    u = 0;
+  }
+};
 
 // face geometry at canonical point zc: W, and component m of c on the given side
 template <typename T>
@@ -284,11 +324,10 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
     __syncthreads();
   }
   // 3. conforming faces, all at once (orthogonal ones were stored in step 1)
-  for (int w = threadIdx.x; w < (orth ? 0 : ne * NFACE * QF1); w += blockDim.x) {
-    const int el = w / (NFACE * QF1);
-    const int rem = w - el * NFACE * QF1;
-    const int k = rem / QF1, j = rem - k * QF1;
-    if (mt->slot[el * 2 * DIM + k].qf != Q) continue;
+  const FaceList fl{mt->fl};
+  for (int w = threadIdx.x; w < (orth ? 0 : fl.nconf() * QF1); w += blockDim.x) {
+    const int i = w / QF1, j = w - i * QF1;
+    const int e = fl.conf(i), el = fl_el(e), k = fl_k(e);
     emit(el, k, F0 + el * PER + k * 4 * QF1, QF1, j % Q, j / Q);
   }
   // 4. faces with a finer shared rule (p-non-conforming): NSC faces per round,
@@ -297,25 +336,35 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
     constexpr int NSC = scratch_slots(DIM);
     constexpr int SL = 4 * (FT + FMAX);  // one slot: Ft [4][FT], Ff [4][FMAX]
     const int nfld = orth ? 2 : 4;
-    for (int k0 = 0; k0 < NFACE; k0 += NSC) {
-      if constexpr (DIM == 2) {
-        for (int w = threadIdx.x; w < ne * NSC * nfld * qfm; w += blockDim.x) {
-          const int el = w / (NSC * nfld * qfm);
-          const int rem = w - el * NSC * nfld * qfm;
-          const int kk = rem / (nfld * qfm), r2 = rem - kk * nfld * qfm;
-          const int f = r2 / qfm, z = r2 - f * qfm;
-          const int k = k0 + kk;
-          const int qf = mt->slot[el * 2 * DIM + k].qf;
-          if (qf == Q || z >= qf) continue;
-          const T* IT = tb + TabLayout::IT(N, qf);
-          const T* src = F0 + el * PER + k * 4 * QF1 + f * QF1;
-          T s = 0;
+    if constexpr (DIM == 2) {
+      // one scratch slot per face (slot k): all fine faces at once, as dense
+      // work lists grouped by the shared rule
+      static_assert(DIM != 2 || NSC == NFACE, "2D keeps one scratch slot per face");
+      auto per_i = [&](int qf) { return nfld * qf; };
+      for (int w = threadIdx.x; w < fl.fine_items(per_i); w += blockDim.x) {
+        int j, u;
+        fl.fine_at(per_i, w, j, u);
+        const int e = fl.fine(j), el = fl_el(e), k = fl_k(e), qf = fl_qf(e);
+        const int f = u / qf, z = u - f * qf;
+        const T* IT = tb + TabLayout::IT(N, qf);
+        const T* src = F0 + el * PER + k * 4 * QF1 + f * QF1;
+        T s = 0;
 #pragma unroll
-          for (int r = 0; r < Q; ++r) s = fma(IT[r * qf + z], src[r], s);
-          F0[el * PER + SC + kk * SL + 4 * FT + f * FMAX + z] = s;
-        }
-        __syncthreads();
-      } else {
+        for (int r = 0; r < Q; ++r) s = fma(IT[r * qf + z], src[r], s);
+        F0[el * PER + SC + k * SL + 4 * FT + f * FMAX + z] = s;
+      }
+      __syncthreads();
+      auto per_e = [&](int qf) { return qf; };
+      for (int w = threadIdx.x; w < fl.fine_items(per_e); w += blockDim.x) {
+        int j, z;
+        fl.fine_at(per_e, w, j, z);
+        const int e = fl.fine(j), el = fl_el(e), k = fl_k(e);
+        emit(el, k, F0 + el * PER + SC + k * SL + 4 * FT, FMAX, z, 0);
+      }
+      __syncthreads();
+    } else {
+    for (int k0 = 0; k0 < NFACE; k0 += NSC) {
+      {
         for (int w = threadIdx.x; w < ne * NSC * nfld * Q * qfm; w += blockDim.x) {
           const int el = w / (NSC * nfld * Q * qfm);
           const int rem = w - el * NSC * nfld * Q * qfm;
@@ -362,6 +411,7 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
       }
       __syncthreads();
     }
+    }
   }
   __syncthreads();
 }
@@ -371,7 +421,7 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
   using S = Shape<DIM, N>;
   constexpr int PER = S::PER_TRACE;
   const int ne = t.count;
-  load_meta<DIM>(a.elist, a.slots, a.eaff, t, mt);
+  load_meta<DIM>(a.elist, a.slots, a.eaff, a.flists, t, mt);
   __syncthreads();
   // one output per thread (2D, and FP64 in 3D: more parallel work for the narrow
   // FP64 pipe) or one line per thread with the matrices as constant-bank operands
@@ -478,6 +528,35 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
   const int ne = t.count;
   const int qfm = t.flags & kTileQfMask;
   const int npm = DIM == 2 ? qfm : qfm * qfm;
+  if constexpr (DIM == 2) {
+    // one scratch slot per face (slot k): all fine faces at once, as dense work
+    // lists grouped by the shared rule
+    static_assert(DIM != 2 || NSC == NFACE, "2D keeps one scratch slot per face");
+    const FaceList fl{mt->fl};
+    auto per_f = [&](int qf) { return qf; };
+    for (int w = threadIdx.x; w < fl.fine_items(per_f); w += blockDim.x) {
+      int j, z;
+      fl.fine_at(per_f, w, j, z);
+      const int e = fl.fine(j), el = fl_el(e), k = fl_k(e);
+      face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, z, 0, F0 + el * per + SC + k * SL + NF * FT, FMAX);
+    }
+    __syncthreads();
+    // projection of the fields in use (s and c_a t where the tile is orthogonal)
+    const int nfu = orth ? 2 : NF;
+    for (int w = threadIdx.x; w < fl.nfine() * nfu * Q; w += blockDim.x) {
+      const int j = w / (nfu * Q), r2 = w - j * nfu * Q;
+      const int fi = r2 / Q, r = r2 - fi * Q;
+      const int e = fl.fine(j), el = fl_el(e), k = fl_k(e), qf = fl_qf(e);
+      const int f = orth && fi == 1 ? 1 + (k >> 1) : fi;
+      const T* II = tb + TabLayout::II(N, qf);
+      const T* src = F0 + el * per + SC + k * SL + NF * FT + f * FMAX;
+      T s = 0;
+      for (int z = 0; z < qf; ++z) s = fma(II[z * Q + r], src[z], s);
+      F0[el * per + k * NF * QF1 + f * QF1 + r] = s;
+    }
+    __syncthreads();
+    return;
+  }
   for (int k0 = 0; k0 < NFACE; k0 += NSC) {
     for (int w = threadIdx.x; w < ne * NSC * npm; w += blockDim.x) {
       const int el = w / (NSC * npm), r2 = w - el * NSC * npm;
@@ -558,7 +637,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   T* G2 = sm + 3 * QV;
   T* R = sm + (1 + DIM) * QV;
   T* const F0 = sm + (2 + DIM) * QV;
-  load_meta<DIM>(a.elist, a.slots, a.eaff, t, mt);
+  load_meta<DIM>(a.elist, a.slots, a.eaff, a.flists, t, mt);
   __syncthreads();
   if (a.ug) {
     for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
@@ -606,13 +685,12 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   {
     const T* DT = tb + TabLayout::DT(N);
     const int nvol = ne * QV;
-    for (int w = threadIdx.x; w < nvol + ne * NFACE * QF1; w += blockDim.x) {
+    const FaceList fl{mt->fl};
+    for (int w = threadIdx.x; w < nvol + fl.nconf() * QF1; w += blockDim.x) {
       if (w >= nvol) {
         const int v = w - nvol;
-        const int el = v / (NFACE * QF1);
-        const int rem = v - el * NFACE * QF1;
-        const int k = rem / QF1, j = rem - k * QF1;
-        if (mt->slot[el * 2 * DIM + k].qf != Q) continue;
+        const int i = v / QF1, j = v - i * QF1;
+        const int e = fl.conf(i), el = fl_el(e), k = fl_k(e);
         face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
         continue;
       }

@@ -57,15 +57,12 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
     if (r2 == SIP_ERR_ARG) { *ms_out = 1e30f; return SIP_OK; }  // tile too large for shared memory
     if (r2) return r2;
     if (per_sm_out) *per_sm_out = sc.per_sm;
-    Tile* td = nullptr;
-    int32_t* cd = nullptr;
-    cudaError_t ee = cudaMalloc((void**)&td, std::max<size_t>(16, sc.tiles.size() * sizeof(Tile)));
-    if (ee == cudaSuccess) ee = cudaMalloc((void**)&cd, sc.cta_off.size() * sizeof(int32_t));
-    if (ee == cudaSuccess) ee = cudaMemcpy(td, sc.tiles.data(), sc.tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
-    if (ee == cudaSuccess) ee = cudaMemcpy(cd, sc.cta_off.data(), sc.cta_off.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (ee != cudaSuccess) { cudaFree(td); cudaFree(cd); return cuda_fail(ee, "autotune tiles"); }
+    DevSchedule d;
+    cudaError_t ee = upload_schedule(sc, d);
+    if (ee != cudaSuccess) return cuda_fail(ee, "autotune tiles");
     auto run = [&]() {
-      return apply_tiles(h, precision, td, cd, sc.nctas(), sc.threads, sc.smem_t, sc.smem_m, x, y, 1, s, 0, nullptr);
+      return apply_tiles(h, precision, d.tiles, d.cta, d.flist, sc.nctas(), sc.threads, sc.smem_t, sc.smem_m, x, y, 1,
+                         s, 0, nullptr);
     };
     for (int w = 0; w < 2 && r2 == SIP_OK; ++w) r2 = run();
     // best of three batches of reps launches
@@ -80,8 +77,7 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
       cudaEventElapsedTime(&ms, a, b);
       best = std::min(best, ms);
     }
-    cudaFree(td);
-    cudaFree(cd);
+    free_schedule(d);
     *ms_out = best;
     return r2;
   };

@@ -156,7 +156,7 @@ int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_p
   // one CTA per tile of the largest size epb allows: the tile count and shared
   // memory bound the rest (a CTA's tiles are never larger)
   if (threads != 64 && threads != 128 && threads != 256) return fail(SIP_ERR_ARG, "threads per CTA must be 64, 128 or 256");
-  build_tiles(p, precision, epb, threads, 0, false, s.tiles, s.cta_off);
+  build_tiles(p, precision, epb, threads, 0, false, s.tiles, s.cta_off, s.flists);
   size_smem();
   s.per_sm = 1;
   s.persistent = persistent;
@@ -179,10 +179,34 @@ int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_p
   // per_sm x SMs CTAs of equal flops, all resident at once
   const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ)
                                      : (int)std::min<int64_t>(occ, std::max<int64_t>(1, ntile / nsm));
-  build_tiles(p, precision, epb, threads, nsm * per_sm, persistent, s.tiles, s.cta_off);
+  build_tiles(p, precision, epb, threads, nsm * per_sm, persistent, s.tiles, s.cta_off, s.flists);
   size_smem();
   s.per_sm = per_sm;
   return SIP_OK;
+}
+
+cudaError_t upload_schedule(const Schedule& sc, DevSchedule& d) {
+  d = DevSchedule{};
+  cudaError_t e = cudaMalloc((void**)&d.tiles, std::max<size_t>(16, sc.tiles.size() * sizeof(Tile)));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d.cta, sc.cta_off.size() * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d.flist, std::max<size_t>(16, sc.flists.size() * sizeof(uint16_t)));
+  if (e == cudaSuccess && !sc.tiles.empty())
+    e = cudaMemcpy(d.tiles, sc.tiles.data(), sc.tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d.cta, sc.cta_off.data(), sc.cta_off.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !sc.flists.empty())
+    e = cudaMemcpy(d.flist, sc.flists.data(), sc.flists.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_schedule(d);
+    cudaGetLastError();
+  }
+  return e;
+}
+
+void free_schedule(DevSchedule& d) {
+  cudaFree(d.tiles);
+  cudaFree(d.cta);
+  cudaFree(d.flist);
+  d = DevSchedule{};
 }
 
 // (Re)build the schedule of one precision (epb_by_n[n] > 0 overrides the default
@@ -193,25 +217,18 @@ int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm
   Schedule sc;
   int rc = make_schedule(h, precision, epb_by_n, ctas_per_sm, persistent, threads, sc);
   if (rc) return rc;
-  Tile* d = nullptr;
-  int32_t* c = nullptr;
-  cudaError_t e = cudaMalloc((void**)&d, std::max<size_t>(16, sc.tiles.size() * sizeof(Tile)));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c, sc.cta_off.size() * sizeof(int32_t));
-  if (e == cudaSuccess && !sc.tiles.empty())
-    e = cudaMemcpy(d, sc.tiles.data(), sc.tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(c, sc.cta_off.data(), sc.cta_off.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    cudaFree(d);
-    cudaFree(c);
-    return cuda_fail(e, "tiles");
-  }
-  if (h->tiles_d[pi] || h->cta_d[pi]) {
+  DevSchedule d;
+  cudaError_t e = upload_schedule(sc, d);
+  if (e != cudaSuccess) return cuda_fail(e, "tiles");
+  if (h->tiles_d[pi] || h->cta_d[pi] || h->flist_d[pi]) {
     cudaDeviceSynchronize();  // earlier launches may still read the old schedule
     cudaFree(h->tiles_d[pi]);
     cudaFree(h->cta_d[pi]);
+    cudaFree(h->flist_d[pi]);
   }
-  h->tiles_d[pi] = d;
-  h->cta_d[pi] = c;
+  h->tiles_d[pi] = d.tiles;
+  h->cta_d[pi] = d.cta;
+  h->flist_d[pi] = d.flist;
   h->tiles_h[pi] = std::move(sc.tiles);
   h->cta_h[pi] = std::move(sc.cta_off);
   h->ctas_per_sm[pi] = sc.per_sm;
@@ -242,6 +259,7 @@ ApplyArgs<T> make_args(sip_handle* h, const T* x, T* y, T* trace, T* ug, int tra
   a.eaff = h->eaff;
   a.tiles = h->tiles_d[std::is_same<T, float>::value ? 1 : 0];
   a.cta_off = h->cta_d[std::is_same<T, float>::value ? 1 : 0];
+  a.flists = h->flist_d[std::is_same<T, float>::value ? 1 : 0];
   a.x = x;
   a.y = y;
   a.trace = trace;
@@ -254,9 +272,9 @@ ApplyArgs<T> make_args(sip_handle* h, const T* x, T* y, T* trace, T* ug, int tra
   return a;
 }
 
-int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t* cta_d, int nctas, int threads,
-                size_t smem_t, size_t smem_m, const void* x, void* y, int nrhs, cudaStream_t s, int transpose,
-                void* scratch_override) {
+int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t* cta_d, const uint16_t* flist_d,
+                int nctas, int threads, size_t smem_t, size_t smem_m, const void* x, void* y, int nrhs, cudaStream_t s,
+                int transpose, void* scratch_override) {
   size_t ug_off = 0;
   apply_scratch_bytes(h, precision, nrhs, &ug_off);
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
@@ -268,6 +286,7 @@ int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t
     auto a = make_args<double>(h, (const double*)x, (double*)y, tr, ug, transpose);
     a.tiles = tiles_d;
     a.cta_off = cta_d;
+    a.flists = flist_d;
     e = h->plan.dim == 2 ? launch_apply_2d_f64(a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2)
                          : launch_apply_3d_f64(a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2);
   } else {
@@ -275,6 +294,7 @@ int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t
     auto a = make_args<float>(h, (const float*)x, (float*)y, tr, nullptr, transpose);
     a.tiles = tiles_d;
     a.cta_off = cta_d;
+    a.flists = flist_d;
     e = h->plan.dim == 2 ? launch_apply_2d_f32(a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2)
                          : launch_apply_3d_f32(a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2);
   }
@@ -293,8 +313,8 @@ int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cu
     if (rc) return rc;
   }
   const int pi = precision == SIP_FP32 ? 1 : 0;
-  return apply_tiles(h, precision, h->tiles_d[pi], h->cta_d[pi], (int)h->cta_h[pi].size() - 1, h->threads[pi],
-                     h->smem_trace[pi], h->smem_main[pi], x, y, nrhs, s, transpose, scratch_override);
+  return apply_tiles(h, precision, h->tiles_d[pi], h->cta_d[pi], h->flist_d[pi], (int)h->cta_h[pi].size() - 1,
+                     h->threads[pi], h->smem_trace[pi], h->smem_main[pi], x, y, nrhs, s, transpose, scratch_override);
 }
 
 }  // namespace sip

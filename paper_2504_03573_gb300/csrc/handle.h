@@ -58,6 +58,7 @@ struct sip_handle {
   sip::Tile* tiles_d[2] = {nullptr, nullptr};   // per precision (FP64, FP32)
   std::vector<sip::Tile> tiles_h[2];
   int32_t* cta_d[2] = {nullptr, nullptr};       // CTA b runs tiles cta_off[b] .. cta_off[b+1]-1
+  uint16_t* flist_d[2] = {nullptr, nullptr};    // face lists of the tiles
   std::vector<int32_t> cta_h[2];
   int epb[2][sip::kNMax + 2] = {};                // elements per tile per order in use (0: default)
   int ctas_per_sm[2] = {0, 0};                    // resident CTAs per SM the schedule is balanced for
@@ -108,6 +109,7 @@ namespace sip {
 struct Schedule {
   std::vector<Tile> tiles;
   std::vector<int32_t> cta_off;
+  std::vector<uint16_t> flists;
   size_t smem_t = 0, smem_m = 0;
   int per_sm = 0;
   bool persistent = false;
@@ -119,6 +121,14 @@ struct Schedule {
 // per_sm x SMs CTAs with several tiles each (build_tiles)
 int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_per_sm, bool persistent, int threads,
                   Schedule& s);
+// device copy of a schedule
+struct DevSchedule {
+  Tile* tiles = nullptr;
+  int32_t* cta = nullptr;
+  uint16_t* flist = nullptr;
+};
+cudaError_t upload_schedule(const Schedule& sc, DevSchedule& d);
+void free_schedule(DevSchedule& d);
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* where);
 // scratch_override: caller-provided scratch holding the trace buffer followed by
@@ -126,9 +136,9 @@ int cuda_fail(cudaError_t e, const char* where);
 int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cudaStream_t s,
               int transpose, void* scratch_override);
 size_t apply_scratch_bytes(const sip_handle* h, int precision, int nrhs, size_t* ug_offset);
-int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t* cta_d, int nctas, int threads,
-                size_t smem_t, size_t smem_m, const void* x, void* y, int nrhs, cudaStream_t s, int transpose,
-                void* scratch_override);
+int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t* cta_d, const uint16_t* flist_d,
+                int nctas, int threads, size_t smem_t, size_t smem_m, const void* x, void* y, int nrhs, cudaStream_t s,
+                int transpose, void* scratch_override);
 int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm, bool persistent, int threads);
 int handle_grow_trace(sip_handle* h, int nrhs);
 }  // namespace sip

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -504,17 +505,37 @@ void element_flops(const Plan& p, int64_t e, double& ft, double& fm) {
 
 namespace {
 
-Tile make_tile(const Plan& p, int n, int64_t s0, int64_t s1) {
+// tile of elist[s0, s1) (order n - 1) with its face list appended to fl
+Tile make_tile(const Plan& p, int n, int64_t s0, int64_t s1, std::vector<uint16_t>& fl) {
   int qfm = n + 1;
   bool orth = true;
+  std::vector<uint16_t> conf, fine;
   for (int64_t s = s0; s < s1; ++s)
     for (int f = 0; f < 2 * p.dim; ++f) {
       const FaceSlot& sl = p.slots[(size_t)p.elist[s] * 2 * p.dim + f];
       qfm = std::max(qfm, (int)sl.qf);
       orth = orth && (sl.flags & kFaceOrth);
+      const uint16_t e = (uint16_t)((s - s0) | (f << 5) | (sl.qf << 8));
+      (sl.qf == n + 1 ? conf : fine).push_back(e);
     }
+  std::stable_sort(fine.begin(), fine.end(), [](uint16_t a, uint16_t b) { return fl_qf(a) < fl_qf(b); });
+  std::vector<std::pair<int, int>> groups;  // (qf, count)
+  for (uint16_t e : fine) {
+    if (groups.empty() || groups.back().first != fl_qf(e)) groups.emplace_back(fl_qf(e), 0);
+    ++groups.back().second;
+  }
+  const int32_t off = (int32_t)fl.size();
+  fl.push_back((uint16_t)conf.size());
+  fl.push_back((uint16_t)fine.size());
+  fl.push_back((uint16_t)groups.size());
+  for (auto& g : groups) {
+    fl.push_back((uint16_t)g.first);
+    fl.push_back((uint16_t)g.second);
+  }
+  fl.insert(fl.end(), conf.begin(), conf.end());
+  fl.insert(fl.end(), fine.begin(), fine.end());
   const int flags = qfm | (qfm > n + 1 ? kTileFine : 0) | (orth ? kTileOrth : 0);
-  return Tile{n, (int32_t)s0, (int32_t)(s1 - s0), flags};
+  return Tile{n, (int32_t)s0, (int32_t)(s1 - s0), flags, off};
 }
 
 }  // namespace
@@ -530,8 +551,9 @@ Tile make_tile(const Plan& p, int n, int64_t s0, int64_t s1) {
 //    share of the run cut into tiles of at most epb elements and run one after
 //    the other.
 void build_tiles(const Plan& p, int precision, const int* epb_override, int threads, int nctas, bool persistent,
-                 std::vector<Tile>& tiles, std::vector<int32_t>& cta_off) {
+                 std::vector<Tile>& tiles, std::vector<int32_t>& cta_off, std::vector<uint16_t>& flists) {
   tiles.clear();
+  flists.clear();
   cta_off.assign(1, 0);
   const int64_t E = p.E;
   double C = 0.0;
@@ -558,7 +580,7 @@ void build_tiles(const Plan& p, int precision, const int* epb_override, int thre
     for (int64_t c = 0; c < kc; ++c) {
       const int64_t r0 = i + (cnt * c) / kc, r1 = i + (cnt * (c + 1)) / kc;
       const int64_t m = r1 - r0, nt = (m + epb - 1) / epb;
-      for (int64_t k = 0; k < nt; ++k) tiles.push_back(make_tile(p, n, r0 + (m * k) / nt, r0 + (m * (k + 1)) / nt));
+      for (int64_t k = 0; k < nt; ++k) tiles.push_back(make_tile(p, n, r0 + (m * k) / nt, r0 + (m * (k + 1)) / nt, flists));
       cta_off.push_back((int32_t)tiles.size());
     }
     i = j;

@@ -130,10 +130,21 @@ struct Tile {
   int32_t start;   // first index into the order-sorted element list
   int32_t count;   // elements in the tile
   int32_t flags;   // kTileQfMask | kTileFine | kTileOrth
+  int32_t flist;   // offset of the tile's face list (16-bit words)
 };
 
-// per-tile copy of element ids, face slots and affine flags, after the table block
-constexpr int kMetaBytes = ((kMaxEpb * (4 + 6 * (int)sizeof(FaceSlot) + 1) + 15) / 16) * 16;
+// Face list of a tile, so that face stages run over dense work items:
+// [nconf, nfine, ngroups, (qf, count) x ngroups, nconf conforming entries
+// (shared rule = own Q points), nfine entries with a finer shared rule in
+// ascending qf (the groups)]; entry = el | k << 5 | qf << 8.
+constexpr int kFaceListMax = 3 + 2 * 16 + kMaxEpb * 6;
+constexpr int fl_el(int e) { return e & 31; }
+constexpr int fl_k(int e) { return (e >> 5) & 7; }
+constexpr int fl_qf(int e) { return e >> 8; }
+
+// per-tile copy of element ids, face slots, affine flags and the face list,
+// after the table block
+constexpr int kMetaBytes = ((kMaxEpb * (4 + 6 * (int)sizeof(FaceSlot) + 1) + 2 * kFaceListMax + 15) / 16) * 16;
 
 // Host plan: everything the device needs, in FP64.
 struct Plan {
@@ -184,6 +195,6 @@ void fill_tables(std::vector<double>& tab);
 int apply_epb(int dim, int n, int precision, int threads);
 void element_flops(const Plan& p, int64_t e, double& ft, double& fm);
 void build_tiles(const Plan& p, int precision, const int* epb_override, int threads, int nctas, bool persistent,
-                 std::vector<Tile>& tiles, std::vector<int32_t>& cta_off);
+                 std::vector<Tile>& tiles, std::vector<int32_t>& cta_off, std::vector<uint16_t>& flists);
 
 }  // namespace sip
