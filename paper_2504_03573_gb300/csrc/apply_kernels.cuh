@@ -37,6 +37,13 @@ namespace sip {
 template <typename T, int DIM>
 __host__ __device__ constexpr bool line_mode() { return DIM == 3 && std::is_same<T, float>::value; }
 
+// face stages of the main kernel over the tile's dense face lists (FP64, where
+// every idle lane of an FP64 instruction costs as much as a busy one) or over
+// all faces with the others skipped (FP32, where the list's index arithmetic
+// costs more than the idle lanes)
+template <typename T>
+__host__ __device__ constexpr bool dense_faces() { return std::is_same<T, double>::value; }
+
 // ---- per-order compile-time shape
 template <int DIM, int N>
 struct Shape {
@@ -153,31 +160,37 @@ template <int Q>
 __device__ __forceinline__ int qpow(int e) { return e == 0 ? 1 : (e == 1 ? Q : Q * Q); }
 
 // ============================================================ trace kernel
-// Per-tile copy of the element ids, face slots and face list (kMetaBytes, after
-// the table block).
+// The tile's copy of its face slots, element ids, affine flags and face list in
+// shared memory (meta_bytes(DIM, count, list length), after the table block).
+template <int DIM>
 struct TileMeta {
-  int32_t eid[kMaxEpb];
-  FaceSlot slot[kMaxEpb * 6];
-  int8_t aff[kMaxEpb];
-  uint16_t fl[kFaceListMax];
+  FaceSlot slot_[kMaxEpb * 6];
+  int32_t eid_[kMaxEpb];
+  int8_t aff_[kMaxEpb];
+  __device__ __forceinline__ const FaceSlot& slot(int i) const { return slot_[i]; }
+  __device__ __forceinline__ FaceSlot& slot(int i) { return slot_[i]; }
+  __device__ __forceinline__ int eid(int el) const { return eid_[el]; }
+  __device__ __forceinline__ int aff(int el) const { return aff_[el]; }
 };
-static_assert(sizeof(TileMeta) <= kMetaBytes, "TileMeta exceeds its shared-memory block");
+static_assert(sizeof(TileMeta<3>) <= kMetaBytes, "tile meta exceeds its shared-memory block");
 
+// list: where to copy the tile's face list (nullptr: not needed; copied only
+// where some face has a finer rule)
 template <int DIM>
 __device__ __forceinline__ void load_meta(const int32_t* elist, const FaceSlot* slots, const int8_t* eaff,
-                                          const uint16_t* flists, const Tile& t, TileMeta* mt) {
+                                          const uint16_t* flists, const Tile& t, TileMeta<DIM>* mt, uint16_t* list) {
+  const uint16_t* fl = flists + t.flist;
+  const int len = list && (t.flags & kTileFine) ? 3 + 2 * fl[2] + fl[0] + fl[1] : 0;
   for (int w = threadIdx.x; w < t.count * 2 * DIM; w += blockDim.x) {
     const int el = w / (2 * DIM), k = w - el * 2 * DIM;
     const int e = elist[t.start + el];
     if (k == 0) {
-      mt->eid[el] = e;
-      mt->aff[el] = eaff[e];
+      mt->eid_[el] = e;
+      mt->aff_[el] = eaff[e];
     }
-    mt->slot[el * 2 * DIM + k] = slots[(int64_t)e * 2 * DIM + k];
+    mt->slot_[el * 2 * DIM + k] = slots[(int64_t)e * 2 * DIM + k];
   }
-  const uint16_t* fl = flists + t.flist;
-  const int len = 3 + 2 * fl[2] + fl[0] + fl[1];
-  for (int w = threadIdx.x; w < len; w += blockDim.x) mt->fl[w] = fl[w];
+  for (int w = threadIdx.x; w < len; w += blockDim.x) list[w] = fl[w];
 }
 
 // The tile's faces as dense work lists: the conforming ones, and the ones with
@@ -234,7 +247,7 @@ struct FaceGeo {
 // trace; faces with a finer shared rule are interpolated one face at a time in
 // the element's scratch.
 template <typename T, int DIM, int N>
-__device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Tile& t, const TileMeta* mt, int rhs,
+__device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Tile& t, const TileMeta<DIM>* mt, int rhs,
                                                 const T* tb, T* sm, const T* U) {
   using S = Shape<DIM, N>;
   constexpr int Q = S::Q, QF1 = S::QF1, FMAX = S::FMAX, FT = S::FT, NFACE = S::NFACE, PER = S::PER_TRACE;
@@ -249,7 +262,7 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
   // normal derivative c . grad_ref u from (u, du/dn_ref, tangential derivatives)
   // and store both at canonical point zc
   auto emit_vals = [&](int el, int k, int z0, int z1, T uv, T dn, T d0, T d1) {
-    const FaceSlot sl = mt->slot[el * 2 * DIM + k];
+    const FaceSlot sl = mt->slot(el * 2 * DIM + k);
     const int qf = sl.qf, ax = k >> 1;
     const int npts = DIM == 2 ? qf : qf * qf;
     const int zc = canon(DIM, sl.side, sl.orient, qf, z0, z1);
@@ -266,7 +279,7 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
     tr[npts] = g;
   };
   auto emit = [&](int el, int k, const T* src, int fs, int z0, int z1) {
-    const int z = z0 + mt->slot[el * 2 * DIM + k].qf * z1;
+    const int z = z0 + mt->slot(el * 2 * DIM + k).qf * z1;
     emit_vals(el, k, z0, z1, src[z], src[fs + z], orth ? T(0) : src[2 * fs + z],
               (DIM == 3 && !orth) ? src[3 * fs + z] : T(0));
   };
@@ -291,7 +304,7 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
       uf = fma(LL[sd * Q + r], v, uf);
       dn = fma(LL[(2 + sd) * Q + r], v, dn);
     }
-    if (orth && mt->slot[el * 2 * DIM + k].qf == Q) {
+    if (orth && mt->slot(el * 2 * DIM + k).qf == Q) {
       emit_vals(el, k, j0, j1, uf, dn, T(0), T(0));
       continue;
     }
@@ -324,10 +337,11 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
     __syncthreads();
   }
   // 3. conforming faces, all at once (orthogonal ones were stored in step 1)
-  const FaceList fl{mt->fl};
-  for (int w = threadIdx.x; w < (orth ? 0 : fl.nconf() * QF1); w += blockDim.x) {
-    const int i = w / QF1, j = w - i * QF1;
-    const int e = fl.conf(i), el = fl_el(e), k = fl_k(e);
+  for (int w = threadIdx.x; w < (orth ? 0 : ne * NFACE * QF1); w += blockDim.x) {
+    const int el = w / (NFACE * QF1);
+    const int rem = w - el * NFACE * QF1;
+    const int k = rem / QF1, j = rem - k * QF1;
+    if (mt->slot(el * 2 * DIM + k).qf != Q) continue;
     emit(el, k, F0 + el * PER + k * 4 * QF1, QF1, j % Q, j / Q);
   }
   // 4. faces with a finer shared rule (p-non-conforming): NSC faces per round,
@@ -336,35 +350,25 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
     constexpr int NSC = scratch_slots(DIM);
     constexpr int SL = 4 * (FT + FMAX);  // one slot: Ft [4][FT], Ff [4][FMAX]
     const int nfld = orth ? 2 : 4;
-    if constexpr (DIM == 2) {
-      // one scratch slot per face (slot k): all fine faces at once, as dense
-      // work lists grouped by the shared rule
-      static_assert(DIM != 2 || NSC == NFACE, "2D keeps one scratch slot per face");
-      auto per_i = [&](int qf) { return nfld * qf; };
-      for (int w = threadIdx.x; w < fl.fine_items(per_i); w += blockDim.x) {
-        int j, u;
-        fl.fine_at(per_i, w, j, u);
-        const int e = fl.fine(j), el = fl_el(e), k = fl_k(e), qf = fl_qf(e);
-        const int f = u / qf, z = u - f * qf;
-        const T* IT = tb + TabLayout::IT(N, qf);
-        const T* src = F0 + el * PER + k * 4 * QF1 + f * QF1;
-        T s = 0;
-#pragma unroll
-        for (int r = 0; r < Q; ++r) s = fma(IT[r * qf + z], src[r], s);
-        F0[el * PER + SC + k * SL + 4 * FT + f * FMAX + z] = s;
-      }
-      __syncthreads();
-      auto per_e = [&](int qf) { return qf; };
-      for (int w = threadIdx.x; w < fl.fine_items(per_e); w += blockDim.x) {
-        int j, z;
-        fl.fine_at(per_e, w, j, z);
-        const int e = fl.fine(j), el = fl_el(e), k = fl_k(e);
-        emit(el, k, F0 + el * PER + SC + k * SL + 4 * FT, FMAX, z, 0);
-      }
-      __syncthreads();
-    } else {
     for (int k0 = 0; k0 < NFACE; k0 += NSC) {
-      {
+      if constexpr (DIM == 2) {
+        for (int w = threadIdx.x; w < ne * NSC * nfld * qfm; w += blockDim.x) {
+          const int el = w / (NSC * nfld * qfm);
+          const int rem = w - el * NSC * nfld * qfm;
+          const int kk = rem / (nfld * qfm), r2 = rem - kk * nfld * qfm;
+          const int f = r2 / qfm, z = r2 - f * qfm;
+          const int k = k0 + kk;
+          const int qf = mt->slot(el * 2 * DIM + k).qf;
+          if (qf == Q || z >= qf) continue;
+          const T* IT = tb + TabLayout::IT(N, qf);
+          const T* src = F0 + el * PER + k * 4 * QF1 + f * QF1;
+          T s = 0;
+#pragma unroll
+          for (int r = 0; r < Q; ++r) s = fma(IT[r * qf + z], src[r], s);
+          F0[el * PER + SC + kk * SL + 4 * FT + f * FMAX + z] = s;
+        }
+        __syncthreads();
+      } else {
         for (int w = threadIdx.x; w < ne * NSC * nfld * Q * qfm; w += blockDim.x) {
           const int el = w / (NSC * nfld * Q * qfm);
           const int rem = w - el * NSC * nfld * Q * qfm;
@@ -372,7 +376,7 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
           const int f = r2 / (Q * qfm), r3 = r2 - f * Q * qfm;
           const int j1 = r3 / qfm, z0 = r3 - j1 * qfm;
           const int k = k0 + kk;
-          const int qf = mt->slot[el * 2 * DIM + k].qf;
+          const int qf = mt->slot(el * 2 * DIM + k).qf;
           if (qf == Q || z0 >= qf) continue;
           const T* IT = tb + TabLayout::IT(N, qf);
           const T* src = F0 + el * PER + k * 4 * QF1 + f * QF1 + j1 * Q;
@@ -389,7 +393,7 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
           const int f = r2 / npm, zz = r2 - f * npm;
           const int z1 = zz / qfm, z0 = zz - z1 * qfm;
           const int k = k0 + kk;
-          const int qf = mt->slot[el * 2 * DIM + k].qf;
+          const int qf = mt->slot(el * 2 * DIM + k).qf;
           if (qf == Q || z0 >= qf || z1 >= qf) continue;
           const T* IT = tb + TabLayout::IT(N, qf);
           const T* src = F0 + el * PER + SC + kk * SL + f * FT + z0;
@@ -405,23 +409,22 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
         const int kk = r2 / npm, zz = r2 - kk * npm;
         const int z0 = zz % qfm, z1 = zz / qfm;
         const int k = k0 + kk;
-        const int qf = mt->slot[el * 2 * DIM + k].qf;
+        const int qf = mt->slot(el * 2 * DIM + k).qf;
         if (qf == Q || z0 >= qf || z1 >= qf) continue;
         emit(el, k, F0 + el * PER + SC + kk * SL + 4 * FT, FMAX, z0, z1);
       }
       __syncthreads();
-    }
     }
   }
   __syncthreads();
 }
 
 template <typename T, int DIM, int N>
-__device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, TileMeta* mt, T* sm) {
+__device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, TileMeta<DIM>* mt, T* sm) {
   using S = Shape<DIM, N>;
   constexpr int PER = S::PER_TRACE;
   const int ne = t.count;
-  load_meta<DIM>(a.elist, a.slots, a.eaff, a.flists, t, mt);
+  load_meta<DIM>(a.elist, a.slots, a.eaff, a.flists, t, mt, nullptr);
   __syncthreads();
   // one output per thread (2D, and FP64 in 3D: more parallel work for the narrow
   // FP64 pipe) or one line per thread with the matrices as constant-bank operands
@@ -433,7 +436,7 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
     const T* BT = tb + TabLayout::BT(N);
     T* bA = sm;
     T* bB = sm + S::QV;
-    auto gx = [&](int el) { return a.x + rhs * a.ndof + a.dof_off[mt->eid[el]]; };
+    auto gx = [&](int el) { return a.x + rhs * a.ndof + a.dof_off[mt->eid(el)]; };
     if constexpr (DIM == 2) {
       cpt_io<T, N, N, 1, 0, Q, false>(gx, [&](int el) { return bB + el * PER; }, ne, BT);
       __syncthreads();
@@ -452,7 +455,7 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
   } else {
     for (int w = threadIdx.x; w < ne * S::NV; w += blockDim.x) {
       const int el = w / S::NV, i = w - el * S::NV;
-      sm[el * PER + i] = a.x[rhs * a.ndof + a.dof_off[mt->eid[el]] + i];
+      sm[el * PER + i] = a.x[rhs * a.ndof + a.dof_off[mt->eid(el)] + i];
     }
     __syncthreads();
     U = to_gauss<T, DIM, N>(sm, sm + S::QV, PER, ne);
@@ -460,7 +463,7 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
   if (a.ug) {
     for (int w = threadIdx.x; w < ne * S::QV; w += blockDim.x) {
       const int el = w / S::QV, q = w - el * S::QV;
-      a.ug[rhs * a.nquad + a.quad_off[mt->eid[el]] + q] = U[el * PER + q];
+      a.ug[rhs * a.nquad + a.quad_off[mt->eid(el)] + q] = U[el * PER + q];
     }
   }
   trace_all_faces<T, DIM, N>(a, t, mt, rhs, tb, sm, U);
@@ -471,9 +474,9 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
 // writes s and c_m t (m = 0..DIM-1; only c_a t where the tile is orthogonal) to
 // dst[f * fs + z0 + qf z1].
 template <typename T, int DIM, int N>
-__device__ __forceinline__ void face_flux(const ApplyArgs<T>& a, const TileMeta* mt, int rhs, const T* tb,
+__device__ __forceinline__ void face_flux(const ApplyArgs<T>& a, const TileMeta<DIM>* mt, int rhs, const T* tb,
                                           bool orth, int el, int k, int z0, int z1, T* dst, int fs) {
-  const FaceSlot sl = mt->slot[el * 2 * DIM + k];
+  const FaceSlot sl = mt->slot(el * 2 * DIM + k);
   const int qf = sl.qf, ax = k >> 1;
   const int npts = DIM == 2 ? qf : qf * qf;
   const int z = z0 + qf * z1;
@@ -518,7 +521,8 @@ __device__ __forceinline__ void face_flux(const ApplyArgs<T>& a, const TileMeta*
 // round: flux at the shared points, then projection back to the element's own
 // face points (TraceIProduct) into the per-face buffers.
 template <typename T, int DIM, int N>
-__device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Tile& t, const TileMeta* mt, int rhs,
+__device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Tile& t, const TileMeta<DIM>* mt,
+                                                const uint16_t* flist, int rhs,
                                                 const T* tb, T* F0, int per, bool orth) {
   using S = Shape<DIM, N>;
   constexpr int Q = S::Q, QF1 = S::QF1, FMAX = S::FMAX, FT = S::FT, NFACE = S::NFACE, NF = 1 + DIM;
@@ -528,11 +532,11 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
   const int ne = t.count;
   const int qfm = t.flags & kTileQfMask;
   const int npm = DIM == 2 ? qfm : qfm * qfm;
-  if constexpr (DIM == 2) {
+  if constexpr (DIM == 2 && dense_faces<T>()) {
     // one scratch slot per face (slot k): all fine faces at once, as dense work
     // lists grouped by the shared rule
     static_assert(DIM != 2 || NSC == NFACE, "2D keeps one scratch slot per face");
-    const FaceList fl{mt->fl};
+    const FaceList fl{flist};
     auto per_f = [&](int qf) { return qf; };
     for (int w = threadIdx.x; w < fl.fine_items(per_f); w += blockDim.x) {
       int j, z;
@@ -555,74 +559,74 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
       F0[el * per + k * NF * QF1 + f * QF1 + r] = s;
     }
     __syncthreads();
-    return;
-  }
-  for (int k0 = 0; k0 < NFACE; k0 += NSC) {
-    for (int w = threadIdx.x; w < ne * NSC * npm; w += blockDim.x) {
-      const int el = w / (NSC * npm), r2 = w - el * NSC * npm;
-      const int kk = r2 / npm, zz = r2 - kk * npm;
-      const int z0 = zz % qfm, z1 = zz / qfm;
-      const int k = k0 + kk;
-      const int qf = mt->slot[el * 2 * DIM + k].qf;
-      if (qf == Q || z0 >= qf || z1 >= qf) continue;
-      face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, z0, z1, F0 + el * per + SC + kk * SL + NF * FT, FMAX);
-    }
-    __syncthreads();
-    if constexpr (DIM == 2) {
-      for (int w = threadIdx.x; w < ne * NSC * NF * Q; w += blockDim.x) {
-        const int el = w / (NSC * NF * Q);
-        const int rem = w - el * NSC * NF * Q;
-        const int kk = rem / (NF * Q), r2 = rem - kk * NF * Q;
-        const int f = r2 / Q, r = r2 - f * Q;
+  } else {
+    for (int k0 = 0; k0 < NFACE; k0 += NSC) {
+      for (int w = threadIdx.x; w < ne * NSC * npm; w += blockDim.x) {
+        const int el = w / (NSC * npm), r2 = w - el * NSC * npm;
+        const int kk = r2 / npm, zz = r2 - kk * npm;
+        const int z0 = zz % qfm, z1 = zz / qfm;
         const int k = k0 + kk;
-        const int qf = mt->slot[el * 2 * DIM + k].qf;
-        if (qf == Q || (orth && f != 0 && f != 1 + (k >> 1))) continue;
-        const T* II = tb + TabLayout::II(N, qf);
-        const T* src = F0 + el * per + SC + kk * SL + NF * FT + f * FMAX;
-        T s = 0;
-        for (int z = 0; z < qf; ++z) s = fma(II[z * Q + r], src[z], s);
-        F0[el * per + k * NF * QF1 + f * QF1 + r] = s;
+        const int qf = mt->slot(el * 2 * DIM + k).qf;
+        if (qf == Q || z0 >= qf || z1 >= qf) continue;
+        face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, z0, z1, F0 + el * per + SC + kk * SL + NF * FT, FMAX);
       }
       __syncthreads();
-    } else {
-      for (int w = threadIdx.x; w < ne * NSC * NF * qfm * Q; w += blockDim.x) {
-        const int el = w / (NSC * NF * qfm * Q);
-        const int rem = w - el * NSC * NF * qfm * Q;
-        const int kk = rem / (NF * qfm * Q), r2 = rem - kk * NF * qfm * Q;
-        const int f = r2 / (qfm * Q), r3 = r2 - f * qfm * Q;
-        const int z1 = r3 / Q, r0 = r3 - z1 * Q;
-        const int k = k0 + kk;
-        const int qf = mt->slot[el * 2 * DIM + k].qf;
-        if (qf == Q || z1 >= qf || (orth && f != 0 && f != 1 + (k >> 1))) continue;
-        const T* II = tb + TabLayout::II(N, qf);
-        const T* src = F0 + el * per + SC + kk * SL + NF * FT + f * FMAX + qf * z1;
-        T s = 0;
-        for (int z0 = 0; z0 < qf; ++z0) s = fma(II[z0 * Q + r0], src[z0], s);
-        F0[el * per + SC + kk * SL + f * FT + z1 * Q + r0] = s;
+      if constexpr (DIM == 2) {
+        for (int w = threadIdx.x; w < ne * NSC * NF * Q; w += blockDim.x) {
+          const int el = w / (NSC * NF * Q);
+          const int rem = w - el * NSC * NF * Q;
+          const int kk = rem / (NF * Q), r2 = rem - kk * NF * Q;
+          const int f = r2 / Q, r = r2 - f * Q;
+          const int k = k0 + kk;
+          const int qf = mt->slot(el * 2 * DIM + k).qf;
+          if (qf == Q || (orth && f != 0 && f != 1 + (k >> 1))) continue;
+          const T* II = tb + TabLayout::II(N, qf);
+          const T* src = F0 + el * per + SC + kk * SL + NF * FT + f * FMAX;
+          T s = 0;
+          for (int z = 0; z < qf; ++z) s = fma(II[z * Q + r], src[z], s);
+          F0[el * per + k * NF * QF1 + f * QF1 + r] = s;
+        }
+        __syncthreads();
+      } else {
+        for (int w = threadIdx.x; w < ne * NSC * NF * qfm * Q; w += blockDim.x) {
+          const int el = w / (NSC * NF * qfm * Q);
+          const int rem = w - el * NSC * NF * qfm * Q;
+          const int kk = rem / (NF * qfm * Q), r2 = rem - kk * NF * qfm * Q;
+          const int f = r2 / (qfm * Q), r3 = r2 - f * qfm * Q;
+          const int z1 = r3 / Q, r0 = r3 - z1 * Q;
+          const int k = k0 + kk;
+          const int qf = mt->slot(el * 2 * DIM + k).qf;
+          if (qf == Q || z1 >= qf || (orth && f != 0 && f != 1 + (k >> 1))) continue;
+          const T* II = tb + TabLayout::II(N, qf);
+          const T* src = F0 + el * per + SC + kk * SL + NF * FT + f * FMAX + qf * z1;
+          T s = 0;
+          for (int z0 = 0; z0 < qf; ++z0) s = fma(II[z0 * Q + r0], src[z0], s);
+          F0[el * per + SC + kk * SL + f * FT + z1 * Q + r0] = s;
+        }
+        __syncthreads();
+        for (int w = threadIdx.x; w < ne * NSC * NF * QF1; w += blockDim.x) {
+          const int el = w / (NSC * NF * QF1);
+          const int rem = w - el * NSC * NF * QF1;
+          const int kk = rem / (NF * QF1), r2 = rem - kk * NF * QF1;
+          const int f = r2 / QF1, r = r2 - f * QF1;
+          const int r0 = r % Q, r1 = r / Q;
+          const int k = k0 + kk;
+          const int qf = mt->slot(el * 2 * DIM + k).qf;
+          if (qf == Q || (orth && f != 0 && f != 1 + (k >> 1))) continue;
+          const T* II = tb + TabLayout::II(N, qf);
+          const T* src = F0 + el * per + SC + kk * SL + f * FT + r0;
+          T s = 0;
+          for (int z1 = 0; z1 < qf; ++z1) s = fma(II[z1 * Q + r1], src[z1 * Q], s);
+          F0[el * per + k * NF * QF1 + f * QF1 + r] = s;
+        }
+        __syncthreads();
       }
-      __syncthreads();
-      for (int w = threadIdx.x; w < ne * NSC * NF * QF1; w += blockDim.x) {
-        const int el = w / (NSC * NF * QF1);
-        const int rem = w - el * NSC * NF * QF1;
-        const int kk = rem / (NF * QF1), r2 = rem - kk * NF * QF1;
-        const int f = r2 / QF1, r = r2 - f * QF1;
-        const int r0 = r % Q, r1 = r / Q;
-        const int k = k0 + kk;
-        const int qf = mt->slot[el * 2 * DIM + k].qf;
-        if (qf == Q || (orth && f != 0 && f != 1 + (k >> 1))) continue;
-        const T* II = tb + TabLayout::II(N, qf);
-        const T* src = F0 + el * per + SC + kk * SL + f * FT + r0;
-        T s = 0;
-        for (int z1 = 0; z1 < qf; ++z1) s = fma(II[z1 * Q + r1], src[z1 * Q], s);
-        F0[el * per + k * NF * QF1 + f * QF1 + r] = s;
-      }
-      __syncthreads();
     }
   }
 }
 
 template <typename T, int DIM, int N>
-__device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, TileMeta* mt, T* sm) {
+__device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, TileMeta<DIM>* mt, T* sm) {
   using S = Shape<DIM, N>;
   constexpr int Q = S::Q, QV = S::QV, NV = S::NV, QF1 = S::QF1, NFACE = S::NFACE, PER = S::PER_MAIN;
   constexpr int NF = 1 + DIM;
@@ -637,19 +641,21 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   T* G2 = sm + 3 * QV;
   T* R = sm + (1 + DIM) * QV;
   T* const F0 = sm + (2 + DIM) * QV;
-  load_meta<DIM>(a.elist, a.slots, a.eaff, a.flists, t, mt);
+  // the face list follows the element buffers (kFaceListBytes, FP64 only)
+  uint16_t* flist = dense_faces<T>() ? reinterpret_cast<uint16_t*>(sm + ne * PER) : nullptr;
+  load_meta<DIM>(a.elist, a.slots, a.eaff, a.flists, t, mt, flist);
   __syncthreads();
   if (a.ug) {
     for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
       const int el = w / QV, q = w - el * QV;
-      U[el * PER + q] = a.ug[rhs * a.nquad + a.quad_off[mt->eid[el]] + q];
+      U[el * PER + q] = a.ug[rhs * a.nquad + a.quad_off[mt->eid(el)] + q];
     }
     __syncthreads();
   } else {
     // recompute the Gauss values: 2D G0 -> G1 -> U, 3D G0 -> G1 -> G2 -> U
     for (int w = threadIdx.x; w < ne * NV; w += blockDim.x) {
       const int el = w / NV, i = w - el * NV;
-      G0[el * PER + i] = a.x[rhs * a.ndof + a.dof_off[mt->eid[el]] + i];
+      G0[el * PER + i] = a.x[rhs * a.ndof + a.dof_off[mt->eid(el)] + i];
     }
     __syncthreads();
     const T* BT = tb + TabLayout::BT(N);
@@ -685,69 +691,151 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   {
     const T* DT = tb + TabLayout::DT(N);
     const int nvol = ne * QV;
-    const FaceList fl{mt->fl};
-    for (int w = threadIdx.x; w < nvol + fl.nconf() * QF1; w += blockDim.x) {
-      if (w >= nvol) {
-        const int v = w - nvol;
-        const int i = v / QF1, j = v - i * QF1;
-        const int e = fl.conf(i), el = fl_el(e), k = fl_k(e);
-        face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
-        continue;
-      }
-      const int el = w / QV, q = w - el * QV;
-      const int e = mt->eid[el];
-      T* b = sm + el * PER;
-      T g[DIM];
-      if constexpr (line_mode<T, DIM>()) {
-#pragma unroll
-        for (int m = 0; m < DIM; ++m) g[m] = b[(1 + m) * QV + q];
-      } else {
-        const int qc[3] = {q % Q, (q / Q) % Q, DIM == 3 ? q / (Q * Q) : 0};
-#pragma unroll
-        for (int m = 0; m < DIM; ++m) {
-          const int sm_ = m == 0 ? 1 : (m == 1 ? Q : Q * Q);
-          const T* u = b + q - qc[m] * sm_;
-          T acc = 0;
-#pragma unroll
-          for (int r = 0; r < Q; ++r) acc = fma(DT[r * Q + qc[m]], u[r * sm_], acc);
-          g[m] = acc;
+    // two copies of the pass: the FP32 one over all faces with the others skipped
+    // (the shape its compiled code is fastest in), the FP64 one over the tile's
+    // list of conforming faces where the tile has finer rules
+    if constexpr (!dense_faces<T>()) {
+      for (int w = threadIdx.x; w < nvol + ne * NFACE * QF1; w += blockDim.x) {
+        if (w >= nvol) {
+          const int v = w - nvol;
+          const int el = v / (NFACE * QF1);
+          const int rem = v - el * NFACE * QF1;
+          const int k = rem / QF1, j = rem - k * QF1;
+          if (mt->slot(el * 2 * DIM + k).qf != Q) continue;
+          face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
+          continue;
         }
-      }
-      // deformed element: factors per point; affine element: constants times the
-      // Gauss weight.  The gradient is scaled first (kappa, weight), so that each
-      // multiply that is 1 is skipped.
-      const bool eaf = mt->aff[el] != 0;
-      const T* geo = a.vgeo + a.vgoff[e] + (eaf ? 0 : q);
-      const int gs = eaf ? 1 : QV;
-      T lwj = a.lambda * geo[DIM == 2 ? 3 * gs : 6 * gs];
-      if (eaf || a.kappa) {
-        T wk = T(1);
-        if (eaf) {
-          const T* gw = tb + TabLayout::GW(N, Q);
-          T wq = gw[q % Q] * gw[(q / Q) % Q];
-          if constexpr (DIM == 3) wq *= gw[q / (Q * Q)];
-          lwj *= wq;
-          wk = wq;
+        const int el = w / QV, q = w - el * QV;
+        const int e = mt->eid(el);
+        T* b = sm + el * PER;
+        T g[DIM];
+        if constexpr (line_mode<T, DIM>()) {
+  #pragma unroll
+          for (int m = 0; m < DIM; ++m) g[m] = b[(1 + m) * QV + q];
+        } else {
+          const int qc[3] = {q % Q, (q / Q) % Q, DIM == 3 ? q / (Q * Q) : 0};
+  #pragma unroll
+          for (int m = 0; m < DIM; ++m) {
+            const int sm_ = m == 0 ? 1 : (m == 1 ? Q : Q * Q);
+            const T* u = b + q - qc[m] * sm_;
+            T acc = 0;
+  #pragma unroll
+            for (int r = 0; r < Q; ++r) acc = fma(DT[r * Q + qc[m]], u[r * sm_], acc);
+            g[m] = acc;
+          }
         }
-        if (a.kappa) wk = eaf ? wk * a.kappa[a.quad_off[e] + q] : a.kappa[a.quad_off[e] + q];
-#pragma unroll
-        for (int m = 0; m < DIM; ++m) g[m] *= wk;
+        // deformed element: factors per point; affine element: constants times the
+        // Gauss weight.  The gradient is scaled first (kappa, weight), so that each
+        // multiply that is 1 is skipped.
+        const bool eaf = mt->aff(el) != 0;
+        const T* geo = a.vgeo + a.vgoff[e] + (eaf ? 0 : q);
+        const int gs = eaf ? 1 : QV;
+        T lwj = a.lambda * geo[DIM == 2 ? 3 * gs : 6 * gs];
+        if (eaf || a.kappa) {
+          T wk = T(1);
+          if (eaf) {
+            const T* gw = tb + TabLayout::GW(N, Q);
+            T wq = gw[q % Q] * gw[(q / Q) % Q];
+            if constexpr (DIM == 3) wq *= gw[q / (Q * Q)];
+            lwj *= wq;
+            wk = wq;
+          }
+          if (a.kappa) wk = eaf ? wk * a.kappa[a.quad_off[e] + q] : a.kappa[a.quad_off[e] + q];
+  #pragma unroll
+          for (int m = 0; m < DIM; ++m) g[m] *= wk;
+        }
+        if constexpr (DIM == 2) {
+          b[QV + q] = geo[0] * g[0] + geo[gs] * g[1];
+          b[2 * QV + q] = geo[gs] * g[0] + geo[2 * gs] * g[1];
+        } else {
+          const T a00 = geo[0], a01 = geo[gs], a02 = geo[2 * gs], a11 = geo[3 * gs], a12 = geo[4 * gs],
+                  a22 = geo[5 * gs];
+          b[QV + q] = a00 * g[0] + a01 * g[1] + a02 * g[2];
+          b[2 * QV + q] = a01 * g[0] + a11 * g[1] + a12 * g[2];
+          b[3 * QV + q] = a02 * g[0] + a12 * g[1] + a22 * g[2];
+        }
+        b[(1 + DIM) * QV + q] = lwj * b[q];
       }
-      if constexpr (DIM == 2) {
-        b[QV + q] = geo[0] * g[0] + geo[gs] * g[1];
-        b[2 * QV + q] = geo[gs] * g[0] + geo[2 * gs] * g[1];
-      } else {
-        const T a00 = geo[0], a01 = geo[gs], a02 = geo[2 * gs], a11 = geo[3 * gs], a12 = geo[4 * gs],
-                a22 = geo[5 * gs];
-        b[QV + q] = a00 * g[0] + a01 * g[1] + a02 * g[2];
-        b[2 * QV + q] = a01 * g[0] + a11 * g[1] + a12 * g[2];
-        b[3 * QV + q] = a02 * g[0] + a12 * g[1] + a22 * g[2];
+    } else {
+      const FaceList fl{flist};
+      // conforming faces: every face of a tile without finer rules; otherwise the
+      // tile's list of them
+      const bool dense = fine;
+      const int nfi = dense ? fl.nconf() * QF1 : ne * NFACE * QF1;
+      for (int w = threadIdx.x; w < nvol + nfi; w += blockDim.x) {
+        if (w >= nvol) {
+          const int v = w - nvol;
+          int el, k, j;
+          if (dense) {
+            const int i = v / QF1, e = fl.conf(i);
+            j = v - i * QF1;
+            el = fl_el(e);
+            k = fl_k(e);
+          } else {
+            el = v / (NFACE * QF1);
+            const int rem = v - el * NFACE * QF1;
+            k = rem / QF1;
+            j = rem - k * QF1;
+            if (fine && mt->slot(el * 2 * DIM + k).qf != Q) continue;
+          }
+          face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
+          continue;
+        }
+        const int el = w / QV, q = w - el * QV;
+        const int e = mt->eid(el);
+        T* b = sm + el * PER;
+        T g[DIM];
+        if constexpr (line_mode<T, DIM>()) {
+  #pragma unroll
+          for (int m = 0; m < DIM; ++m) g[m] = b[(1 + m) * QV + q];
+        } else {
+          const int qc[3] = {q % Q, (q / Q) % Q, DIM == 3 ? q / (Q * Q) : 0};
+  #pragma unroll
+          for (int m = 0; m < DIM; ++m) {
+            const int sm_ = m == 0 ? 1 : (m == 1 ? Q : Q * Q);
+            const T* u = b + q - qc[m] * sm_;
+            T acc = 0;
+  #pragma unroll
+            for (int r = 0; r < Q; ++r) acc = fma(DT[r * Q + qc[m]], u[r * sm_], acc);
+            g[m] = acc;
+          }
+        }
+        // deformed element: factors per point; affine element: constants times the
+        // Gauss weight.  The gradient is scaled first (kappa, weight), so that each
+        // multiply that is 1 is skipped.
+        const bool eaf = mt->aff(el) != 0;
+        const T* geo = a.vgeo + a.vgoff[e] + (eaf ? 0 : q);
+        const int gs = eaf ? 1 : QV;
+        T lwj = a.lambda * geo[DIM == 2 ? 3 * gs : 6 * gs];
+        if (eaf || a.kappa) {
+          T wk = T(1);
+          if (eaf) {
+            const T* gw = tb + TabLayout::GW(N, Q);
+            T wq = gw[q % Q] * gw[(q / Q) % Q];
+            if constexpr (DIM == 3) wq *= gw[q / (Q * Q)];
+            lwj *= wq;
+            wk = wq;
+          }
+          if (a.kappa) wk = eaf ? wk * a.kappa[a.quad_off[e] + q] : a.kappa[a.quad_off[e] + q];
+  #pragma unroll
+          for (int m = 0; m < DIM; ++m) g[m] *= wk;
+        }
+        if constexpr (DIM == 2) {
+          b[QV + q] = geo[0] * g[0] + geo[gs] * g[1];
+          b[2 * QV + q] = geo[gs] * g[0] + geo[2 * gs] * g[1];
+        } else {
+          const T a00 = geo[0], a01 = geo[gs], a02 = geo[2 * gs], a11 = geo[3 * gs], a12 = geo[4 * gs],
+                  a22 = geo[5 * gs];
+          b[QV + q] = a00 * g[0] + a01 * g[1] + a02 * g[2];
+          b[2 * QV + q] = a01 * g[0] + a11 * g[1] + a12 * g[2];
+          b[3 * QV + q] = a02 * g[0] + a12 * g[1] + a22 * g[2];
+        }
+        b[(1 + DIM) * QV + q] = lwj * b[q];
       }
-      b[(1 + DIM) * QV + q] = lwj * b[q];
     }
   }
   __syncthreads();
-  if (fine) lift_fine_faces<T, DIM, N>(a, t, mt, rhs, tb, F0, PER, orth);
+  if (fine) lift_fine_faces<T, DIM, N>(a, t, mt, flist, rhs, tb, F0, PER, orth);
   // face field P = s + sum_{tangential m} D_m^T (c_m t) on the face (the
   // tangential part of the lift after the transposed gradient); c_a t stays as
   // is and is lifted with l'(+-1)
@@ -817,7 +905,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   }
   // y = (B^T x B^T (x B^T)) H; the last contraction writes y in global memory
   const T* BB = tb + TabLayout::BB(N);
-  auto gy = [&](int el) { return a.y + rhs * a.ndof + a.dof_off[mt->eid[el]]; };
+  auto gy = [&](int el) { return a.y + rhs * a.ndof + a.dof_off[mt->eid(el)]; };
   T* res = nullptr;
   if constexpr (DIM == 2) {
     cpt<T, Q, Q, 1, 0, N, false>(U, G0, PER, ne, BB);
@@ -842,7 +930,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
     __syncthreads();
     for (int w = threadIdx.x; w < ne * NV; w += blockDim.x) {
       const int el = w / NV, i = w - el * NV;
-      a.y[rhs * a.ndof + a.dof_off[mt->eid[el]] + i] = res[el * PER + i];
+      a.y[rhs * a.ndof + a.dof_off[mt->eid(el)] + i] = res[el * PER + i];
     }
   } else {
     (void)res;
@@ -850,8 +938,8 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   }
 }
 
-// Shared memory of a CTA: [table block of its order (table_block_bytes)][TileMeta
-// (kMetaBytes)][elements].  A CTA runs a list of tiles of one order (its share
+// Shared memory of a CTA: [table block of its order (table_block_bytes)][tile
+// meta (kMetaBytes)][elements].  A CTA runs a list of tiles of one order (its share
 // of the launch, tiles cta_off[b] .. cta_off[b+1]-1) one after the other, with the
 // order's tables loaded once.
 #define SIP_ORDER_SWITCH(FN) \
@@ -870,7 +958,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
 template <typename T, int DIM, int N, bool MAIN>
 __device__ __forceinline__ void run_tiles(const ApplyArgs<T>& a, int ti0, int ti1, int rhs, unsigned char* smem_raw) {
   T* tb = reinterpret_cast<T*>(smem_raw);
-  TileMeta* mt = reinterpret_cast<TileMeta*>(smem_raw + table_block_bytes(sizeof(T), N));
+  TileMeta<DIM>* mt = reinterpret_cast<TileMeta<DIM>*>(smem_raw + table_block_bytes(sizeof(T), N));
   T* sm = reinterpret_cast<T*>(smem_raw + table_block_bytes(sizeof(T), N) + kMetaBytes);
   load_tables<T, N>(tb);
   for (int ti = ti0; ti < ti1; ++ti) {
@@ -892,8 +980,16 @@ __global__ void __launch_bounds__(256) k_trace(ApplyArgs<T> a) {
 #undef SIP_TRACE_CASE
 }
 
+// Launch bounds of the main kernel, set by the translation unit that
+// instantiates it: FP64 asks for registers for 4 resident CTAs per SM (room for
+// the wider values without spilling), FP32 gives no hint, which keeps its
+// register count and so its occupancy highest.
+#ifndef SIP_MAIN_LAUNCH_BOUNDS
+#define SIP_MAIN_LAUNCH_BOUNDS 256
+#endif
+
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_main(ApplyArgs<T> a) {
+__global__ void __launch_bounds__(SIP_MAIN_LAUNCH_BOUNDS) k_main(ApplyArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ti0 = a.cta_off[blockIdx.x], ti1 = a.cta_off[blockIdx.x + 1];
   if (ti0 >= ti1) return;

@@ -166,7 +166,7 @@ extern "C" int sip_set_tiling(sip_handle* h, int precision, const sip_tiling* t)
   bool pers = false;
   if (t) {
     for (int P = 0; P <= kMaxOrder; ++P) {
-      if (t->epb[P] < 0 || t->epb[P] > kMaxEpb) return fail(SIP_ERR_ARG, "elements per tile must be in 0..32");
+      if (t->epb[P] < 0 || t->epb[P] > kMaxEpb) return fail(SIP_ERR_ARG, "elements per tile must be in 0.." + std::to_string(kMaxEpb));
       e[P + 1] = t->epb[P];
     }
     if (t->ctas_per_sm < 0) return fail(SIP_ERR_ARG, "ctas_per_sm must be >= 0");

@@ -150,7 +150,8 @@ int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_p
     for (const Tile& t : s.tiles) {
       const size_t fixed = (size_t)table_block_bytes(es, t.n) + kMetaBytes;
       s.smem_t = std::max(s.smem_t, fixed + (size_t)t.count * per_elem_trace(p.dim, t.n) * es);
-      s.smem_m = std::max(s.smem_m, fixed + (size_t)t.count * per_elem_main(p.dim, t.n) * es);
+      s.smem_m = std::max(s.smem_m, fixed + (size_t)t.count * per_elem_main(p.dim, t.n) * es +
+                                        (precision == SIP_FP64 ? kFaceListBytes : 0));
     }
   };
   // one CTA per tile of the largest size epb allows: the tile count and shared

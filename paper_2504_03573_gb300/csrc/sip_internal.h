@@ -112,7 +112,7 @@ constexpr int kFaceBnd = 1;     // boundary face
 constexpr int kFaceOrth = 2;    // c = J^-1 n has no tangential component on either side
 constexpr int kFaceAffine = 4;  // both sides affine: geometry stored as constants (W without the weight)
 
-struct FaceSlot {
+struct FaceSlot {  // 8 bytes
   int32_t face;    // face id
   int8_t side;     // 0: minus side (or boundary), 1: plus side
   int8_t orient;   // plus side: bit0 flip t0, bit1 flip t1, bit2 transpose; else 0
@@ -137,14 +137,16 @@ struct Tile {
 // [nconf, nfine, ngroups, (qf, count) x ngroups, nconf conforming entries
 // (shared rule = own Q points), nfine entries with a finer shared rule in
 // ascending qf (the groups)]; entry = el | k << 5 | qf << 8.
-constexpr int kFaceListMax = 3 + 2 * 16 + kMaxEpb * 6;
+constexpr int kFaceListMax = 3 + 2 * 16 + kMaxEpb * 6;  // at most 16 groups (qf <= 16)
 constexpr int fl_el(int e) { return e & 31; }
 constexpr int fl_k(int e) { return (e >> 5) & 7; }
 constexpr int fl_qf(int e) { return e >> 8; }
 
-// per-tile copy of element ids, face slots, affine flags and the face list,
-// after the table block
-constexpr int kMetaBytes = ((kMaxEpb * (4 + 6 * (int)sizeof(FaceSlot) + 1) + 2 * kFaceListMax + 15) / 16) * 16;
+// per-tile copy of the face slots, element ids and affine flags, after the table
+// block (a fixed size, so that the element buffers that follow sit at a
+// compile-time offset); the face list, where used, follows the element buffers
+constexpr int kMetaBytes = ((kMaxEpb * (6 * (int)sizeof(FaceSlot) + 4 + 1) + 15) / 16) * 16;
+constexpr int kFaceListBytes = ((2 * kFaceListMax + 15) / 16) * 16;
 
 // Host plan: everything the device needs, in FP64.
 struct Plan {
