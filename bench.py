@@ -43,7 +43,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # DRAM bytes (read + write) per launch of the FP64 main kernel, from one ncu capture
 # of that workload with the current kernels (profiles/apply_<workload>.md)
-NCU_MAIN_TRAFFIC = {"c2_2d_64x64_jitter_p2to6": 10.892544e6, "c3_3d_32cube_p4": 183.451392e6 + 23.756288e6}
+NCU_MAIN_TRAFFIC = {"c2_2d_64x64_jitter_p2to6": 10.928896e6, "c3_3d_32cube_p4": 183.080960e6 + 23.036928e6}
 
 
 def peaks():
@@ -206,7 +206,19 @@ def run_gb300(args):
     op = g.SipOperator.from_mesh(mesh)
     n = op.ndof
     # tile shapes chosen by the library's autotuner (set-up, outside the timed region)
-    tiling = {"fp64": op.autotune(g.SIP_FP64), "fp32": op.autotune(g.SIP_FP32)} if not args.no_tune else None
+    precs = {"fp64": g.SIP_FP64, "fp32": g.SIP_FP32}
+    if args.tiling:
+        # a schedule saved by an earlier run (--save-tiling), e.g. to profile exactly it
+        saved = json.load(open(args.tiling))
+        tiling = {k: op.set_tiling(precs[k], v["epb_by_order"], v["ctas_per_sm"], v["persistent"], v["threads"])
+                  for k, v in saved.items()}
+    elif not args.no_tune:
+        tiling = {k: op.autotune(p) for k, p in precs.items()}
+    else:
+        tiling = None
+    if args.save_tiling:
+        with open(args.save_tiling, "w") as f:
+            json.dump({k: op.tiling(p) for k, p in precs.items()}, f)
     x = torch.tensor(si.random_vector(n, 0), device="cuda")
     y = torch.empty_like(x)
     x32 = x.float()
@@ -357,6 +369,8 @@ def main():
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--tiling", default=None, help="install the schedule saved by --save-tiling instead of tuning")
+    ap.add_argument("--save-tiling", default=None, help="write the schedule in use to this JSON file")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     args = ap.parse_args()
     if args.warmup < 3:

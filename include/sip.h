@@ -233,9 +233,9 @@ int  sip_autotune(sip_handle* h, int precision, int reps, void* stream);
 
 /* A launch schedule of the apply kernels. */
 typedef struct sip_tiling {
-    int32_t epb[SIP_MAX_ORDER + 1]; /* largest elements per tile for order P, P = 0..SIP_MAX_ORDER
+    int32_t epb[SIP_MAX_ORDER + 1]; /* elements per tile, at most, for order P, P = 0..SIP_MAX_ORDER
                                        (set: 0 = the default for the order, at most 32;
-                                       get: 0 where the order is absent) */
+                                       get: the value in use, 0 where the order is absent) */
     int32_t ctas_per_sm;            /* resident CTAs per SM balanced for (set: 0 = as many as
                                        fit, at most the tiles per SM that epb gives; larger
                                        values are capped at the occupancy) */

@@ -149,7 +149,10 @@ extern "C" int sip_get_tiling(const sip_handle* h, int precision, sip_tiling* ou
   if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
   const int pi = precision == SIP_FP32 ? 1 : 0;
   std::memset(out, 0, sizeof(*out));
-  for (const Tile& t : h->tiles_h[pi]) out->epb[t.n - 1] = std::max(out->epb[t.n - 1], (int32_t)t.count);
+  for (const Tile& t : h->tiles_h[pi]) {
+    const int set = h->epb[pi][t.n];
+    out->epb[t.n - 1] = std::min(kMaxEpb, set > 0 ? set : apply_epb(h->plan.dim, t.n, precision, h->threads[pi]));
+  }
   out->ctas_per_sm = h->ctas_per_sm[pi];
   out->persistent = h->persistent[pi];
   out->threads = h->threads[pi];
