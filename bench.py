@@ -41,6 +41,10 @@ METRIC = "SIP apply GDoF/s (FP64 vs FP32-refined) and CG time to 1e-10 residual"
 FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
+# right-hand sides per apply: the batched 24^3 workload applies to a batch of 32
+# N(0,1) vectors (seed 4) in one launch pair; the others to one vector (seed 0)
+NRHS = {"c4_3d_24cube_jitter_p2to7": 32}
+
 # DRAM bytes (read + write) per launch of the FP64 main kernel, from one ncu capture
 # of that workload with the current kernels (profiles/apply_<workload>.md)
 NCU_MAIN_TRAFFIC = {"c2_2d_64x64_jitter_p2to6": 10.928896e6, "c3_3d_32cube_p4": 183.080960e6 + 23.036928e6}
@@ -135,13 +139,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_apply_rate(mesh, budget_s=12.0, seed=0):
+def oracle_apply_rate(mesh, budget_s=12.0, seed=0, nrhs=1):
     """The oracle as it stands on a bounded sample: rows of A for a prefix of a
-    shuffled element list, built from the local blocks and applied to x, until
-    the time budget is spent.  Returns (DOF/s, dofs done, elements, seconds)."""
+    shuffled element list, built from the local blocks and applied to x (nrhs
+    columns), until the time budget is spent.  Returns (DOF/s counted per
+    right-hand side, dofs done, elements, seconds, cores)."""
     from oracle import SipOracle
     orc = SipOracle(mesh, lam=mesh.lam)
-    x = si.random_vector(orc.ndof, 0)
+    x = si.random_vector(orc.ndof, 0) if nrhs == 1 else si.random_rhs_batch(nrhs, orc.ndof, 4).T.copy()
     order = np.random.default_rng(seed).permutation(mesh.n_elem)
     t0 = time.perf_counter()
     c0 = time.process_time()
@@ -150,7 +155,7 @@ def oracle_apply_rate(mesh, budget_s=12.0, seed=0):
         els = order[i:i + 8]
         R = orc.rows_for_elements(els)
         _ = R @ x
-        done += R.shape[0]
+        done += R.shape[0] * nrhs
         nel += len(els)
         if time.perf_counter() - t0 > budget_s:
             break
@@ -164,10 +169,11 @@ def run_reference(args):
     if rank != 0:
         return 0
     mesh = si.workload(args.workload)
+    nrhs = NRHS.get(args.workload, 1)
     budget = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     rates = []
     for k in range(args.warmup + args.steps):
-        r, done, nel, dt, cores = oracle_apply_rate(mesh, budget_s=budget, seed=k)
+        r, done, nel, dt, cores = oracle_apply_rate(mesh, budget_s=budget, seed=k, nrhs=nrhs)
         if k >= args.warmup:
             rates.append((r, done, nel, dt, cores))
     val = statistics.median(r[0] for r in rates) / 1e9
@@ -177,10 +183,10 @@ def run_reference(args):
         "ms_per_step": 1e3 * statistics.median(r[3] for r in rates),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "precision": "fp64", "l2": "n/a (host)"},
+        "config": {"workload": args.workload, "nrhs": nrhs, "precision": "fp64", "l2": "n/a (host)"},
         "cpu_baseline": {"value": val, "unit": "GDoF/s", "cores": round(max(r[4] for r in rates), 2),
                          "kind": "oracle",
-                         "sample": f"rows of {rates[0][2]} elements ({rates[0][1]} DOFs) per step, "
+                         "sample": f"rows of {rates[0][2]} elements ({rates[0][1]} DOF-columns) per step, "
                                    f"{budget:.0f} s budget; cores = CPU time / wall time"},
         "e2e": {"value": val, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -205,6 +211,7 @@ def run_gb300(args):
     mesh = si.workload(args.workload)
     op = g.SipOperator.from_mesh(mesh)
     n = op.ndof
+    nrhs = NRHS.get(args.workload, 1)
     # tile shapes chosen by the library's autotuner (set-up, outside the timed region)
     precs = {"fp64": g.SIP_FP64, "fp32": g.SIP_FP32}
     if args.tiling:
@@ -219,7 +226,8 @@ def run_gb300(args):
     if args.save_tiling:
         with open(args.save_tiling, "w") as f:
             json.dump({k: op.tiling(p) for k, p in precs.items()}, f)
-    x = torch.tensor(si.random_vector(n, 0), device="cuda")
+    xhost = si.random_vector(n, 0) if nrhs == 1 else si.random_rhs_batch(nrhs, n, 4)
+    x = torch.tensor(xhost, device="cuda")
     y = torch.empty_like(x)
     x32 = x.float()
     y32 = torch.empty_like(x32)
@@ -260,7 +268,7 @@ def run_gb300(args):
     clocks = clk.summary()
     t_step = sum(ms) / len(ms) / 1e3
     t_max = max_over_ranks(t_step, world, device="cuda")
-    value = job_throughput(n, world, t_max) / 1e9
+    value = job_throughput(nrhs * n, world, t_max) / 1e9
 
     # ---- FP32 apply (same protocol)
     ms32, kt32, _ = timed_applies(x32, y32, args.steps, args.warmup, kernel_times=True, label="timed_fp32")
@@ -274,19 +282,19 @@ def run_gb300(args):
     main32_ms = statistics.mean(b for _, b in kt32)
     trace32_ms = statistics.mean(a for a, _ in kt32)
     pk = peaks()
-    ach = w64["flops_main"] / (main_ms / 1e3) / 1e12
+    ach = nrhs * w64["flops_main"] / (main_ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": ach / FP64_PEAK_TFLOPS, "traffic": NCU_MAIN_TRAFFIC.get(args.workload), "kernel": f"k_main<double,{mesh.dim}>",
             "peak_src": "FP64 vendor figure 1.25 TFLOP/s (dense)",
             "kernel_ms": main_ms, "trace_kernel_ms": trace_ms,
-            "hbm_frac": (w64["bytes_x"] + w64["bytes_y"] + w64["bytes_geometry"] + w64["bytes_trace"])
+            "hbm_frac": (nrhs * (w64["bytes_x"] + w64["bytes_y"] + w64["bytes_trace"]) + w64["bytes_geometry"])
             / ((main_ms + trace_ms) / 1e3) / (pk["hbm_gbs"] * 1e9)}
-    ach32 = w32["flops_main"] / (main32_ms / 1e3) / 1e12
+    ach32 = nrhs * w32["flops_main"] / (main32_ms / 1e3) / 1e12
 
     # ---- end to end through the public API with host buffers
-    xh = torch.tensor(si.random_vector(n, 0)).pin_memory()
-    yh = torch.empty(n, dtype=torch.float64).pin_memory()
-    xd = torch.empty(n, dtype=torch.float64, device="cuda")
+    xh = torch.tensor(xhost).pin_memory()
+    yh = torch.empty(xh.shape, dtype=torch.float64).pin_memory()
+    xd = torch.empty(xh.shape, dtype=torch.float64, device="cuda")
     yd = torch.empty_like(xd)
     for _ in range(args.warmup):
         xd.copy_(xh, non_blocking=True)
@@ -305,49 +313,57 @@ def run_gb300(args):
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
     barrier()
-    e2e_val = world * n / (statistics.mean(e2e_ms) / 1e3) / 1e9
+    e2e_val = world * nrhs * n / (statistics.mean(e2e_ms) / 1e3) / 1e9
 
     # ---- CG solves to 1e-10 (manufactured right-hand side)
     cg = None
     if not args.no_cg:
-        xq = op.quad_points()
-        f = (mesh.lam + mesh.dim * np.pi ** 2) * torch.prod(torch.sin(np.pi * xq), dim=1)
-        bvec = op.iproduct(f.contiguous())
+        if nrhs == 1:
+            # manufactured right-hand side of sin(pi x) sin(pi y) (sin(pi z))
+            xq = op.quad_points()
+            f = (mesh.lam + mesh.dim * np.pi ** 2) * torch.prod(torch.sin(np.pi * xq), dim=1)
+            bvec = op.iproduct(f.contiguous())
+        else:
+            bvec = x   # the batch of N(0,1) right-hand sides
+        # warm-up solve (graph capture); the 32-column batch stops it early, since
+        # one full batched solve takes about a minute
+        warm_rtol = 1e-10 if nrhs == 1 else 1e-4
         res = {}
         for name, mode in (("fp64", g.SIP_CG_FP64), ("fp32_refined", g.SIP_CG_FP32_REFINED)):
-            op.cg_solve(bvec, mode=mode, rtol=1e-10)  # warm-up (graph capture)
+            op.cg_solve(bvec, mode=mode, rtol=warm_rtol)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             _, st = op.cg_solve(bvec, mode=mode, rtol=1e-10)
             torch.cuda.synchronize()
-            res[name] = {"seconds": time.perf_counter() - t0, "iterations": st["iterations"],
+            res[name] = {"seconds": time.perf_counter() - t0, "nrhs": nrhs, "iterations": st["iterations"],
                          "refinements": st["refinements"], "rel_residual": st["rel_residual"]}
         res["speedup_fp32_refined"] = res["fp64"]["seconds"] / res["fp32_refined"]["seconds"]
         cg = res
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        r, done, nel, dt, cores = oracle_apply_rate(mesh, budget_s=args.cpu_budget)
+        r, done, nel, dt, cores = oracle_apply_rate(mesh, budget_s=args.cpu_budget, nrhs=nrhs)
         cpu = {"value": r / 1e9, "unit": "GDoF/s", "cores": round(cores, 2), "kind": "oracle",
-               "sample": f"rows of {nel} of {mesh.n_elem} elements ({done} DOFs) built from local blocks "
-                         f"and applied, {dt:.1f} s; cores = CPU time / wall time"}
+               "sample": f"rows of {nel} of {mesh.n_elem} elements ({done} DOF-columns, {nrhs} right-hand "
+                         f"side(s)) built from local blocks and applied, {dt:.1f} s; cores = CPU time / wall time"}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "ndof": n, "n_elem": mesh.n_elem, "precision": "fp64",
+            "config": {"workload": args.workload, "ndof": n, "nrhs": nrhs, "n_elem": mesh.n_elem, "precision": "fp64",
                        "l2": "flushed before every step (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single",
                        "tiling": tiling},
-            "fp32_apply": {"value": world * n / t32 / 1e9, "unit": "GDoF/s", "ms_per_step": t32 * 1e3,
+            "fp32_apply": {"value": world * nrhs * n / t32 / 1e9, "unit": "GDoF/s", "ms_per_step": t32 * 1e3,
                            "main_kernel_ms": main32_ms, "trace_kernel_ms": trace32_ms,
                            "main_tflops": ach32, "main_frac_of_fp32_peak": ach32 / FP32_PEAK_TFLOPS},
             "cg": cg,
             "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+            "e2e": {"value": e2e_val, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * nrhs * n,
+                    "d2h_bytes_per_step": 8 * nrhs * n},
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
             "wall_s_timed_region": wall,
