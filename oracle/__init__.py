@@ -20,6 +20,10 @@ Parity status of each part (what pins it is in ``tests/test_oracle_*.py``):
   penalty closed form for an element indicator, Galerkin consistency for
   polynomials vanishing on the boundary, constant null space of the
   pure-Neumann stiffness, manufactured-solution convergence order P+1);
+* point-to-point interpolation variant (Sec. 3.3, Table 2): pinned (equals
+  the shared-rule operator on conforming meshes and wherever the low-order
+  side's rule is exact; symmetric exactly under the paper's exactness
+  condition; the paper's three Table 2 cases classified as the paper does);
 * penalty length h_f on jittered (non-affine) faces: parity unpinned (the
   paper does not define h_f; the reading min(|K-|,|K+|)/|F| is checked only
   through the invariants above, which hold for any positive h_f);

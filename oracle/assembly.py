@@ -20,6 +20,18 @@ with {w} = (w- + w+)/2 and [[u]] = u- n- + u+ n+ (Sec. 2.2, average and jump).
   geometric map (the shared trace space of Sec. 3.3; evaluating each side's
   own polynomial at the shared points is the mortar-equivalent of Sec. 3.3,
   Eq. after "mortar project").
+* Point-to-point variant (``face_scheme="p2p"``, the comparison method of
+  Sec. 3.3, "Point-to-point interpolation", and Table 2): each side of an
+  interior face integrates on its OWN face rule (Q of that element), with the
+  other side's trace values Lagrange-interpolated from the other side's own
+  face points to its points; the rows of each element are then tested and
+  lifted on its own rule.  The transferred quantities are the two scalars of
+  the trace exchange (u and grad u . n, n the minus side's unit normal at the
+  source point; Sec. 5.1 exchanges two scalars per trace point), which equals
+  the paper's interpolated gradient wherever n is constant over the face.
+* ``rule="gll"`` swaps every Gauss rule (volume and face) for the
+  Gauss-Lobatto-Legendre rule with the same number of points (the set-up of
+  Table 2), and ``qorders`` sets Q per element.
 * Boundary faces: Nitsche weak Dirichlet with g = 0, i.e. [[u]] = u n and
   {grad u} = grad u on the boundary (reading of "u+ from boundary
   conditions", Sec. 2.2).
@@ -129,17 +141,28 @@ class SipOracle:
     mesh: object with dim, vert [nv, dim], elem_vert [E, 2^dim], orders [E].
     kappa: None (= 1) or a sequence of per-element arrays of Q_e^dim values.
     boundary: False drops boundary faces (pure-Neumann variant, for tests).
+    face_scheme: "shared" (one shared rule per face, Sec. 3.3) or "p2p"
+        (point-to-point interpolation between the two sides' own rules).
+    rule: "gauss" or "gll" quadrature points (volume and faces).
+    qorders: quadrature points per direction of each element (default P + qvol_extra).
     """
 
     def __init__(self, mesh, lam: float = 1.0, tau_scale: float = 2.0, qvol_extra: int = 2,
-                 kappa=None, boundary: bool = True):
+                 kappa=None, boundary: bool = True, face_scheme: str = "shared", rule: str = "gauss",
+                 qorders=None):
+        if face_scheme not in ("shared", "p2p"):
+            raise ValueError("face_scheme must be 'shared' or 'p2p'")
+        if rule not in ("gauss", "gll"):
+            raise ValueError("rule must be 'gauss' or 'gll'")
+        self.face_scheme = face_scheme
+        self.rule = rule
         self.dim = int(mesh.dim)
         self.vert = np.asarray(mesh.vert, dtype=np.float64)
         self.elem_vert = np.asarray(mesh.elem_vert, dtype=np.int64)
         self.P = np.asarray(mesh.orders, dtype=np.int64)
         self.E = self.elem_vert.shape[0]
         self.N = self.P + 1
-        self.Q = self.P + qvol_extra
+        self.Q = self.P + qvol_extra if qorders is None else np.asarray(qorders, dtype=np.int64)
         self.lam = float(lam)
         self.tau_scale = float(tau_scale)
         self.boundary = boundary
@@ -158,19 +181,22 @@ class SipOracle:
         return self._vol_cache[e]
 
     # ---- reference data per (N, Q)
-    def _ref_volume(self, n, q):
-        key = ("vol", n, q)
+    def _rule_1d(self, q, rule=None):
+        return (gauss_lobatto if (rule or self.rule) == "gll" else gauss_legendre)(q)
+
+    def _ref_volume(self, n, q, rule=None):
+        key = ("vol", n, q, rule or self.rule)
         if key not in self._ref:
-            x1, w1 = gauss_legendre(q)
+            x1, w1 = self._rule_1d(q, rule)
             pts, w = _tensor_points(x1, w1, self.dim)
             phi, dphi = basis_at(n, pts)
             self._ref[key] = (pts, w, phi, dphi)
         return self._ref[key]
 
-    def _element_geometry(self, e, q=None):
+    def _element_geometry(self, e, q=None, rule=None):
         n = int(self.N[e])
         q = int(self.Q[e]) if q is None else q
-        pts, w, phi, dphi = self._ref_volume(n, q)
+        pts, w, phi, dphi = self._ref_volume(n, q, rule)
         x, J = _map(self.vert[self.elem_vert[e]], pts)
         det = np.linalg.det(J)
         if np.any(det <= 0):
@@ -208,9 +234,9 @@ class SipOracle:
         self.bfaces.sort()
 
     def _face_rule(self, q):
-        key = ("face", q)
+        key = ("face", q, self.rule)
         if key not in self._ref:
-            x1, w1 = gauss_legendre(q)
+            x1, w1 = self._rule_1d(q)
             if self.dim == 2:
                 self._ref[key] = (x1[:, None], w1)
             else:
@@ -226,11 +252,15 @@ class SipOracle:
         gphys = np.einsum("pki,pkb->pib", Jinv, dphi)
         return phi, gphys, J, Jinv
 
-    def face_data(self, pair):
+    def face_data(self, pair, qf=None):
         """Quadrature data of one interior face: W [Z], n [Z, d], tau, and for each
-        side (phi, gphys·n) at the shared points."""
+        side (phi, gphys·n) at the points of the qf-point face rule (default: the
+        shared rule, qf = max(Q-, Q+)), placed in the minus side's face
+        parametrisation.  tau always comes from the shared rule's area."""
         (em, km), (ep, kp) = pair
-        qf = int(max(self.Q[em], self.Q[ep]))
+        qshared = int(max(self.Q[em], self.Q[ep]))
+        if qf is None:
+            qf = qshared
         zs, wz = self._face_rule(qf)
         am, sm = divmod(km, 2)
         xi_m = np.zeros((zs.shape[0], self.dim))
@@ -247,7 +277,7 @@ class SipOracle:
         nrm = np.linalg.norm(nraw, axis=1)
         nvec = nraw / nrm[:, None]
         W = wz * np.abs(np.linalg.det(Jm)) * nrm
-        area = W.sum()
+        area = W.sum() if qf == qshared else self.face_data(pair)[0].sum()
         h = min(self.volume(em), self.volume(ep)) / area
         tau = self.tau_scale * (max(self.P[em], self.P[ep]) + 1) ** 2 / h
         dnm = np.einsum("pib,pi->pb", gm, nvec)
@@ -282,21 +312,57 @@ class SipOracle:
         M = np.einsum("p,pb,pc->bc", wdet, phi, phi)
         return K + self.lam * M
 
+    def _face_interp(self, q_from, q_to):
+        """Lagrange interpolation on the face from the q_from-point rule to the
+        q_to-point rule: [q_to^(d-1), q_from^(d-1)], face points z0 + q z1."""
+        x_from, _ = self._rule_1d(q_from)
+        x_to, _ = self._rule_1d(q_to)
+        L = lagrange_matrix(x_from, x_to)
+        return L if self.dim == 2 else np.kron(L, L)
+
+    @staticmethod
+    def _sip_face_block(W, tau, pv, dv, sv, pw, dw, sw):
+        """sum_z W [ -1/2 s_w (dn_v)_i phi_w_j - 1/2 s_v phi_v_i (dn_w)_j + tau s_v s_w phi_v_i phi_w_j ]."""
+        return (-0.5 * sw * np.einsum("z,zi,zj->ij", W, dv, pw)
+                - 0.5 * sv * np.einsum("z,zi,zj->ij", W, pv, dw)
+                + tau * sv * sw * np.einsum("z,zi,zj->ij", W, pv, pw))
+
     def interior_face_blocks(self, pair):
         """Blocks {(v, w): A_vw} of one interior face, v, w in {0 (minus), 1 (plus)}:
         sum_z W [ -1/2 s_w (dn_v)_i phi_w_j - 1/2 s_v phi_v_i (dn_w)_j + tau s_v s_w phi_v_i phi_w_j ],
-        s_minus = +1, s_plus = -1, normal derivatives along the minus side's normal."""
-        W, _, tau, (phim, dnm), (phip, dnp) = self.face_data(pair)
-        sides = [(phim, dnm, 1.0), (phip, dnp, -1.0)]
+        s_minus = +1, s_plus = -1, normal derivatives along the minus side's normal.
+
+        Shared scheme: one rule for all four blocks.  Point-to-point scheme: the
+        rows of side v use side v's own rule, with side w's values (phi_w,
+        dn_w) taken at side w's own points and interpolated to side v's."""
+        if self.face_scheme == "shared":
+            W, _, tau, (phim, dnm), (phip, dnp) = self.face_data(pair)
+            sides = [(phim, dnm, 1.0), (phip, dnp, -1.0)]
+            out = {}
+            for v in range(2):
+                for w in range(2):
+                    pv, dv, sv = sides[v]
+                    pw, dw, sw = sides[w]
+                    out[(v, w)] = self._sip_face_block(W, tau, pv, dv, sv, pw, dw, sw)
+            return out
+        (em, _), (ep, _) = pair
+        q = (int(self.Q[em]), int(self.Q[ep]))
+        # each side's data at its own rule: W, and (phi, dn) of that side
+        own = []
+        for v in range(2):
+            W, _, tau, side_m, side_p = self.face_data(pair, qf=q[v])
+            own.append((W, side_m if v == 0 else side_p))
+        sgn = (1.0, -1.0)
         out = {}
         for v in range(2):
+            Wv, (pv, dv) = own[v]
             for w in range(2):
-                pv, dv, sv = sides[v]
-                pw, dw, sw = sides[w]
-                blk = (-0.5 * sw * np.einsum("z,zi,zj->ij", W, dv, pw)
-                       - 0.5 * sv * np.einsum("z,zi,zj->ij", W, pv, dw)
-                       + tau * sv * sw * np.einsum("z,zi,zj->ij", W, pv, pw))
-                out[(v, w)] = blk
+                if w == v:
+                    pw, dw = pv, dv
+                else:
+                    L = self._face_interp(q[w], q[v])
+                    pw, dw = L @ own[w][1][0], L @ own[w][1][1]
+                out[(v, w)] = self._sip_face_block(Wv, tau, pv, dv, sgn[v], pw, dw, sgn[w])
         return out
 
     def boundary_face_block(self, e, k):
@@ -390,7 +456,7 @@ class SipOracle:
         """sqrt( sum_K int_K (u_h - u)^2 ) with a (P + extra)-point Gauss rule."""
         err = 0.0
         for e in range(self.E):
-            x, phi, _, _, wdet = self._element_geometry(e, q=int(self.P[e]) + extra)
+            x, phi, _, _, wdet = self._element_geometry(e, q=int(self.P[e]) + extra, rule="gauss")
             diff = phi @ uh[self.off[e]:self.off[e + 1]] - u_exact(x)
             err += np.sum(wdet * diff * diff)
         return np.sqrt(err)

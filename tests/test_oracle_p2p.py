@@ -1,0 +1,95 @@
+"""Pins of the oracle's point-to-point interpolation variant (Sec. 3.3,
+"Point-to-point interpolation"; Sec. 4.1, Table 2) against what the paper and
+the mathematics fix:
+
+* on a conforming mesh both sides' own rules coincide, the interpolation is the
+  identity, and the variant equals the shared-rule operator;
+* the variant is symmetric exactly when the low-order side's own rule
+  integrates the face integrand exactly (the paper's condition, Sec. 3.3); it
+  then equals the shared-rule operator, which is exact as well;
+* the paper's three Table 2 cases on 2^3 hexahedra with GLL rules: P3Q4-P5Q6
+  non-symmetric, P3Q5-P5Q6 symmetric to round-off, P4Q5-P5Q6 symmetric on
+  affine geometry (p_geom = 0) and non-symmetric on trilinear geometry
+  (p_geom = 1), while the shared-rule operator (the paper's method) is
+  symmetric in every case.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import sip_inputs as si
+from oracle import SipOracle
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table2_p2p.json")))
+
+
+def _asym(A):
+    """||A - A^T||_1 / ||A||_1 (induced 1-norm)."""
+    return np.linalg.norm(A - A.T, 1) / np.linalg.norm(A, 1)
+
+
+def _half_mesh(dim, n, p_low, p_high, jitter=0.0, seed=1):
+    m = si.structured_mesh(dim, n, jitter=jitter, seed=seed, order=1)
+    left = m.vert[m.elem_vert].mean(axis=1)[:, 0] < 0.5
+    m.orders = np.where(left, p_low, p_high).astype(np.int32)
+    return m, left
+
+
+def _dense(m, **kw):
+    return SipOracle(m, lam=1.0, **kw).assemble().toarray()
+
+
+@pytest.mark.parametrize("dim,rule", [(2, "gauss"), (3, "gauss"), (2, "gll")])
+def test_conforming_mesh_equals_shared(dim, rule):
+    m = si.rotate_elements(si.structured_mesh(dim, 3, jitter=0.2, seed=2, order=3), seed=5)
+    A = _dense(m, face_scheme="p2p", rule=rule)
+    B = _dense(m, face_scheme="shared", rule=rule)
+    assert np.abs(A - B).max() <= 1e-14 * np.abs(B).max()
+
+
+@pytest.mark.parametrize("name", list(GOLD["cases"]))
+def test_table2_cases_affine(name):
+    c = GOLD["cases"][name]
+    m, left = _half_mesh(3, 2, c["deg_low"], c["deg_high"])
+    qo = np.where(left, c["q_low"], c["q_high"])
+    A = _dense(m, face_scheme="p2p", rule="gll", qorders=qo)
+    S = _dense(m, face_scheme="shared", rule="gll", qorders=qo)
+    assert _asym(S) <= 1e-14
+    # affine faces: integrand degree (deg_low + deg_high); GLL with q points is exact to 2q - 3
+    exact = c["deg_low"] + c["deg_high"] <= 2 * c["q_low"] - 3
+    if exact:
+        assert _asym(A) <= 1e-13
+        assert np.abs(A - S).max() <= 1e-13 * np.abs(S).max()
+    else:
+        assert _asym(A) >= 1e-3
+    if name != "P4Q5-P5Q6":   # that case needs p_geom = 1 (next test)
+        assert exact == GOLD["cases"][name]["paper_symmetric"]
+
+
+def test_table2_p4q5_needs_nonaffine_geometry():
+    """P4Q5-P5Q6: required degree 3 + 4 + p_geom exceeds 2*5 - 3 = 7 only with
+    p_geom >= 1; moving the one interior vertex makes the hexahedra trilinear."""
+    c = GOLD["cases"]["P4Q5-P5Q6"]
+    m, left = _half_mesh(3, 2, c["deg_low"], c["deg_high"], jitter=0.2, seed=1)
+    qo = np.where(left, c["q_low"], c["q_high"])
+    A = _dense(m, face_scheme="p2p", rule="gll", qorders=qo)
+    S = _dense(m, face_scheme="shared", rule="gll", qorders=qo)
+    assert _asym(A) >= 1e-3
+    assert _asym(S) <= 1e-14
+
+
+@pytest.mark.parametrize("p_low,p_high,symmetric", [(2, 5, True), (2, 6, False), (3, 6, True), (3, 7, False)])
+def test_gauss_rule_condition(p_low, p_high, symmetric):
+    """Gauss rules with Q = P + 2: the low side's Q-point rule is exact to degree
+    2Q - 1 = 2 p_low + 3, the affine face integrand has degree p_low + p_high."""
+    m, _ = _half_mesh(2, 4, p_low, p_high)
+    A = _dense(m, face_scheme="p2p")
+    S = _dense(m, face_scheme="shared")
+    assert symmetric == (p_low + p_high <= 2 * p_low + 3)
+    if symmetric:
+        assert _asym(A) <= 1e-13
+        assert np.abs(A - S).max() <= 1e-13 * np.abs(S).max()
+    else:
+        assert _asym(A) >= 1e-4
