@@ -209,9 +209,12 @@ def run_gb300(args):
     import paper_2504_03573_gb300 as g
 
     mesh = si.workload(args.workload)
-    op = g.SipOperator.from_mesh(mesh)
+    p2p = args.faces == "p2p"
+    op = g.SipOperator.from_mesh(mesh, opts=g.options(face_scheme=g.SIP_FACES_P2P) if p2p else None)
     n = op.ndof
     nrhs = NRHS.get(args.workload, 1)
+    if p2p:
+        args.no_cg = True   # CG needs the symmetric shared-rule operator
     # tile shapes chosen by the library's autotuner (set-up, outside the timed region)
     precs = {"fp64": g.SIP_FP64, "fp32": g.SIP_FP32}
     if args.tiling:
@@ -284,7 +287,8 @@ def run_gb300(args):
     pk = peaks()
     ach = nrhs * w64["flops_main"] / (main_ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_TFLOPS, "traffic": NCU_MAIN_TRAFFIC.get(args.workload), "kernel": f"k_main<double,{mesh.dim}>",
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None if p2p else NCU_MAIN_TRAFFIC.get(args.workload),
+            "kernel": f"k_main<double,{mesh.dim},{'true' if p2p else 'false'}>",
             "peak_src": "FP64 vendor figure 1.25 TFLOP/s (dense)",
             "kernel_ms": main_ms, "trace_kernel_ms": trace_ms,
             "hbm_frac": (nrhs * (w64["bytes_x"] + w64["bytes_y"] + w64["bytes_trace"]) + w64["bytes_geometry"])
@@ -353,6 +357,7 @@ def run_gb300(args):
             "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "ndof": n, "nrhs": nrhs, "n_elem": mesh.n_elem, "precision": "fp64",
+                       "faces": args.faces,
                        "l2": "flushed before every step (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single",
                        "tiling": tiling},
@@ -375,6 +380,61 @@ def run_gb300(args):
     return 0
 
 
+def run_sweep(args):
+    """Throughput sweeps shaped like the paper's CPU measurements (Sec. 5.2):
+    uniform hex meshes of [0,1]^3 (affine elements, one order each), FP64 and
+    FP32 applies, one JSON line per mesh.
+
+    orders: P = 1..8 at about 1.1e7 DOFs each (the paper's sub-operator study
+            uses 1.1e7 DOFs per order);
+    dofs:   P = 4 from about 1e4 to 1e8 DOFs (the paper's size sweep)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2504_03573_gb300 as g
+    if args.sweep == "orders":
+        cases = [(p, max(2, round(1.1e7 ** (1 / 3) / (p + 1)))) for p in range(1, 9)]
+    else:
+        cases = [(4, n) for n in (4, 8, 16, 24, 32, 48, 64, 90)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for p, n in cases:
+        mesh = si.structured_mesh(3, n, order=p)
+        op = g.SipOperator.from_mesh(mesh)
+        line = {"sweep": args.sweep, "order": p, "n": n, "n_elem": mesh.n_elem, "ndof": op.ndof,
+                "unit": "GDoF/s", "l2": "flushed before every step (256 MiB write)"}
+        for name, prec, dt in (("fp64", g.SIP_FP64, torch.float64), ("fp32", g.SIP_FP32, torch.float32)):
+            op.autotune(prec, reps=3)
+            x = torch.tensor(si.random_vector(op.ndof, 0), device="cuda", dtype=dt)
+            y = torch.empty_like(x)
+            for _ in range(args.warmup):
+                op.apply(x, out=y)
+            op.set_timing(True)
+            ms, kt = [], []
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                op.apply(x, out=y)
+                b.record(stream)
+                kt.append(op.last_kernel_ms())
+                ms.append((a, b))
+            torch.cuda.synchronize()
+            op.set_timing(False)
+            t = statistics.median(a.elapsed_time(b) for a, b in ms) / 1e3
+            main_ms = statistics.median(m for _, m in kt)
+            w = op.work_model(prec)
+            line[name] = {"value": op.ndof / t / 1e9, "ms_per_apply": t * 1e3, "main_kernel_ms": main_ms,
+                          "trace_kernel_ms": statistics.median(tr for tr, _ in kt),
+                          "main_tflops": w["flops_main"] / (main_ms / 1e3) / 1e12}
+        line["fp64"]["main_frac_of_fp64_peak"] = line["fp64"]["main_tflops"] / FP64_PEAK_TFLOPS
+        line["fp32"]["main_frac_of_fp32_peak"] = line["fp32"]["main_tflops"] / FP32_PEAK_TFLOPS
+        print(json.dumps(line), flush=True)
+        del op
+        torch.cuda.empty_cache()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -388,9 +448,16 @@ def main():
     ap.add_argument("--tiling", default=None, help="install the schedule saved by --save-tiling instead of tuning")
     ap.add_argument("--save-tiling", default=None, help="write the schedule in use to this JSON file")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--faces", default="shared", choices=["shared", "p2p"],
+                    help="interior-face flux: one shared rule per face (the method) or point-to-point "
+                         "interpolation between the two sides' own rules (the comparison variant)")
+    ap.add_argument("--sweep", default=None, choices=["orders", "dofs"],
+                    help="throughput sweep on uniform hex meshes instead of the benchmark line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.sweep:
+        return run_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gb300(args)

@@ -57,6 +57,11 @@ extern "C" {
 #define SIP_FP64 0              /* apply in double precision */
 #define SIP_FP32 1              /* apply in single precision with single accumulation */
 
+/* Interior-face flux evaluation (sip_options.face_scheme) */
+#define SIP_FACES_SHARED    0   /* one Gauss rule per face shared by both sides (Sec. 3.3) */
+#define SIP_FACES_P2P       1   /* point-to-point interpolation between the sides' own rules
+                                   (Sec. 3.3 "Point-to-point interpolation", Table 2) */
+
 #define SIP_CG_FP64         0   /* plain CG, FP64 apply */
 #define SIP_CG_FP32_REFINED 1   /* FP64 iterative refinement around an FP32-apply CG */
 
@@ -83,6 +88,15 @@ typedef struct sip_options {
     int32_t max_refine;       /* outer refinement steps cap, default 30 */
     int32_t checkpoint_every; /* save (x, r, p, r.r, k) every k CG iterations; 0 = off */
     int32_t checkpoint_slots; /* ring size for checkpoints, default 8 */
+    int32_t face_scheme;      /* SIP_FACES_SHARED (default) or SIP_FACES_P2P.  P2P: each side of
+                                 an interior face evaluates the flux on its OWN (P+2)-point Gauss
+                                 face rule, with the other side's two trace scalars (u and
+                                 grad u . n) Lagrange-interpolated from that side's own points,
+                                 and lifts it on its own rule.  The operator is then symmetric
+                                 only where the lower-order side's rule integrates the face
+                                 integrand exactly (Sec. 3.3), so P2P handles support sip_apply
+                                 (and sip_apply_static_scratch) only: transpose applies, CG
+                                 solves and gradients return SIP_ERR_ARG. */
 } sip_options;
 
 typedef struct sip_stats {
@@ -104,7 +118,9 @@ typedef struct sip_plan_info {
     int64_t n_elem_affine;            /* elements whose map is affine (constant Jacobian) */
     int64_t orient_hist[8];           /* interior faces per orientation code of the plus side */
     int64_t order_hist[SIP_MAX_ORDER + 1];
-    int64_t trace_points;             /* sum over faces of the shared face points */
+    int64_t trace_points;             /* trace buffer size per right-hand side / 4 values:
+                                         sum over faces of the shared face points (P2P: of
+                                         the two sides' own points) */
     double  min_h_face, max_tau;
 } sip_plan_info;
 

@@ -22,6 +22,8 @@ SIP_FP64 = 0
 SIP_FP32 = 1
 SIP_CG_FP64 = 0
 SIP_CG_FP32_REFINED = 1
+SIP_FACES_SHARED = 0
+SIP_FACES_P2P = 1
 SIP_MAX_ORDER = 8
 SIP_STATIC_TRACE_BYTES = 16 << 20
 
@@ -45,7 +47,7 @@ class sip_options(C.Structure):
     _fields_ = [("tau_scale", C.c_double), ("qvol_extra", C.c_int32), ("boundary", C.c_int32),
                 ("inner_rtol", C.c_double), ("max_iter", C.c_int32), ("check_every", C.c_int32),
                 ("max_refine", C.c_int32), ("checkpoint_every", C.c_int32),
-                ("checkpoint_slots", C.c_int32)]
+                ("checkpoint_slots", C.c_int32), ("face_scheme", C.c_int32)]
 
 
 class sip_stats(C.Structure):

@@ -242,11 +242,45 @@ struct FaceGeo {
   }
 };
 
+// points of one face at a q-point rule per direction
+template <int DIM>
+__device__ __forceinline__ int face_npts(int q) { return DIM == 2 ? q : q * q; }
+
+// Point-to-point interpolation variant (SIP_FACES_P2P).  Face geometry of an
+// interior face: [W-, c-] at the minus side's own points, then [W+, c+] at the
+// plus side's (boundary and affine faces as with a shared rule).  Trace slot:
+// one block per side, [u, g, u~, g~] at that side's own points, u~ and g~ being
+// the other side's values interpolated to them by the other side's trace kernel
+// (read from the other side's own block instead where both rules are equal).
+template <typename T>
+struct FaceGeoP2P {
+  const T* g;   // this side's W values (affine: the face's constants)
+  const T* gc;  // this side's c values [dim][npts]
+  int npts, zc, side, dim;
+  bool aff;
+  T w;
+  __device__ __forceinline__ T W() const { return aff ? g[0] * w : g[zc]; }
+  __device__ __forceinline__ T c(int m) const { return aff ? g[1 + side * dim + m] : gc[(int64_t)m * npts + zc]; }
+};
+// npm: points of the minus side's own rule
+template <typename T, int DIM>
+__device__ __forceinline__ FaceGeoP2P<T> face_geo_p2p(const ApplyArgs<T>& a, const FaceSlot& sl, int npts, int npm,
+                                                      int zc, T w) {
+  const T* g = a.fgeo + a.f_goff[sl.face];
+  const bool aff = (sl.flags & kFaceAffine) != 0;
+  if (aff) return FaceGeoP2P<T>{g, g, npts, zc, sl.side, DIM, true, w};
+  if (sl.flags & kFaceBnd) return FaceGeoP2P<T>{g, g + npts, npts, zc, 0, DIM, false, w};
+  const T* gw = g + (int64_t)sl.side * (1 + DIM) * npm;
+  return FaceGeoP2P<T>{gw, gw + npts, npts, zc, sl.side, DIM, false, w};
+}
+// offset of this side's block in the face's trace slot
+__device__ __forceinline__ int64_t p2p_own_block(int side, int npm) { return (int64_t)side * 4 * npm; }
+
 // Trace values of all 2 DIM faces of every element of the tile.  Conforming
 // faces (shared rule = own Q points) go straight from the per-face buffer to the
 // trace; faces with a finer shared rule are interpolated one face at a time in
 // the element's scratch.
-template <typename T, int DIM, int N>
+template <typename T, int DIM, int N, bool P2P>
 __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Tile& t, const TileMeta<DIM>* mt, int rhs,
                                                 const T* tb, T* sm, const T* U) {
   using S = Shape<DIM, N>;
@@ -266,17 +300,32 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
     const int qf = sl.qf, ax = k >> 1;
     const int npts = DIM == 2 ? qf : qf * qf;
     const int zc = canon(DIM, sl.side, sl.orient, qf, z0, z1);
-    FaceGeo<T> fg{a.fgeo + a.f_goff[sl.face], npts, zc, sl.side, DIM, (sl.flags & kFaceAffine) != 0, T(0)};
-    T g = fg.c(ax) * dn;
-    if (!orth) {
-      int t0, t1;
-      tang_axes<DIM>(ax, t0, t1);
-      g += fg.c(t0) * d0;
-      if constexpr (DIM == 3) g += fg.c(t1) * d1;
+    if constexpr (P2P) {
+      const int npm = face_npts<DIM>(sl.side ? face_oq(sl.flags) : qf);
+      const FaceGeoP2P<T> fg = face_geo_p2p<T, DIM>(a, sl, npts, npm, zc, T(0));
+      T g = fg.c(ax) * dn;
+      if (!orth) {
+        int t0, t1;
+        tang_axes<DIM>(ax, t0, t1);
+        g += fg.c(t0) * d0;
+        if constexpr (DIM == 3) g += fg.c(t1) * d1;
+      }
+      T* tr = a.trace + rhs * a.trace_stride + 4 * a.f_troff[sl.face] + p2p_own_block(sl.side, npm) + zc;
+      tr[0] = uv;
+      tr[npts] = g;
+    } else {
+      FaceGeo<T> fg{a.fgeo + a.f_goff[sl.face], npts, zc, sl.side, DIM, (sl.flags & kFaceAffine) != 0, T(0)};
+      T g = fg.c(ax) * dn;
+      if (!orth) {
+        int t0, t1;
+        tang_axes<DIM>(ax, t0, t1);
+        g += fg.c(t0) * d0;
+        if constexpr (DIM == 3) g += fg.c(t1) * d1;
+      }
+      T* tr = a.trace + rhs * a.trace_stride + 4 * a.f_troff[sl.face] + (int64_t)(2 * sl.side) * npts + zc;
+      tr[0] = uv;
+      tr[npts] = g;
     }
-    T* tr = a.trace + rhs * a.trace_stride + 4 * a.f_troff[sl.face] + (int64_t)(2 * sl.side) * npts + zc;
-    tr[0] = uv;
-    tr[npts] = g;
   };
   auto emit = [&](int el, int k, const T* src, int fs, int z0, int z1) {
     const int z = z0 + mt->slot(el * 2 * DIM + k).qf * z1;
@@ -419,7 +468,58 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
   __syncthreads();
 }
 
+// Point-to-point interpolation (Sec. 3.3): on every interior face whose other
+// side has another rule, this side's u and g, stored just before at its own Q
+// points (canonical order), are interpolated to the other side's own oq-point
+// rule and written into the other side's block, where its main kernel reads
+// them as the neighbour's trace.  The stored values are read back from global
+// memory, visible to the whole CTA after the barrier that ends the face stages.
 template <typename T, int DIM, int N>
+__device__ __forceinline__ void p2p_send(const ApplyArgs<T>& a, const Tile& t, const TileMeta<DIM>* mt, int rhs) {
+  constexpr int Q = N + 1, NFACE = 2 * DIM, FMAX = cpow(kQMax, DIM - 1), NP = cpow(Q, DIM - 1);
+  const int ne = t.count;
+  for (int w = threadIdx.x; w < ne * NFACE * FMAX; w += blockDim.x) {
+    const int el = w / (NFACE * FMAX), rem = w - el * NFACE * FMAX;
+    const int k = rem / FMAX, z = rem - k * FMAX;
+    const FaceSlot sl = mt->slot(el * 2 * DIM + k);
+    const int oq = face_oq(sl.flags);
+    const int npo = face_npts<DIM>(oq);
+    if ((sl.flags & kFaceBnd) || oq == Q || z >= npo) continue;
+    const int npm = sl.side ? npo : NP;
+    T* base = a.trace + rhs * a.trace_stride + 4 * a.f_troff[sl.face];
+    const T* src = base + (int64_t)sl.side * 4 * npm;                // own [u][g], Q points
+    T* dst = base + (sl.side ? 0 : (int64_t)4 * npm) + 2 * npo;      // the other side's [u~][g~]
+    const T* I = a.p2p_I + (Q * (kQMax + 1) + oq) * (kQMax * kQMax);  // Q-point rule -> oq-point rule
+    T u = 0, g = 0;
+    if constexpr (DIM == 2) {
+#pragma unroll 1
+      for (int r = 0; r < Q; ++r) {
+        const T wv = I[z * kQMax + r];
+        u = fma(wv, src[r], u);
+        g = fma(wv, src[NP + r], g);
+      }
+    } else {
+      const int z0 = z % oq, z1 = z / oq;
+#pragma unroll 1
+      for (int r1 = 0; r1 < Q; ++r1) {
+        T su = 0, sg = 0;
+#pragma unroll 1
+        for (int r0 = 0; r0 < Q; ++r0) {
+          const T wv = I[z0 * kQMax + r0];
+          su = fma(wv, src[r0 + Q * r1], su);
+          sg = fma(wv, src[NP + r0 + Q * r1], sg);
+        }
+        const T w1 = I[z1 * kQMax + r1];
+        u = fma(w1, su, u);
+        g = fma(w1, sg, g);
+      }
+    }
+    dst[z] = u;
+    dst[npo + z] = g;
+  }
+}
+
+template <typename T, int DIM, int N, bool P2P>
 __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, TileMeta<DIM>* mt, T* sm) {
   using S = Shape<DIM, N>;
   constexpr int PER = S::PER_TRACE;
@@ -466,7 +566,8 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
       a.ug[rhs * a.nquad + a.quad_off[mt->eid(el)] + q] = U[el * PER + q];
     }
   }
-  trace_all_faces<T, DIM, N>(a, t, mt, rhs, tb, sm, U);
+  trace_all_faces<T, DIM, N, P2P>(a, t, mt, rhs, tb, sm, U);
+  if constexpr (P2P) p2p_send<T, DIM, N>(a, t, mt, rhs);
 }
 
 // ============================================================ main kernel
@@ -474,8 +575,16 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
 // writes s and c_m t (m = 0..DIM-1; only c_a t where the tile is orthogonal) to
 // dst[f * fs + z0 + qf z1].
 template <typename T, int DIM, int N>
+__device__ __forceinline__ void face_flux_p2p(const ApplyArgs<T>& a, const TileMeta<DIM>* mt, int rhs, const T* tb,
+                                              bool orth, int el, int k, int z0, int z1, T* dst, int fs);
+
+template <typename T, int DIM, int N, bool P2P>
 __device__ __forceinline__ void face_flux(const ApplyArgs<T>& a, const TileMeta<DIM>* mt, int rhs, const T* tb,
                                           bool orth, int el, int k, int z0, int z1, T* dst, int fs) {
+  if constexpr (P2P) {
+    face_flux_p2p<T, DIM, N>(a, mt, rhs, tb, orth, el, k, z0, z1, dst, fs);
+    return;
+  }
   const FaceSlot sl = mt->slot(el * 2 * DIM + k);
   const int qf = sl.qf, ax = k >> 1;
   const int npts = DIM == 2 ? qf : qf * qf;
@@ -517,10 +626,52 @@ __device__ __forceinline__ void face_flux(const ApplyArgs<T>& a, const TileMeta<
     if (!orth || m == ax) dst[(1 + m) * fs + z] = fg.c(m) * tt;
 }
 
+// The same flux with point-to-point interpolation: this side's own rule, the
+// other side's values already interpolated to its points by the other side's
+// trace kernel (rows only; the transpose apply is not defined for this variant).
+template <typename T, int DIM, int N>
+__device__ __forceinline__ void face_flux_p2p(const ApplyArgs<T>& a, const TileMeta<DIM>* mt, int rhs, const T* tb,
+                                              bool orth, int el, int k, int z0, int z1, T* dst, int fs) {
+  const FaceSlot sl = mt->slot(el * 2 * DIM + k);
+  const int qf = sl.qf, ax = k >> 1;
+  const int npts = DIM == 2 ? qf : qf * qf;
+  const int z = z0 + qf * z1;
+  const int zc = canon(DIM, sl.side, sl.orient, qf, z0, z1);
+  const int oq = face_oq(sl.flags);
+  const int npm = face_npts<DIM>(sl.side ? oq : qf);
+  const bool faff = (sl.flags & kFaceAffine) != 0;
+  const T* GWf = tb + TabLayout::GW(N, qf);
+  const T wz = faff ? (DIM == 2 ? GWf[zc] : GWf[zc % qf] * GWf[zc / qf]) : T(0);
+  const FaceGeoP2P<T> fg = face_geo_p2p<T, DIM>(a, sl, npts, npm, zc, wz);
+  const T* trf = a.trace + rhs * a.trace_stride + 4 * a.f_troff[sl.face];
+  const T* tr = trf + p2p_own_block(sl.side, npm) + zc;
+  const T W = fg.W();
+  const T tau = a.f_tau[sl.face];
+  const T uo = tr[0];
+  const T go_ = tr[npts];
+  T s, tt;
+  if (sl.flags & kFaceBnd) {
+    s = W * (tau * uo - go_);
+    tt = -W * uo;
+  } else {
+    const T* trn = oq == qf ? trf + p2p_own_block(1 - sl.side, npm) + zc : tr + 2 * npts;
+    const T un = trn[0];
+    const T gn = trn[npts];
+    const T jmp = uo - un;
+    const T avg = T(0.5) * (go_ - gn);
+    s = W * (tau * jmp - avg);
+    tt = T(-0.5) * W * jmp;
+  }
+  dst[z] = s;
+#pragma unroll
+  for (int m = 0; m < DIM; ++m)
+    if (!orth || m == ax) dst[(1 + m) * fs + z] = fg.c(m) * tt;
+}
+
 // Flux of faces with a finer shared rule (p-non-conforming), SC slots per
 // round: flux at the shared points, then projection back to the element's own
 // face points (TraceIProduct) into the per-face buffers.
-template <typename T, int DIM, int N>
+template <typename T, int DIM, int N, bool P2P>
 __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Tile& t, const TileMeta<DIM>* mt,
                                                 const uint16_t* flist, int rhs,
                                                 const T* tb, T* F0, int per, bool orth) {
@@ -542,7 +693,7 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
       int j, z;
       fl.fine_at(per_f, w, j, z);
       const int e = fl.fine(j), el = fl_el(e), k = fl_k(e);
-      face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, z, 0, F0 + el * per + SC + k * SL + NF * FT, FMAX);
+      face_flux<T, DIM, N, P2P>(a, mt, rhs, tb, orth, el, k, z, 0, F0 + el * per + SC + k * SL + NF * FT, FMAX);
     }
     __syncthreads();
     // projection of the fields in use (s and c_a t where the tile is orthogonal)
@@ -568,7 +719,7 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
         const int k = k0 + kk;
         const int qf = mt->slot(el * 2 * DIM + k).qf;
         if (qf == Q || z0 >= qf || z1 >= qf) continue;
-        face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, z0, z1, F0 + el * per + SC + kk * SL + NF * FT, FMAX);
+        face_flux<T, DIM, N, P2P>(a, mt, rhs, tb, orth, el, k, z0, z1, F0 + el * per + SC + kk * SL + NF * FT, FMAX);
       }
       __syncthreads();
       if constexpr (DIM == 2) {
@@ -625,7 +776,7 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
   }
 }
 
-template <typename T, int DIM, int N>
+template <typename T, int DIM, int N, bool P2P>
 __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, TileMeta<DIM>* mt, T* sm) {
   using S = Shape<DIM, N>;
   constexpr int Q = S::Q, QV = S::QV, NV = S::NV, QF1 = S::QF1, NFACE = S::NFACE, PER = S::PER_MAIN;
@@ -702,7 +853,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
           const int rem = v - el * NFACE * QF1;
           const int k = rem / QF1, j = rem - k * QF1;
           if (mt->slot(el * 2 * DIM + k).qf != Q) continue;
-          face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
+          face_flux<T, DIM, N, P2P>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
           continue;
         }
         const int el = w / QV, q = w - el * QV;
@@ -778,7 +929,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
             j = rem - k * QF1;
             if (fine && mt->slot(el * 2 * DIM + k).qf != Q) continue;
           }
-          face_flux<T, DIM, N>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
+          face_flux<T, DIM, N, P2P>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
           continue;
         }
         const int el = w / QV, q = w - el * QV;
@@ -835,7 +986,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
     }
   }
   __syncthreads();
-  if (fine) lift_fine_faces<T, DIM, N>(a, t, mt, flist, rhs, tb, F0, PER, orth);
+  if (fine) lift_fine_faces<T, DIM, N, P2P>(a, t, mt, flist, rhs, tb, F0, PER, orth);
   // face field P = s + sum_{tangential m} D_m^T (c_m t) on the face (the
   // tangential part of the lift after the transposed gradient); c_a t stays as
   // is and is lifted with l'(+-1)
@@ -955,7 +1106,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
     default: break;          \
   }
 
-template <typename T, int DIM, int N, bool MAIN>
+template <typename T, int DIM, int N, bool MAIN, bool P2P>
 __device__ __forceinline__ void run_tiles(const ApplyArgs<T>& a, int ti0, int ti1, int rhs, unsigned char* smem_raw) {
   T* tb = reinterpret_cast<T*>(smem_raw);
   TileMeta<DIM>* mt = reinterpret_cast<TileMeta<DIM>*>(smem_raw + table_block_bytes(sizeof(T), N));
@@ -964,18 +1115,20 @@ __device__ __forceinline__ void run_tiles(const ApplyArgs<T>& a, int ti0, int ti
   for (int ti = ti0; ti < ti1; ++ti) {
     if (ti > ti0) __syncthreads();  // the previous tile's last stage still reads shared memory
     const Tile t = a.tiles[ti];
-    if constexpr (MAIN) main_tile<T, DIM, N>(a, t, rhs, tb, mt, sm);
-    else trace_tile<T, DIM, N>(a, t, rhs, tb, mt, sm);
+    if constexpr (MAIN) main_tile<T, DIM, N, P2P>(a, t, rhs, tb, mt, sm);
+    else trace_tile<T, DIM, N, P2P>(a, t, rhs, tb, mt, sm);
   }
 }
 
-template <typename T, int DIM>
+// P2P: the point-to-point interpolation variant (SIP_FACES_P2P); the shared-rule
+// kernels are compiled without any of its code.
+template <typename T, int DIM, bool P2P>
 __global__ void __launch_bounds__(256) k_trace(ApplyArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ti0 = a.cta_off[blockIdx.x], ti1 = a.cta_off[blockIdx.x + 1];
   if (ti0 >= ti1) return;
   const Tile t = a.tiles[ti0];  // every tile of the CTA has this order
-#define SIP_TRACE_CASE(NN) run_tiles<T, DIM, NN, false>(a, ti0, ti1, blockIdx.y, smem_raw)
+#define SIP_TRACE_CASE(NN) run_tiles<T, DIM, NN, false, P2P>(a, ti0, ti1, blockIdx.y, smem_raw)
   SIP_ORDER_SWITCH(SIP_TRACE_CASE)
 #undef SIP_TRACE_CASE
 }
@@ -988,13 +1141,13 @@ __global__ void __launch_bounds__(256) k_trace(ApplyArgs<T> a) {
 #define SIP_MAIN_LAUNCH_BOUNDS 256
 #endif
 
-template <typename T, int DIM>
+template <typename T, int DIM, bool P2P>
 __global__ void __launch_bounds__(SIP_MAIN_LAUNCH_BOUNDS) k_main(ApplyArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ti0 = a.cta_off[blockIdx.x], ti1 = a.cta_off[blockIdx.x + 1];
   if (ti0 >= ti1) return;
   const Tile t = a.tiles[ti0];
-#define SIP_MAIN_CASE(NN) run_tiles<T, DIM, NN, true>(a, ti0, ti1, blockIdx.y, smem_raw)
+#define SIP_MAIN_CASE(NN) run_tiles<T, DIM, NN, true, P2P>(a, ti0, ti1, blockIdx.y, smem_raw)
   SIP_ORDER_SWITCH(SIP_MAIN_CASE)
 #undef SIP_MAIN_CASE
 }

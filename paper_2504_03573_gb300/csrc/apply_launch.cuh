@@ -20,18 +20,20 @@
     return cudaMemcpyToSymbol(c_ioff, ioff, sizeof(int) * (kQMax + 1) * (kQMax + 1));             \
   }                                                                                               \
   cudaError_t prepare_##SUFFIX() {                                                                 \
-    cudaError_t e = cudaFuncSetAttribute(k_trace<TYPE, DIM>,                                      \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
-    if (e != cudaSuccess) return e;                                                               \
-    return cudaFuncSetAttribute(k_main<TYPE, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                200 * 1024);                                                      \
+    cudaError_t e = cudaSuccess;                                                                  \
+    for (auto fn : {k_trace<TYPE, DIM, false>, k_trace<TYPE, DIM, true>, k_main<TYPE, DIM, false>,  \
+                    k_main<TYPE, DIM, true>})                                                     \
+      if (e == cudaSuccess)                                                                       \
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);    \
+    return e;                                                                                     \
   }                                                                                               \
   cudaError_t occupancy_##SUFFIX(int threads, size_t smem_trace, size_t smem_main, int* blocks) { \
     int bt = 0, bm = 0;                                                                           \
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bt, k_trace<TYPE, DIM>, threads, \
-                                                                  smem_trace);                    \
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bt, k_trace<TYPE, DIM, false>,   \
+                                                                  threads, smem_trace);           \
     if (e != cudaSuccess) return e;                                                               \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, k_main<TYPE, DIM>, threads, smem_main); \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, k_main<TYPE, DIM, false>, threads,      \
+                                                      smem_main);                                 \
     *blocks = bt < bm ? bt : bm;                                                                  \
     return e;                                                                                     \
   }                                                                                               \
@@ -41,9 +43,11 @@
     if (nctas == 0) return cudaSuccess;                                                           \
     dim3 grid(nctas, nrhs);                                                                       \
     if (ev0) cudaEventRecord(ev0, s);                                                             \
-    k_trace<TYPE, DIM><<<grid, threads, smem_trace, s>>>(a);                                      \
+    if (a.p2p_I) k_trace<TYPE, DIM, true><<<grid, threads, smem_trace, s>>>(a);                     \
+    else k_trace<TYPE, DIM, false><<<grid, threads, smem_trace, s>>>(a);                           \
     if (ev1) cudaEventRecord(ev1, s);                                                             \
-    k_main<TYPE, DIM><<<grid, threads, smem_main, s>>>(a);                                        \
+    if (a.p2p_I) k_main<TYPE, DIM, true><<<grid, threads, smem_main, s>>>(a);                       \
+    else k_main<TYPE, DIM, false><<<grid, threads, smem_main, s>>>(a);                             \
     if (ev2) cudaEventRecord(ev2, s);                                                             \
     return cudaGetLastError();                                                                    \
   }                                                                                               \

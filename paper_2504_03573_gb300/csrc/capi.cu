@@ -270,6 +270,7 @@ ApplyArgs<T> make_args(sip_handle* h, const T* x, T* y, T* trace, T* ug, int tra
   a.trace_stride = 4 * h->plan.trace_points;
   a.lambda = (T)h->lambda;
   a.transpose = transpose;
+  a.p2p_I = h->p2p_interp<T>();
   return a;
 }
 
@@ -309,6 +310,8 @@ int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cu
   if (!h || !x || !y) return fail(SIP_ERR_ARG, "null handle or vector");
   if (nrhs < 1) return fail(SIP_ERR_ARG, "nrhs must be >= 1");
   if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
+  if (transpose && h->p2p())
+    return fail(SIP_ERR_ARG, "the transpose apply needs the shared-rule operator (face_scheme SIP_FACES_SHARED)");
   if (!scratch_override) {
     int rc = handle_grow_trace(h, nrhs);
     if (rc) return rc;
@@ -337,6 +340,7 @@ void sip_options_default(sip_options* o) {
   o->max_refine = 30;
   o->checkpoint_every = 0;
   o->checkpoint_slots = 8;
+  o->face_scheme = SIP_FACES_SHARED;
 }
 
 struct sip_plan {
@@ -437,6 +441,25 @@ int sip_create(const sip_mesh* mesh, const int32_t* orders, double lambda, const
   UP(h->gf.fgeo, ff);
   UP(h->gf.tau, tf);
   UP(h->xq, p.xq);
+  if (h->p2p()) {
+    // Lagrange interpolation from every f-point Gauss rule to every t-point one:
+    // block (f, t) at (f (kQMax+1) + t) kQMax^2, entry [z][r] = l_{f,r}(xi_{t,z})
+    const size_t blk = (size_t)kQMax * kQMax;
+    std::vector<double> I((size_t)(kQMax + 1) * (kQMax + 1) * blk, 0.0);
+    std::vector<double> xf, wf, xt, wt;
+    for (int f = kQMin; f <= kQMax; ++f) {
+      gauss_legendre(f, xf, wf);
+      for (int t = kQMin; t <= kQMax; ++t) {
+        gauss_legendre(t, xt, wt);
+        double* B = &I[((size_t)f * (kQMax + 1) + t) * blk];
+        for (int z = 0; z < t; ++z)
+          for (int r = 0; r < f; ++r) B[z * kQMax + r] = lagrange(xf, r, xt[z]);
+      }
+    }
+    std::vector<float> If = to_float(I);
+    UP(h->p2p_I_d, I);
+    UP(h->p2p_I_f, If);
+  }
 #undef UP
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->gd.kappa, std::max<size_t>(16, p.nquad * sizeof(double)));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->gf.kappa, std::max<size_t>(16, p.nquad * sizeof(float)));

@@ -36,6 +36,10 @@ struct ApplyArgs {
   int64_t trace_stride;    // per-RHS stride of the trace buffer
   T lambda;
   int transpose;
+  // SIP_FACES_P2P: Lagrange interpolation between Gauss rules, the matrix from the
+  // f-point to the t-point rule at p2p_I + (f (kQMax+1) + t) kQMax^2, entry
+  // [z][r] = l^G_{f,r}(xi^G_{t,z}) at z kQMax + r; nullptr with a shared rule
+  const T* p2p_I;
 };
 
 constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }

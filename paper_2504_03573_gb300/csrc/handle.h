@@ -65,10 +65,16 @@ struct sip_handle {
   int persistent[2] = {0, 0};                     // CTAs run several tiles each
   int threads[2] = {256, 256};                    // threads per CTA
   double* xq = nullptr;
+  // point-to-point interpolation matrices between Gauss rules (SIP_FACES_P2P only)
+  double* p2p_I_d = nullptr;
+  float* p2p_I_f = nullptr;
   sip::DevGeom<double> gd;
   sip::DevGeom<float> gf;
   template <typename T>
   const sip::DevGeom<T>& geom() const;
+  template <typename T>
+  const T* p2p_interp() const;
+  bool p2p() const { return plan.opt.face_scheme == SIP_FACES_P2P; }
   // scratch (sized for the largest nrhs seen, in doubles): trace buffer and, for
   // FP64 applies, the Gauss-point values handed from the trace to the main kernel
   double* trace_d = nullptr;
@@ -102,6 +108,10 @@ template <>
 inline const sip::DevGeom<double>& sip_handle::geom<double>() const { return gd; }
 template <>
 inline const sip::DevGeom<float>& sip_handle::geom<float>() const { return gf; }
+template <>
+inline const double* sip_handle::p2p_interp<double>() const { return p2p_I_d; }
+template <>
+inline const float* sip_handle::p2p_interp<float>() const { return p2p_I_f; }
 
 namespace sip {
 // Tiles of one precision and the CTA that runs each, with the shared memory of

@@ -122,6 +122,11 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
   if (opt_in) opt = *opt_in; else sip_options_default(&opt);
   if (opt.qvol_extra != 2) { err = "only qvol_extra = 2 (Q = P + 2) is supported"; return SIP_ERR_ARG; }
   if (!(opt.tau_scale > 0.0)) { err = "tau_scale must be > 0"; return SIP_ERR_ARG; }
+  if (opt.face_scheme != SIP_FACES_SHARED && opt.face_scheme != SIP_FACES_P2P) {
+    err = "face_scheme must be SIP_FACES_SHARED or SIP_FACES_P2P";
+    return SIP_ERR_ARG;
+  }
+  const bool p2p = opt.face_scheme == SIP_FACES_P2P;
   p.opt = opt;
   p.dim = dim;
   const int64_t E = mesh->n_elem;
@@ -275,12 +280,25 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
     const Pair& pr = f < p.n_int ? inter[f] : bnd[f - p.n_int];
     p.f_em[f] = pr.em; p.f_km[f] = pr.km; p.f_ep[f] = pr.ep; p.f_kp[f] = pr.kp;
     const int qm = p.P[pr.em] + 2;
-    const int qf = pr.ep >= 0 ? std::max(qm, p.P[pr.ep] + 2) : qm;
+    const int qp = pr.ep >= 0 ? p.P[pr.ep] + 2 : qm;
+    const int qf = std::max(qm, qp);
     p.f_qf[f] = qf;
     if (pr.ep >= 0 && p.P[pr.ep] != p.P[pr.em]) ++p.n_nonconf;
     const int64_t npts = dim == 2 ? qf : (int64_t)qf * qf;
-    p.f_troff[f + 1] = p.f_troff[f] + npts;
-    p.f_goff[f + 1] = p.f_goff[f] + npts * (pr.ep >= 0 ? 1 + 2 * dim : 1 + dim);
+    if (p2p && pr.ep >= 0) {
+      // each side's own rule: trace [u-, g-, u+~, g+~] at qm points then
+      // [u+, g+, u-~, g-~] at qp points (~: the other side's values interpolated
+      // to these points); geometry [W-, c-] then [W+, c+]
+      const int64_t npm = dim == 2 ? qm : (int64_t)qm * qm, npp = dim == 2 ? qp : (int64_t)qp * qp;
+      p.f_troff[f + 1] = p.f_troff[f] + npm + npp;
+      p.f_goff[f + 1] = p.f_goff[f] + (npm + npp) * (1 + dim);
+    } else {
+      p.f_troff[f + 1] = p.f_troff[f] + npts;
+      p.f_goff[f + 1] = p.f_goff[f] + npts * (pr.ep >= 0 ? 1 + 2 * dim : 1 + dim);
+    }
+    // rule of each side's own points (qf: the shared rule), and the other side's
+    // rule in the slot flags
+    const int q_own_m = p2p ? qm : qf, q_own_p = p2p ? qp : qf;
     if (pr.ep >= 0) {
       // orientation: plus corner (beta0, beta1) must carry the same vertex as minus
       // corner b with b_perm[m] = beta_m xor flip_m
@@ -309,32 +327,34 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
       if (found < 0) { err = "face " + std::to_string(f) + ": no orientation matches"; return SIP_ERR_MESH; }
       p.f_orient[f] = found;
       p.orient_hist[found] += 1;
-      p.slots[(size_t)pr.em * nf + pr.km] = FaceSlot{(int32_t)f, 0, 0, (int8_t)qf, 0};
-      p.slots[(size_t)pr.ep * nf + pr.kp] = FaceSlot{(int32_t)f, 1, (int8_t)found, (int8_t)qf, 0};
+      p.slots[(size_t)pr.em * nf + pr.km] = FaceSlot{(int32_t)f, 0, 0, (int8_t)q_own_m, face_oq_bits(q_own_p)};
+      p.slots[(size_t)pr.ep * nf + pr.kp] = FaceSlot{(int32_t)f, 1, (int8_t)found, (int8_t)q_own_p, face_oq_bits(q_own_m)};
     } else {
-      p.slots[(size_t)pr.em * nf + pr.km] = FaceSlot{(int32_t)f, 0, 0, (int8_t)qf, (int8_t)kFaceBnd};
+      p.slots[(size_t)pr.em * nf + pr.km] = FaceSlot{(int32_t)f, 0, 0, (int8_t)qf, (int8_t)(kFaceBnd | face_oq_bits(qf))};
     }
   }
   p.trace_points = p.f_troff[F];
 
   // ---- face geometry in canonical (minus side) point order
-  p.fgeo.assign(p.f_goff[F], 0.0);
-  for (int64_t f = 0; f < F; ++f) {
-    const int qf = p.f_qf[f];
-    gauss_legendre(qf, xg, wg);
+  // W = w |J| |J^-T e_a| and c = J^-1 n of the minus side (cm) and of the plus
+  // side (cp, c+ = J+^-1 (-n)) at the canonical points of the q-point Gauss rule
+  // of face f; W [npts], cm and cp [dim][npts], nullptr where not wanted.
+  // Returns the face area by that rule, or -1 if the two sides do not coincide.
+  auto eval_face = [&](int64_t f, int qf, double* Wo, double* cmo, double* cpo) -> double {
+    std::vector<double> xgq, wgq;
+    gauss_legendre(qf, xgq, wgq);
     const int npts = dim == 2 ? qf : qf * qf;
     const int em = p.f_em[f], km = p.f_km[f], ep = p.f_ep[f], kp = p.f_kp[f];
     const int am = km / 2, sm = km % 2;
     int tm[2], ntm = 0;
     for (int k = 0; k < dim; ++k) if (k != am) tm[ntm++] = k;
-    double* fg = &p.fgeo[p.f_goff[f]];
     double area = 0.0;
     for (int z = 0; z < npts; ++z) {
       const int zi[2] = {z % qf, z / qf};
       double xi[3];
       xi[am] = sm ? 1.0 : -1.0;
       double w = 1.0;
-      for (int m = 0; m < dim - 1; ++m) { xi[tm[m]] = xg[zi[m]]; w *= wg[zi[m]]; }
+      for (int m = 0; m < dim - 1; ++m) { xi[tm[m]] = xgq[zi[m]]; w *= wgq[zi[m]]; }
       Geo g;
       eval_map(dim, &ev[(size_t)em * nc * dim], xi, g);
       double nraw[3], nn = 0.0;
@@ -344,12 +364,13 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
       for (int i = 0; i < dim; ++i) n[i] = nraw[i] / nn;
       const double W = w * std::fabs(g.det) * nn;
       area += W;
-      fg[z] = W;
-      for (int m = 0; m < dim; ++m) {
-        double c = 0.0;
-        for (int i = 0; i < dim; ++i) c += g.Ji[m][i] * n[i];
-        fg[(1 + m) * npts + z] = c;
-      }
+      if (Wo) Wo[z] = W;
+      if (cmo)
+        for (int m = 0; m < dim; ++m) {
+          double c = 0.0;
+          for (int i = 0; i < dim; ++i) c += g.Ji[m][i] * n[i];
+          cmo[m * npts + z] = c;
+        }
       if (ep >= 0) {
         // plus-side reference point of the same physical point: invert orient_map
         const int ap = kp / 2, sp = kp % 2;
@@ -367,7 +388,7 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
           }
         double xip[3];
         xip[ap] = sp ? 1.0 : -1.0;
-        for (int m = 0; m < dim - 1; ++m) xip[tp[m]] = xg[jj[m]];
+        for (int m = 0; m < dim - 1; ++m) xip[tp[m]] = xgq[jj[m]];
         Geo gp;
         eval_map(dim, &ev[(size_t)ep * nc * dim], xip, gp);
         double dx = 0.0, h = 0.0;
@@ -375,29 +396,56 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
           dx = std::max(dx, std::fabs(gp.x[i] - g.x[i]));
           h = std::max(h, std::fabs(g.J[i][0]) + std::fabs(g.J[i][1]) + (dim == 3 ? std::fabs(g.J[i][2]) : 0.0));
         }
-        if (dx > 1e-11 * h) {
-          err = "face " + std::to_string(f) + ": sides do not coincide (mesh not conforming)";
-          return SIP_ERR_MESH;
-        }
-        for (int m = 0; m < dim; ++m) {
-          double c = 0.0;
-          for (int i = 0; i < dim; ++i) c -= gp.Ji[m][i] * n[i];   // c+ = J+^-1 (-n)
-          fg[(1 + dim + m) * npts + z] = c;
-        }
+        if (dx > 1e-11 * h) return -1.0;
+        if (cpo)
+          for (int m = 0; m < dim; ++m) {
+            double c = 0.0;
+            for (int i = 0; i < dim; ++i) c -= gp.Ji[m][i] * n[i];   // c+ = J+^-1 (-n)
+            cpo[m * npts + z] = c;
+          }
       }
+    }
+    return area;
+  };
+  p.fgeo.assign(p.f_goff[F], 0.0);
+  std::vector<double> shared_tmp;
+  for (int64_t f = 0; f < F; ++f) {
+    const int qf = p.f_qf[f];
+    const int npts = dim == 2 ? qf : qf * qf;
+    const int em = p.f_em[f], km = p.f_km[f], ep = p.f_ep[f], kp = p.f_kp[f];
+    const int am = km / 2;
+    double* fg = &p.fgeo[p.f_goff[f]];
+    // the shared rule's [W, c-, c+] (for the area, hence tau, and the orthogonality
+    // test): stored as is, or (point-to-point) a temporary beside each side's own
+    // rule [W-, c-] at Q- points then [W+, c+] at Q+ points
+    const bool own = p2p && ep >= 0;
+    if (own) shared_tmp.assign((size_t)(1 + 2 * dim) * npts, 0.0);
+    double* sg = own ? shared_tmp.data() : fg;
+    const double area = eval_face(f, qf, sg, sg + npts, ep >= 0 ? sg + (1 + dim) * npts : nullptr);
+    bool ok = area > 0.0;
+    if (own && ok) {
+      const int qm = p.P[em] + 2, qp = p.P[ep] + 2;
+      const int npm = dim == 2 ? qm : qm * qm, npp = dim == 2 ? qp : qp * qp;
+      ok = eval_face(f, qm, fg, fg + npm, nullptr) > 0.0;
+      double* fp = fg + (1 + dim) * npm;
+      ok = ok && eval_face(f, qp, fp, nullptr, fp + npp) > 0.0;
+    }
+    if (!ok) {
+      err = "face " + std::to_string(f) + ": sides do not coincide (mesh not conforming)";
+      return SIP_ERR_MESH;
     }
     // orthogonal face: c has no tangential component on either side
     {
       bool orth = true;
       for (int z = 0; z < npts && orth; ++z) {
-        const double cn = std::fabs(fg[(1 + am) * npts + z]);
+        const double cn = std::fabs(sg[(1 + am) * npts + z]);
         for (int m = 0; m < dim; ++m)
-          if (m != am && std::fabs(fg[(1 + m) * npts + z]) > 1e-13 * cn) orth = false;
+          if (m != am && std::fabs(sg[(1 + m) * npts + z]) > 1e-13 * cn) orth = false;
         if (ep >= 0) {
           const int ap = kp / 2;
-          const double cp = std::fabs(fg[(1 + dim + ap) * npts + z]);
+          const double cp = std::fabs(sg[(1 + dim + ap) * npts + z]);
           for (int m = 0; m < dim; ++m)
-            if (m != ap && std::fabs(fg[(1 + dim + m) * npts + z]) > 1e-13 * cp) orth = false;
+            if (m != ap && std::fabs(sg[(1 + dim + m) * npts + z]) > 1e-13 * cp) orth = false;
         }
       }
       if (orth) {
@@ -449,7 +497,21 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
       const int qf = p.f_qf[f];
       const int npts = dim == 2 ? qf : qf * qf;
       const int ncomp = p.f_ep[f] >= 0 ? 1 + 2 * dim : 1 + dim;
-      if (faff[f]) {
+      if (faff[f] && p2p && p.f_ep[f] >= 0) {
+        // own rules: [W-, c-] at Q- points, [W+, c+] at Q+ points -> the same
+        // constants as a shared face (W without the weight, c-, c+)
+        const int qm = p.P[p.f_em[f]] + 2, qp = p.P[p.f_ep[f]] + 2;
+        const int npm = dim == 2 ? qm : qm * qm, npp = dim == 2 ? qp : qp * qp;
+        gauss_legendre(qm, wv, wq);
+        const double wz = dim == 2 ? wq[0] : wq[0] * wq[0];
+        fgn[fnew[f]] = src[0] / wz;
+        for (int m = 0; m < dim; ++m) {
+          fgn[fnew[f] + 1 + m] = src[(1 + m) * npm];
+          fgn[fnew[f] + 1 + dim + m] = src[(1 + dim) * npm + (1 + m) * npp];
+        }
+        p.slots[(size_t)p.f_em[f] * 2 * dim + p.f_km[f]].flags |= kFaceAffine;
+        p.slots[(size_t)p.f_ep[f] * 2 * dim + p.f_kp[f]].flags |= kFaceAffine;
+      } else if (faff[f]) {
         gauss_legendre(qf, wv, wq);
         const double wz = dim == 2 ? wq[0] : wq[0] * wq[0];
         fgn[fnew[f]] = src[0] / wz;
@@ -457,7 +519,7 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
         p.slots[(size_t)p.f_em[f] * 2 * dim + p.f_km[f]].flags |= kFaceAffine;
         if (p.f_ep[f] >= 0) p.slots[(size_t)p.f_ep[f] * 2 * dim + p.f_kp[f]].flags |= kFaceAffine;
       } else {
-        std::copy(src, src + ncomp * npts, fgn.begin() + fnew[f]);
+        std::copy(src, src + (p.f_goff[f + 1] - p.f_goff[f]), fgn.begin() + fnew[f]);
       }
     }
     p.fgeo.swap(fgn);
@@ -500,6 +562,11 @@ void element_flops(const Plan& p, int64_t e, double& ft, double& fm) {
     // flux, projection, tangential transposed derivative on the face (P), and the
     // lift l(+-1) P + l'(+-1) c_a t at every Gauss point
     fm += 12.0 * np + (orth ? 1.0 : d) * np + interp_m + (orth ? 0.0 : 2.0 * (d - 1) * Q * QF1) + 2.0 * 2.0 * QV;
+    // point-to-point interpolation of this side's two trace scalars from its own
+    // rule to the other side's oq-point rule
+    const int oq = face_oq(sl.flags);
+    if (!(sl.flags & kFaceBnd) && oq != sl.qf)
+      ft += (d == 2 ? oq : oq * oq) * 2.0 * 2.0 * (d == 2 ? qf : qf * (qf + 1.0));
   }
 }
 

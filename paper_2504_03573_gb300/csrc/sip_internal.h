@@ -112,12 +112,20 @@ constexpr int kFaceBnd = 1;     // boundary face
 constexpr int kFaceOrth = 2;    // c = J^-1 n has no tangential component on either side
 constexpr int kFaceAffine = 4;  // both sides affine: geometry stored as constants (W without the weight)
 
+// bits 3-6 of the slot flags: points per direction of the OTHER side's rule
+// (equal to qf with a shared rule; the neighbour's own rule with point-to-point
+// interpolation, SIP_FACES_P2P)
+constexpr int kFaceOqShift = 3;
+constexpr int8_t face_oq_bits(int q) { return (int8_t)(q << kFaceOqShift); }
+constexpr int face_oq(int flags) { return (flags >> kFaceOqShift) & 15; }
+
 struct FaceSlot {  // 8 bytes
   int32_t face;    // face id
   int8_t side;     // 0: minus side (or boundary), 1: plus side
   int8_t orient;   // plus side: bit0 flip t0, bit1 flip t1, bit2 transpose; else 0
-  int8_t qf;       // points per direction of the shared face rule
-  int8_t flags;    // kFaceBnd | kFaceOrth
+  int8_t qf;       // points per direction of this side's face rule (the shared rule,
+                   // or with SIP_FACES_P2P this element's own Q)
+  int8_t flags;    // kFaceBnd | kFaceOrth | kFaceAffine | face_oq_bits(other side's rule)
 };
 
 constexpr int kTileQfMask = 0xff;  // bits 0-7: largest face rule of the tile
@@ -170,7 +178,9 @@ struct Plan {
   std::vector<int64_t> f_goff;   // face geometry offset
   std::vector<double> f_tau;
   // face geometry, canonical point order (minus side's parametrisation):
-  // interior: W, c-_0..c-_{d-1}, c+_0..c+_{d-1}; boundary: W, c_0..c_{d-1}
+  // interior: W, c-_0..c-_{d-1}, c+_0..c+_{d-1}; boundary: W, c_0..c_{d-1};
+  // SIP_FACES_P2P interior faces: W-, c- at the minus side's own Q- points, then
+  // W+, c+ at the plus side's own Q+ points
   // each comp holds npts = qf^(dim-1) values; c = J^-1 n of that side;
   // affine faces (kFaceAffine) store one value per comp, W without the weight w_z
   std::vector<double> fgeo;

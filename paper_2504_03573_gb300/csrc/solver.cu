@@ -211,6 +211,8 @@ void sip_handle::release() {
   cudaFree(gd.vgeo); cudaFree(gd.fgeo); cudaFree(gd.tau); cudaFree(gd.kappa);
   cudaFree(gf.vgeo); cudaFree(gf.fgeo); cudaFree(gf.tau); cudaFree(gf.kappa);
   cudaFree(trace_d);
+  cudaFree(p2p_I_d);
+  cudaFree(p2p_I_f);
   cudaFree(ug_d);
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);
@@ -680,11 +682,13 @@ extern "C" {
 
 int sip_cg_solve(sip_handle* h, int mode, const double* b, double* x, int nrhs, double rtol, sip_stats* stats,
                  void* stream) {
+  if (h && h->p2p()) return fail(SIP_ERR_ARG, "CG needs the symmetric shared-rule operator (face_scheme SIP_FACES_SHARED)");
   return solve_impl(h, mode, b, x, nrhs, rtol, stats, (cudaStream_t)stream, 0);
 }
 
 int sip_cg_solve_transpose(sip_handle* h, int mode, const double* b, double* x, int nrhs, double rtol,
                            sip_stats* stats, void* stream) {
+  if (h && h->p2p()) return fail(SIP_ERR_ARG, "CG needs the symmetric shared-rule operator (face_scheme SIP_FACES_SHARED)");
   return solve_impl(h, mode, b, x, nrhs, rtol, stats, (cudaStream_t)stream, 1);
 }
 
@@ -709,6 +713,7 @@ int sip_cg_checkpoint_get(sip_handle* h, int slot, double* x, double* r, double*
 
 int sip_cg_replay(sip_handle* h, double* x, double* r, double* p, double* rr_host, int iters, void* stream) {
   if (!h || !x || !r || !p || !rr_host || iters < 0) return fail(SIP_ERR_ARG, "bad argument");
+  if (h->p2p()) return fail(SIP_ERR_ARG, "CG needs the symmetric shared-rule operator (face_scheme SIP_FACES_SHARED)");
   int rc = ensure_solver(h, 1);
   if (rc) return rc;
   rc = ensure_cg(h, h->cg64, sizeof(double), 1);

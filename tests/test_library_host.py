@@ -136,3 +136,22 @@ def test_create_without_gpu_fails_loudly(pkg):
     m = si.workload("c1_2d_4x4_p3")
     with pytest.raises(pkg.SipError):
         pkg.SipOperator.from_mesh(m)
+
+
+def test_p2p_plan(pkg):
+    """Point-to-point variant: each interior face holds one trace block per side
+    at that side's own (P+2)-point rule, [u, g, u~, g~] (4 values per point);
+    boundary faces as with the shared rule.  Penalties do not change."""
+    m = si.rotate_elements(si.structured_mesh(3, 3, jitter=0.1, seed=3, order_range=(1, 6)), 4)
+    a = _info(pkg, m)
+    b = _info(pkg, m, face_scheme=pkg.SIP_FACES_P2P)
+    orc_faces = __import__("oracle").SipOracle(m)
+    q = m.orders + 2
+    shared = sum(max(q[em], q[ep]) ** 2 for (em, _), (ep, _) in orc_faces.interior) + sum(q[e] ** 2 for e, _ in orc_faces.bfaces)
+    own = sum(q[em] ** 2 + q[ep] ** 2 for (em, _), (ep, _) in orc_faces.interior) + sum(q[e] ** 2 for e, _ in orc_faces.bfaces)
+    assert a["trace_points"] == shared
+    assert b["trace_points"] == own
+    for k in ("max_tau", "min_h_face", "n_faces_interior", "n_faces_nonconforming", "ndof", "nquad"):
+        assert a[k] == b[k], k
+    with pytest.raises(pkg.SipError):
+        _info(pkg, m, face_scheme=2)
