@@ -5,11 +5,14 @@
 // groups of equal order of Sec. 5.1).
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
-#include <utility>
 #include <string>
+#include <thread>
+#include <utility>
 #include <vector>
 
 #include "sip_internal.h"
@@ -17,6 +20,36 @@
 namespace sip {
 
 namespace {
+
+// Gauss rules of every size the plan uses, computed once
+struct GaussRules {
+  std::vector<double> x[kQMax + 1], w[kQMax + 1];
+  GaussRules() {
+    for (int q = 1; q <= kQMax; ++q) gauss_legendre(q, x[q], w[q]);
+  }
+};
+
+// body(i0, i1) over [0, n) split into contiguous chunks on the host's cores;
+// the first failure (nonzero return) of any chunk is returned with its message
+template <typename F>
+int parallel_chunks(int64_t n, F body, std::string& err) {
+  const int64_t min_chunk = 256;
+  int nt = (int)std::min<int64_t>(std::max(1u, std::thread::hardware_concurrency()), 64);
+  nt = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (n + min_chunk - 1) / min_chunk));
+  if (nt == 1) return body(0, n, err);
+  std::vector<std::thread> th;
+  std::vector<std::string> errs(nt);
+  std::vector<int> rcs(nt, 0);
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t]() { rcs[t] = body(n * t / nt, n * (t + 1) / nt, errs[t]); });
+  for (auto& x : th) x.join();
+  for (int t = 0; t < nt; ++t)
+    if (rcs[t]) {
+      err = errs[t];
+      return rcs[t];
+    }
+  return 0;
+}
 
 struct Geo {
   double x[3];
@@ -162,8 +195,8 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
       for (int i = 0; i < dim; ++i)
         ev[(e * nc + c) * dim + i] = mesh->vert[mesh->elem_vert[e * nc + c] * dim + i];
 
-  // ---- volume geometry
-  std::vector<double> xg, wg;
+  // ---- volume geometry (elements in parallel)
+  const GaussRules rules;
   const int nG = dim == 2 ? 4 : 7;
   p.vgoff.assign(E + 1, 0);
   for (int64_t e = 0; e < E; ++e) p.vgoff[e + 1] = p.vgoff[e] + (int64_t)nG * (p.quad_off[e + 1] - p.quad_off[e]);
@@ -171,9 +204,11 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
   p.xq.assign((size_t)p.nquad * dim, 0.0);
   p.vol.assign(E, 0.0);
   p.affine.assign(E, 0);
-  for (int64_t e = 0; e < E; ++e) {
+  int vrc = parallel_chunks(E, [&](int64_t e0, int64_t e1, std::string& verr) -> int {
+  for (int64_t e = e0; e < e1; ++e) {
     const int Q = p.P[e] + 2;
-    gauss_legendre(Q, xg, wg);
+    const std::vector<double>& xg = rules.x[Q];
+    const std::vector<double>& wg = rules.w[Q];
     const double* v = &ev[(size_t)e * nc * dim];
     const int nq = dim == 2 ? Q * Q : Q * Q * Q;
     double* G = &p.vgeo[p.vgoff[e]];
@@ -185,7 +220,7 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
       Geo g;
       eval_map(dim, v, xi, g);
       if (!(g.det > 0.0)) {
-        err = "element " + std::to_string(e) + ": non-positive Jacobian at a volume Gauss point";
+        verr = "element " + std::to_string(e) + ": non-positive Jacobian at a volume Gauss point";
         return SIP_ERR_MESH;
       }
       const double wj = w * g.det;
@@ -227,6 +262,9 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
     }
     p.affine[e] = mixed <= 1e-13 * hmax ? 1 : 0;
   }
+  return 0;
+  }, err);
+  if (vrc) return vrc;
 
   // ---- face pairing by vertex sets
   const int nfc = 1 << (dim - 1);
@@ -341,8 +379,8 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
   // of face f; W [npts], cm and cp [dim][npts], nullptr where not wanted.
   // Returns the face area by that rule, or -1 if the two sides do not coincide.
   auto eval_face = [&](int64_t f, int qf, double* Wo, double* cmo, double* cpo) -> double {
-    std::vector<double> xgq, wgq;
-    gauss_legendre(qf, xgq, wgq);
+    const std::vector<double>& xgq = rules.x[qf];
+    const std::vector<double>& wgq = rules.w[qf];
     const int npts = dim == 2 ? qf : qf * qf;
     const int em = p.f_em[f], km = p.f_km[f], ep = p.f_ep[f], kp = p.f_kp[f];
     const int am = km / 2, sm = km % 2;
@@ -408,8 +446,11 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
     return area;
   };
   p.fgeo.assign(p.f_goff[F], 0.0);
+  // faces in parallel: each writes only its own geometry, penalty and the flags
+  // of its own two slots
+  int frc = parallel_chunks(F, [&](int64_t f0, int64_t f1, std::string& ferr) -> int {
   std::vector<double> shared_tmp;
-  for (int64_t f = 0; f < F; ++f) {
+  for (int64_t f = f0; f < f1; ++f) {
     const int qf = p.f_qf[f];
     const int npts = dim == 2 ? qf : qf * qf;
     const int em = p.f_em[f], km = p.f_km[f], ep = p.f_ep[f], kp = p.f_kp[f];
@@ -431,7 +472,7 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
       ok = ok && eval_face(f, qp, fp, nullptr, fp + npp) > 0.0;
     }
     if (!ok) {
-      err = "face " + std::to_string(f) + ": sides do not coincide (mesh not conforming)";
+      ferr = "face " + std::to_string(f) + ": sides do not coincide (mesh not conforming)";
       return SIP_ERR_MESH;
     }
     // orthogonal face: c has no tangential component on either side
@@ -460,6 +501,9 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
     if (ep < 0 && !opt.boundary)  // pure-Neumann variant: boundary faces contribute nothing
       for (int z = 0; z < npts; ++z) fg[z] = 0.0;
   }
+  return 0;
+  }, err);
+  if (frc) return frc;
 
   // ---- regular (affine) elements and faces keep constants only (Sec. 5.1: regular
   // vs deformed elements): the kernels multiply by the Gauss weights themselves
@@ -473,7 +517,7 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
       const int64_t nq = p.quad_off[e + 1] - p.quad_off[e];
       const double* src = &p.vgeo[p.vgoff[e]];
       if (p.affine[e]) {
-        gauss_legendre(p.P[e] + 2, wv, wq);
+        const std::vector<double>& wq = rules.w[p.P[e] + 2];
         double w0 = 1.0;
         for (int k = 0; k < dim; ++k) w0 *= wq[0];
         for (int c = 0; c < nG; ++c) vg[vnew[e] + c] = src[c * nq] / w0;
@@ -502,7 +546,7 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
         // constants as a shared face (W without the weight, c-, c+)
         const int qm = p.P[p.f_em[f]] + 2, qp = p.P[p.f_ep[f]] + 2;
         const int npm = dim == 2 ? qm : qm * qm, npp = dim == 2 ? qp : qp * qp;
-        gauss_legendre(qm, wv, wq);
+        const std::vector<double>& wq = rules.w[qm];
         const double wz = dim == 2 ? wq[0] : wq[0] * wq[0];
         fgn[fnew[f]] = src[0] / wz;
         for (int m = 0; m < dim; ++m) {
@@ -512,7 +556,7 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
         p.slots[(size_t)p.f_em[f] * 2 * dim + p.f_km[f]].flags |= kFaceAffine;
         p.slots[(size_t)p.f_ep[f] * 2 * dim + p.f_kp[f]].flags |= kFaceAffine;
       } else if (faff[f]) {
-        gauss_legendre(qf, wv, wq);
+        const std::vector<double>& wq = rules.w[qf];
         const double wz = dim == 2 ? wq[0] : wq[0] * wq[0];
         fgn[fnew[f]] = src[0] / wz;
         for (int c = 1; c < ncomp; ++c) fgn[fnew[f] + c] = src[c * npts];

@@ -28,7 +28,7 @@ import numpy as np
 __all__ = [
     "Mesh", "structured_mesh", "workload", "WORKLOADS", "ndof", "dof_offsets",
     "random_vector", "random_rhs_batch", "kappa_lattice_field", "rotate_elements",
-    "affine_map_vertices",
+    "affine_map_vertices", "pulse_refined_mesh",
 ]
 
 
@@ -184,6 +184,18 @@ def affine_map_vertices(mesh: Mesh, a: np.ndarray, b: np.ndarray | None = None) 
     if b is not None:
         v = v + np.asarray(b, dtype=np.float64)
     return dataclasses.replace(mesh, vert=v)
+
+
+def pulse_refined_mesh(dim: int, n: int, p_low: int, p_high: int, box: float = 0.5) -> Mesh:
+    """Local p-refinement set-up of the Gaussian-pulse study: the cube [-1,1]^dim
+    as an n^dim grid, elements whose centre lies in [-box, box]^dim at order
+    p_high, the others at p_low."""
+    m = structured_mesh(dim, n, order=p_low)
+    m = affine_map_vertices(m, 2.0 * np.eye(dim), -np.ones(dim))
+    cent = m.vert[m.elem_vert].mean(axis=1)
+    inside = np.all(np.abs(cent) < box, axis=1)
+    orders = np.where(inside, p_high, p_low).astype(np.int32)
+    return dataclasses.replace(m, orders=orders, name=f"pulse_{dim}d_{n}_p{p_low}_{p_high}")
 
 
 WORKLOADS = {
