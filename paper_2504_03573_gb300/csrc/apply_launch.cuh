@@ -5,6 +5,27 @@
 #include "apply_kernels.cuh"
 #include "aux_kernels.cuh"
 
+namespace sip {
+// Launch of an apply kernel, with programmatic stream serialisation when pdl
+// (the kernel may begin while the previous one in the stream finishes; its
+// grid_dep_wait() orders every dependent read).
+template <typename A>
+inline cudaError_t launch_dependent(void (*kern)(A), dim3 grid, int threads, size_t smem, cudaStream_t s, bool pdl,
+                                    const A& a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+}  // namespace sip
+
 #define SIP_DEFINE_APPLY_TU(SUFFIX, TYPE, DIM)                                                     \
   namespace sip {                                                                                 \
   cudaError_t upload_tables_##SUFFIX(const double* tab_d, const float* tab_f, const int* ioff,     \
@@ -42,12 +63,16 @@
                                     cudaEvent_t ev0, cudaEvent_t ev1, cudaEvent_t ev2) {          \
     if (nctas == 0) return cudaSuccess;                                                           \
     dim3 grid(nctas, nrhs);                                                                       \
+    /* programmatic dependent launch, except when events time each kernel */                      \
+    const bool pdl = ev0 == nullptr;                                                              \
     if (ev0) cudaEventRecord(ev0, s);                                                             \
-    if (a.p2p_I) k_trace<TYPE, DIM, true><<<grid, threads, smem_trace, s>>>(a);                     \
-    else k_trace<TYPE, DIM, false><<<grid, threads, smem_trace, s>>>(a);                           \
+    cudaError_t e = launch_dependent(a.p2p_I ? k_trace<TYPE, DIM, true> : k_trace<TYPE, DIM, false>, \
+                                     grid, threads, smem_trace, s, pdl, a);                       \
+    if (e != cudaSuccess) return e;                                                               \
     if (ev1) cudaEventRecord(ev1, s);                                                             \
-    if (a.p2p_I) k_main<TYPE, DIM, true><<<grid, threads, smem_main, s>>>(a);                       \
-    else k_main<TYPE, DIM, false><<<grid, threads, smem_main, s>>>(a);                             \
+    e = launch_dependent(a.p2p_I ? k_main<TYPE, DIM, true> : k_main<TYPE, DIM, false>, grid,       \
+                         threads, smem_main, s, pdl, a);                                          \
+    if (e != cudaSuccess) return e;                                                               \
     if (ev2) cudaEventRecord(ev2, s);                                                             \
     return cudaGetLastError();                                                                    \
   }                                                                                               \
