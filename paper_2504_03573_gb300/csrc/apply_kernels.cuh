@@ -1106,24 +1106,13 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
     default: break;          \
   }
 
-// Programmatic dependent launch: a kernel launched with programmatic stream
-// serialisation may start while the kernel before it in the stream is still
-// running.  Everything before grid_dep_wait() reads only data that no kernel
-// writes (tables, the mesh's face slots and tile lists); the wait returns once
-// the previous kernel has completed and its writes are visible.  Without the
-// launch attribute it returns at once.
-__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-// lets the next kernel in the stream (launched with the attribute) start its
-// CTAs, which then wait in grid_dep_wait() for this kernel to complete
-__device__ __forceinline__ void grid_dep_launch_next() { asm volatile("griddepcontrol.launch_dependents;" :::); }
-
 template <typename T, int DIM, int N, bool MAIN, bool P2P>
 __device__ __forceinline__ void run_tiles(const ApplyArgs<T>& a, int ti0, int ti1, int rhs, unsigned char* smem_raw) {
   T* tb = reinterpret_cast<T*>(smem_raw);
   TileMeta<DIM>* mt = reinterpret_cast<TileMeta<DIM>*>(smem_raw + table_block_bytes(sizeof(T), N));
   T* sm = reinterpret_cast<T*>(smem_raw + table_block_bytes(sizeof(T), N) + kMetaBytes);
   load_tables<T, N>(tb);
-  grid_dep_wait();
+  grid_dep_wait();  // before anything that another kernel writes
   for (int ti = ti0; ti < ti1; ++ti) {
     if (ti > ti0) __syncthreads();  // the previous tile's last stage still reads shared memory
     const Tile t = a.tiles[ti];

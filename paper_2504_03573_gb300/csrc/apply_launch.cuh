@@ -5,26 +5,6 @@
 #include "apply_kernels.cuh"
 #include "aux_kernels.cuh"
 
-namespace sip {
-// Launch of an apply kernel, with programmatic stream serialisation when pdl
-// (the kernel may begin while the previous one in the stream finishes; its
-// grid_dep_wait() orders every dependent read).
-template <typename A>
-inline cudaError_t launch_dependent(void (*kern)(A), dim3 grid, int threads, size_t smem, cudaStream_t s, bool pdl,
-                                    const A& a) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = dim3(threads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, kern, a);
-}
-}  // namespace sip
 
 #define SIP_DEFINE_APPLY_TU(SUFFIX, TYPE, DIM)                                                     \
   namespace sip {                                                                                 \
@@ -67,11 +47,11 @@ inline cudaError_t launch_dependent(void (*kern)(A), dim3 grid, int threads, siz
     const bool pdl = ev0 == nullptr;                                                              \
     if (ev0) cudaEventRecord(ev0, s);                                                             \
     cudaError_t e = launch_dependent(a.p2p_I ? k_trace<TYPE, DIM, true> : k_trace<TYPE, DIM, false>, \
-                                     grid, threads, smem_trace, s, pdl, a);                       \
+                                     grid, dim3(threads), smem_trace, s, pdl, a);                 \
     if (e != cudaSuccess) return e;                                                               \
     if (ev1) cudaEventRecord(ev1, s);                                                             \
     e = launch_dependent(a.p2p_I ? k_main<TYPE, DIM, true> : k_main<TYPE, DIM, false>, grid,       \
-                         threads, smem_main, s, pdl, a);                                          \
+                         dim3(threads), smem_main, s, pdl, a);                                    \
     if (e != cudaSuccess) return e;                                                               \
     if (ev2) cudaEventRecord(ev2, s);                                                             \
     return cudaGetLastError();                                                                    \

@@ -3,8 +3,11 @@
 // the auxiliary kernels, face geometry helpers.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <type_traits>
+#include <utility>
 
 #include "sip_internal.h"
 
@@ -43,6 +46,35 @@ struct ApplyArgs {
 };
 
 constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation (launch_dependent below) may start while the kernel before it
+// in the stream is still running.  Everything a kernel does before
+// grid_dep_wait() reads only data that no kernel writes (tables, the mesh's
+// face slots and tile lists); the wait returns once the previous kernel has
+// completed and its writes are visible.  Without the launch attribute it
+// returns at once.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// lets the next kernel in the stream (launched with the attribute) start its
+// CTAs, which then wait in grid_dep_wait() for this kernel to complete
+__device__ __forceinline__ void grid_dep_launch_next() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+// Launch with programmatic stream serialisation when pdl.
+template <typename... P, typename... A>
+inline cudaError_t launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                                    A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
 
 // ---- constant tables; each translation unit that includes this header holds
 // its own copy, uploaded by sip_upload_tables_<tu>() at handle creation.
