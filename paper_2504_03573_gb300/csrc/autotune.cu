@@ -23,6 +23,7 @@ using namespace sip;
 extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream) {
   if (!h) return fail(SIP_ERR_ARG, "null handle");
   if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
+  NvtxRange range("sip_autotune");
   if (reps < 1) reps = 10;
   cudaStream_t s = (cudaStream_t)stream;
   const Plan& p = h->plan;

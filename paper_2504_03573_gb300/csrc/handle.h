@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <map>
 #include <string>
@@ -114,6 +115,15 @@ template <>
 inline const float* sip_handle::p2p_interp<float>() const { return p2p_I_f; }
 
 namespace sip {
+// NVTX range for the lifetime of the object: the library's entry points mark
+// themselves (sip_apply, sip_cg_solve, refinement steps, sip_autotune) so that
+// profilers can select them; without an attached tool this costs a branch.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 // Tiles of one precision and the CTA that runs each, with the shared memory of
 // the two kernels.  per_sm: resident CTAs per SM the CTAs were balanced for.
 struct Schedule {

@@ -404,6 +404,7 @@ int norms2(sip_handle* h, CgWork& W, const double* v, int nrhs, cudaStream_t s, 
 
 int solve_impl(sip_handle* h, int mode, const double* b, double* x_out, int nrhs, double rtol,
                sip_stats* stats, cudaStream_t user, int transpose) {
+  NvtxRange range(mode == SIP_CG_FP32_REFINED ? "sip_cg_solve fp32-refined" : "sip_cg_solve fp64");
   auto t0 = std::chrono::steady_clock::now();
   if (!h || !b || !x_out) return fail(SIP_ERR_ARG, "null argument");
   if (nrhs < 1) return fail(SIP_ERR_ARG, "nrhs must be >= 1");
@@ -585,6 +586,7 @@ int solve_impl(sip_handle* h, int mode, const double* b, double* x_out, int nrhs
       }
       since = 0;
       // refinement: FP64 residual of the FP64 iterate
+      NvtxRange refine("sip_cg refinement");
       rc = apply_any(h, SIP_FP64, h->x64, h->r64, nrhs, s, transpose, nullptr);
       if (rc) break;
       st.applies_fp64 += 1;
