@@ -517,10 +517,12 @@ int sip_set_lambda(sip_handle* h, double lambda) {
 }
 
 int sip_apply(sip_handle* h, int precision, const void* x, void* y, int nrhs, void* stream) {
+  NvtxRange r("sip_apply");
   return apply_any(h, precision, x, y, nrhs, (cudaStream_t)stream, 0, nullptr);
 }
 
 int sip_apply_transpose(sip_handle* h, int precision, const void* x, void* y, int nrhs, void* stream) {
+  NvtxRange r("sip_apply_transpose");
   return apply_any(h, precision, x, y, nrhs, (cudaStream_t)stream, 1, nullptr);
 }
 
