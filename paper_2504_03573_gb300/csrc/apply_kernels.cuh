@@ -398,7 +398,9 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
   if (fine) {
     constexpr int NSC = scratch_slots(DIM);
     constexpr int SL = 4 * (FT + FMAX);  // one slot: Ft [4][FT], Ff [4][FMAX]
-    const int nfld = orth ? 2 : 4;
+    // fields to carry to the finer rule: u and du/dn_ref, plus the tangential
+    // derivatives (one in 2D, two in 3D) where c has tangential components
+    const int nfld = orth ? 2 : 2 + (DIM - 1);
     for (int k0 = 0; k0 < NFACE; k0 += NSC) {
       if constexpr (DIM == 2) {
         for (int w = threadIdx.x; w < ne * NSC * nfld * qfm; w += blockDim.x) {

@@ -595,7 +595,7 @@ void element_flops(const Plan& p, int64_t e, double& ft, double& fm) {
     const bool orth = sl.flags & kFaceOrth;  // tangential terms vanish identically
     const double qf = sl.qf;
     const double np = d == 2 ? qf : qf * qf;
-    const double nfl_t = orth ? 2.0 : 4.0, nfl_m = orth ? 2.0 : 1.0 + d;
+    const double nfl_t = orth ? 2.0 : 1.0 + d, nfl_m = orth ? 2.0 : 1.0 + d;
     double interp_t = 0.0, interp_m = 0.0;
     if (sl.qf != (int)Q) {
       const double per_field = 2.0 * (d == 2 ? qf * Q : (Q * qf * Q + qf * qf * Q));
