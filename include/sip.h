@@ -162,7 +162,8 @@ int  sip_set_lambda(sip_handle* h, double lambda);
 int  sip_set_kappa(sip_handle* h, const double* kappa_dev, void* stream);
 
 /* y = A x (a1-a7: volume term by sum factorisation, trace evaluation at the
- * shared face Gauss points, SIP flux, lift to both sides without atomics).
+ * shared face Gauss points, SIP flux, lift to both sides without atomics; with
+ * face_scheme SIP_FACES_P2P, the point-to-point variant of Sec. 3.3).
  * precision SIP_FP64: x_dev, y_dev are double [nrhs][ndof];
  * SIP_FP32: float [nrhs][ndof] (FP32 arithmetic and accumulation).
  * x and y must not overlap.  nrhs >= 1. */
@@ -170,7 +171,8 @@ int  sip_apply(sip_handle* h, int precision, const void* x_dev, void* y_dev, int
 
 /* y = A^T x with the roles of trial side (trace evaluation) and test side
  * (lift) exchanged in the face terms (Appendix A: A^T has blocks M'_C <-> M_C^T).
- * For this operator A^T = A, so the result equals sip_apply up to rounding. */
+ * For this operator A^T = A, so the result equals sip_apply up to rounding.
+ * SIP_FACES_P2P handles: SIP_ERR_ARG. */
 int  sip_apply_transpose(sip_handle* h, int precision, const void* x_dev, void* y_dev, int nrhs,
                          void* stream);
 
@@ -186,7 +188,9 @@ int  sip_apply_transpose(sip_handle* h, int precision, const void* x_dev, void* 
 int  sip_cg_solve(sip_handle* h, int mode, const double* b_dev, double* x_dev, int nrhs,
                   double rtol, sip_stats* stats, void* stream);
 
-/* Solves A^T x = b with the transpose apply (adjoint solve); same contract. */
+/* Solves A^T x = b with the transpose apply (adjoint solve); same contract.
+ * Both solves, and sip_cg_replay, need the symmetric operator: SIP_FACES_P2P
+ * handles return SIP_ERR_ARG. */
 int  sip_cg_solve_transpose(sip_handle* h, int mode, const double* b_dev, double* x_dev, int nrhs,
                             double rtol, sip_stats* stats, void* stream);
 
