@@ -47,7 +47,7 @@ NRHS = {"c4_3d_24cube_jitter_p2to7": 32}
 
 # DRAM bytes (read + write) per launch of the FP64 main kernel, from one ncu capture
 # of that workload with the current kernels (profiles/apply_<workload>.md)
-NCU_MAIN_TRAFFIC = {"c2_2d_64x64_jitter_p2to6": 10.937344e6, "c3_3d_32cube_p4": 183.435264e6 + 22.599168e6}
+NCU_MAIN_TRAFFIC = {"c2_2d_64x64_jitter_p2to6": 10.929664e6, "c3_3d_32cube_p4": 183.096576e6 + 22.797568e6}
 
 
 def peaks():
