@@ -77,3 +77,50 @@ def test_planted_mistake_is_caught(mutation):
     lam = 1.1
     res = _checks(Mutant(m, mutation, lam=lam), m, np.eye(2), np.zeros(2), lam)
     assert not all(res), (mutation, res)
+
+
+class P2PMutant(SipOracle):
+    """The point-to-point variant with one planted mistake (a copy of the
+    variant's block formula with the mistake switched in)."""
+
+    def __init__(self, mesh, mutation, **kw):
+        self.mutation = mutation
+        super().__init__(mesh, face_scheme="p2p", **kw)
+
+    def interior_face_blocks(self, pair):
+        (em, _), (ep, _) = pair
+        q = (int(self.Q[em]), int(self.Q[ep]))
+        own = []
+        for v in range(2):
+            W, _, tau, side_m, side_p = self.face_data(pair, qf=q[v])
+            phi, dn = side_m if v == 0 else side_p
+            if v == 1 and self.mutation == "plus_normal_flipped":
+                dn = -dn
+            own.append((W, (phi, dn)))
+        sgn = (1.0, -1.0)
+        half = 1.0 if self.mutation == "no_half_in_consistency" else 0.5
+        out = {}
+        for v in range(2):
+            Wv, (pv, dv) = own[v]
+            for w in range(2):
+                if w == v:
+                    pw, dw = pv, dv
+                else:
+                    L = self._face_interp(q[w], q[v])
+                    pw, dw = L @ own[w][1][0], L @ own[w][1][1]
+                out[(v, w)] = (-0.5 * sgn[w] * np.einsum("z,zi,zj->ij", Wv, dv, pw)
+                               - half * sgn[v] * np.einsum("z,zi,zj->ij", Wv, pv, dw)
+                               + tau * sgn[v] * sgn[w] * np.einsum("z,zi,zj->ij", Wv, pv, pw))
+        return out
+
+
+@pytest.mark.parametrize("mutation", ["plus_normal_flipped", "no_half_in_consistency"])
+def test_planted_p2p_mistake_is_caught(mutation):
+    """The variant's pins: it equals the shared-rule operator wherever the lower
+    order's rule is exact (here orders 2 and 4 with Gauss rules, Q = P + 2)."""
+    m = si.structured_mesh(2, 4, jitter=0.0, seed=3, order_range=(2, 4))
+    S = SipOracle(m).assemble().toarray()
+    good = P2PMutant(m, "none").assemble().toarray()
+    assert np.abs(good - S).max() <= 1e-13 * np.abs(S).max()
+    bad = P2PMutant(m, mutation).assemble().toarray()
+    assert np.abs(bad - S).max() > 1e-6 * np.abs(S).max()
