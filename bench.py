@@ -14,6 +14,11 @@ with host buffers, clocks sampled during the timed region and the oracle's
 throughput on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+                  [--faces shared|p2p] [--tiling FILE | --save-tiling FILE] [--no-cg] [--no-cpu]
+  python bench.py --sweep orders|dofs      (hex throughput sweeps, one JSON line per mesh)
+
+The batched 24^3 workload applies to (and solves for) its 32 right-hand sides in
+one call; its GDoF/s count every right-hand side's DOFs.
 """
 from __future__ import annotations
 
