@@ -5,10 +5,8 @@
 // groups of equal order of Sec. 5.1).
 #include <algorithm>
 #include <array>
-#include <atomic>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <numeric>
 #include <string>
 #include <thread>
