@@ -155,6 +155,21 @@ class SipOperator:
         check(fn(self._h, precision, _ptr(x), _ptr(y), nrhs, _stream()))
         return y
 
+    def apply_host(self, x, precision=None, out=None):
+        """y = A x for CPU tensors (pinned or pageable), through sip_apply_host:
+        the library copies x in, applies and copies y out, and returns when y is
+        complete."""
+        torch = _torch()
+        if precision is None:
+            precision = SIP_FP32 if x.dtype == torch.float32 else SIP_FP64
+        dtype = torch.float32 if precision == SIP_FP32 else torch.float64
+        if x.is_cuda or x.dtype != dtype or not x.is_contiguous() or x.shape[-1] != self.ndof:
+            raise SipError(_lib.SIP_ERR_ARG, f"expected contiguous CPU {dtype} [..., {self.ndof}]")
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        y = torch.empty_like(x) if out is None else out
+        check(lib.sip_apply_host(self._h, precision, _ptr(x), _ptr(y), nrhs, _stream()))
+        return y
+
     def apply_transpose(self, x, precision=None, out=None):
         return self.apply(x, precision, out, transpose=True)
 

@@ -108,6 +108,7 @@ SIGNATURES = {
     "sip_set_lambda": (_I, [_H, _D]),
     "sip_set_kappa": (_I, [_H, _P, _P]),
     "sip_apply": (_I, [_H, _I, _P, _P, _I, _P]),
+    "sip_apply_host": (_I, [_H, _I, _P, _P, _I, _P]),
     "sip_apply_transpose": (_I, [_H, _I, _P, _P, _I, _P]),
     "sip_cg_solve": (_I, [_H, _I, _P, _P, _I, _D, C.POINTER(sip_stats), _P]),
     "sip_cg_solve_transpose": (_I, [_H, _I, _P, _P, _I, _D, C.POINTER(sip_stats), _P]),

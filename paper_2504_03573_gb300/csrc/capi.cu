@@ -521,6 +521,37 @@ int sip_apply(sip_handle* h, int precision, const void* x, void* y, int nrhs, vo
   return apply_any(h, precision, x, y, nrhs, (cudaStream_t)stream, 0, nullptr);
 }
 
+int sip_apply_host(sip_handle* h, int precision, const void* x, void* y, int nrhs, void* stream) {
+  NvtxRange r("sip_apply_host");
+  if (!h || !x || !y) return fail(SIP_ERR_ARG, "null handle or vector");
+  if (nrhs < 1) return fail(SIP_ERR_ARG, "nrhs must be >= 1");
+  if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
+  const size_t bytes = (size_t)nrhs * (size_t)h->plan.ndof * (precision == SIP_FP64 ? sizeof(double) : sizeof(float));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (bytes > h->io_cap) {
+    cudaStreamSynchronize(s);  // earlier calls may still use the old buffers
+    cudaFree(h->io_x);
+    cudaFree(h->io_y);
+    h->io_x = h->io_y = nullptr;
+    h->io_cap = 0;
+    cudaError_t e = cudaMalloc(&h->io_x, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->io_y, bytes);
+    if (e != cudaSuccess) {
+      cudaFree(h->io_x);
+      h->io_x = nullptr;
+      return cuda_fail(e, "sip_apply_host buffers");
+    }
+    h->io_cap = bytes;
+  }
+  cudaError_t e = cudaMemcpyAsync(h->io_x, x, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "sip_apply_host copy in");
+  int rc = apply_any(h, precision, h->io_x, h->io_y, nrhs, s, 0, nullptr);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(y, h->io_y, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? SIP_OK : cuda_fail(e, "sip_apply_host copy out");
+}
+
 int sip_apply_transpose(sip_handle* h, int precision, const void* x, void* y, int nrhs, void* stream) {
   NvtxRange r("sip_apply_transpose");
   return apply_any(h, precision, x, y, nrhs, (cudaStream_t)stream, 1, nullptr);

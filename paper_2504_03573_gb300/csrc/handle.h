@@ -82,6 +82,10 @@ struct sip_handle {
   size_t trace_cap = 0;
   double* ug_d = nullptr;
   size_t ug_cap = 0;
+  // device copies of host vectors for sip_apply_host (x, y; bytes each)
+  void* io_x = nullptr;
+  void* io_y = nullptr;
+  size_t io_cap = 0;
   size_t smem_trace[2] = {0, 0};
   size_t smem_main[2] = {0, 0};
   // timing

@@ -211,6 +211,8 @@ void sip_handle::release() {
   cudaFree(gd.vgeo); cudaFree(gd.fgeo); cudaFree(gd.tau); cudaFree(gd.kappa);
   cudaFree(gf.vgeo); cudaFree(gf.fgeo); cudaFree(gf.tau); cudaFree(gf.kappa);
   cudaFree(trace_d);
+  cudaFree(io_x);
+  cudaFree(io_y);
   cudaFree(p2p_I_d);
   cudaFree(p2p_I_f);
   cudaFree(ug_d);
