@@ -93,3 +93,30 @@ def test_gauss_rule_condition(p_low, p_high, symmetric):
         assert np.abs(A - S).max() <= 1e-13 * np.abs(S).max()
     else:
         assert _asym(A) >= 1e-4
+
+
+def test_transition_layer_restores_symmetry():
+    """Sec. 3.3: a P4Q5 element (4 coefficients, 5 GLL points) cannot neighbour a
+    P2Q3 one under point-to-point interpolation, but a transition layer of P2Q5
+    elements (the lower order's coefficients, the higher order's points) between
+    them makes both interfaces safe: P4Q5-P2Q5 shares its points, and P2Q5-P2Q3
+    integrates degree 1 + 1 on the 3-point GLL rule (exact to degree 3).
+    2D, columns of quads along x; the paper's counts are coefficients, so degree
+    = count - 1."""
+    def column_mesh(n, spec):
+        m = si.structured_mesh(2, n, order=1)
+        col = (m.vert[m.elem_vert].mean(axis=1)[:, 0] * n).astype(int)
+        deg = np.array([spec[c][0] for c in col], dtype=np.int32)
+        q = np.array([spec[c][1] for c in col])
+        m.orders = deg
+        return m, q
+
+    high, trans, low = (3, 5), (1, 5), (1, 3)
+    m, q = column_mesh(2, [high, low])
+    direct = _dense(m, face_scheme="p2p", rule="gll", qorders=q)
+    m, q = column_mesh(3, [high, trans, low])
+    layered = _dense(m, face_scheme="p2p", rule="gll", qorders=q)
+    shared = _dense(m, face_scheme="shared", rule="gll", qorders=q)
+    assert _asym(direct) >= 1e-3
+    assert _asym(layered) <= 1e-13
+    assert np.abs(layered - shared).max() <= 1e-12 * np.abs(shared).max()
