@@ -245,3 +245,28 @@ def test_convergence_order_3d():
     errs = [_sine_error(3, n, 2) for n in (2, 4, 6)]
     rate = np.log(errs[1] / errs[2]) / np.log(6 / 4)
     assert rate >= 3 - 0.2, (errs, rate)
+
+
+@pytest.mark.parametrize("P", [2, 3])
+def test_half_domain_p_refinement(P):
+    """Sec. 4.2: with half of the domain one order higher (sin(2 pi x) sin(2 pi y),
+    k = 2 pi), the L2 error converges at the rate of the lower order, P + 1,
+    like the unrefined mesh, and is only somewhat lower than its error (the
+    lower-order half dominates)."""
+    k = 2 * np.pi
+
+    def err(n, p_left, p_right):
+        m = si.structured_mesh(2, n, order=1)
+        left = m.vert[m.elem_vert].mean(axis=1)[:, 0] < 0.5
+        m.orders = np.where(left, p_left, p_right).astype(np.int32)
+        orc = SipOracle(m)
+        ue = lambda x: np.prod(np.sin(k * x), axis=1)
+        uh = spla.spsolve(orc.assemble().tocsc(), orc.rhs(lambda x: (1 + 2 * k * k) * ue(x)))
+        return orc.l2_error(uh, ue)
+
+    uni = [err(n, P, P) for n in (4, 8, 16)]
+    half = [err(n, P, P + 1) for n in (4, 8, 16)]
+    rate = np.log2(half[1] / half[2])
+    assert abs(rate - np.log2(uni[1] / uni[2])) <= 0.2 and rate >= P + 1 - 0.2, (half, uni)
+    for h, u in zip(half, uni):
+        assert 0.4 * u <= h < u
