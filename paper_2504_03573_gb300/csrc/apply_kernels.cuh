@@ -22,11 +22,19 @@
 //
 // Thread mapping: every stage is a loop over the OUTPUT values of the tile's
 // elements (one output per work item), so a stage exposes elements x Q^DIM
-// independent items.  The 1D matrices live in shared memory in layouts where
-// the lanes of a warp (consecutive outputs) read consecutive addresses.
-// Elements are grouped in tiles of equal order (the paper's element groups);
-// one CTA per tile and right-hand side; a switch on the order selects the
-// compile-time specialisation (Sec. 5.1, "separate kernels for different orders").
+// independent items (FP32 in 3D: one line of Q outputs per work item, with the
+// matrices as constant-bank operands).  The 1D matrices live in shared memory
+// in layouts where the lanes of a warp (consecutive outputs) read consecutive
+// addresses.  Elements are grouped in tiles of equal order (the paper's element
+// groups); a CTA runs one or more tiles of one order per right-hand side
+// (grid.y); a switch on the order selects the compile-time specialisation
+// (Sec. 5.1, "separate kernels for different orders").
+//
+// Template flag P2P: the point-to-point interpolation variant (Sec. 3.3), where
+// each side keeps its own face rule; the shared-rule kernels contain none of
+// its code.  Both kernels start with programmatic dependent launch in mind:
+// they load their tables, then wait for the previous kernel in the stream
+// (griddepcontrol) before reading anything another kernel writes.
 #pragma once
 
 #include "common.cuh"
