@@ -155,3 +155,44 @@ def test_p2p_plan(pkg):
         assert a[k] == b[k], k
     with pytest.raises(pkg.SipError):
         _info(pkg, m, face_scheme=2)
+
+
+def test_header_is_plain_c_and_links(pkg, tmp_path):
+    """include/sip.h compiles as C99 and a C program linked against libsip.so
+    runs the host-only plan analysis through the ABI."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "sip.h"
+int main(void) {
+    /* 2 x 1 quads of [0,2] x [0,1], orders 2 and 3 */
+    const double vert[] = {0,0, 1,0, 2,0, 0,1, 1,1, 2,1};
+    const int64_t ev[] = {0,1,3,4, 1,2,4,5};
+    const int32_t orders[] = {2, 3};
+    sip_mesh m = {2, 6, vert, 2, ev};
+    sip_options o;
+    sip_options_default(&o);
+    sip_plan* p = NULL;
+    if (sip_plan_create(&m, orders, &o, &p) != SIP_OK) { printf("error %s\n", sip_last_error()); return 1; }
+    sip_plan_info info;
+    sip_plan_info_get(p, &info);
+    printf("%lld %lld %lld %lld\n", (long long)info.ndof, (long long)info.n_faces_interior,
+           (long long)info.n_faces_boundary, (long long)info.n_faces_nonconforming);
+    sip_plan_destroy(p);
+    return 0;
+}
+''')
+    lib = pkg._lib.LIB_PATH
+    exe = tmp_path / "abi"
+    inc = os.path.join(HERE, "..", "include")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", inc, str(src), lib, "-o", str(exe),
+                        "-Wl,-rpath," + os.path.dirname(lib)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.split() == ["25", "1", "6", "1"]
