@@ -50,3 +50,14 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(0.5, 1) == 0.5
     assert bench.job_throughput(10, 1, 0.5) == 20.0
+
+
+def test_reference_arm_prints_on_rank_zero_only(repo_root):
+    """Under torchrun the reference arm (the oracle on the host) runs on rank 0
+    alone; the other ranks exit 0 without work or output."""
+    import subprocess
+    import sys
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(repo_root, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "3"], capture_output=True, text=True, env=env, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == ""
