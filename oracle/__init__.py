@@ -20,16 +20,21 @@ Parity status of each part (what pins it is in ``tests/test_oracle_*.py``):
   penalty closed form for an element indicator, Galerkin consistency for
   polynomials vanishing on the boundary, constant null space of the
   pure-Neumann stiffness, manufactured-solution convergence order P+1);
+* face geometry of non-affine (bilinear / trilinear) elements: pinned by
+  Galerkin consistency on jittered meshes, which is exact there (the
+  integrands are polynomials once the Jacobian's adjugate is factored out),
+  and by the penalty closed form on jittered quads and hexahedra with
+  independently computed areas and volumes; this also pins the penalty
+  length h_F = min(|K-|, |K+|) / |F| (the paper leaves tau and h_F undefined;
+  that definition is the reading, |F| by the face's shared Gauss rule);
+* diffusivity kappa: pinned in the volume term by exact consistency with
+  -div(kappa grad u) for a kappa equal to 1 on every face; that face terms
+  keep kappa = 1 is a reading (the paper has no kappa), invisible to any pin
+  built on such a kappa;
 * point-to-point interpolation variant (Sec. 3.3, Table 2): pinned (equals
   the shared-rule operator on conforming meshes and wherever the low-order
   side's rule is exact; symmetric exactly under the paper's exactness
-  condition; the paper's three Table 2 cases classified as the paper does);
-* penalty length h_f on jittered (non-affine) faces: parity unpinned (the
-  paper does not define h_f; the reading min(|K-|,|K+|)/|F| is checked only
-  through the invariants above, which hold for any positive h_f);
-* diffusivity placement (kappa multiplies the volume diffusion term only):
-  parity unpinned beyond finite differences of the oracle's own assembly,
-  because the paper has no kappa.
+  condition; the paper's three Table 2 cases classified as the paper does).
 """
 from .quadrature import gauss_legendre, gauss_lobatto, lagrange_matrix, lagrange_deriv_matrix
 from .assembly import SipOracle

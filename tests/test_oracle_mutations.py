@@ -124,3 +124,75 @@ def test_planted_p2p_mistake_is_caught(mutation):
     assert np.abs(good - S).max() <= 1e-13 * np.abs(S).max()
     bad = P2PMutant(m, mutation).assemble().toarray()
     assert np.abs(bad - S).max() > 1e-6 * np.abs(S).max()
+
+
+# ---------------------------------------------------------------- non-affine face geometry
+# Mistakes that leave every affine pin intact (there the Jacobian is one constant
+# per element), caught by the jittered pins of test_oracle_nonaffine.py.
+
+class FaceGradMutant(SipOracle):
+    """Face gradients with the inverse Jacobian of the element centre instead
+    of the one at each face point."""
+
+    def _side_values(self, e, k, xi):
+        from oracle.assembly import basis_at, _map
+        phi, dphi = basis_at(int(self.N[e]), xi)
+        _, J = _map(self.vert[self.elem_vert[e]], xi)
+        _, Jc = _map(self.vert[self.elem_vert[e]], np.zeros((1, self.dim)))
+        Jinv_c = np.repeat(np.linalg.inv(Jc), xi.shape[0], axis=0)
+        gphys = np.einsum("pki,pkb->pib", Jinv_c, dphi)
+        return phi, gphys, J, np.linalg.inv(J)
+
+
+class PlusAreaMutant(SipOracle):
+    """Face area element W built from the plus side's |det J| (at the located
+    points) instead of the minus side's."""
+
+    def face_data(self, pair, qf=None):
+        from oracle.assembly import _locate, _map
+        (em, km), (ep, kp) = pair
+        qf = int(max(self.Q[em], self.Q[ep])) if qf is None else qf
+        zs, wz = self._face_rule(qf)
+        am, sm = divmod(km, 2)
+        xi_m = np.zeros((zs.shape[0], self.dim))
+        xi_m[:, am] = 1.0 if sm else -1.0
+        for j, b in enumerate([b for b in range(self.dim) if b != am]):
+            xi_m[:, b] = zs[:, j]
+        phim, gm, Jm, Jinvm = self._side_values(em, km, xi_m)
+        xphys, _ = _map(self.vert[self.elem_vert[em]], xi_m)
+        ap, sp_ = divmod(kp, 2)
+        xi_p = _locate(self.vert[self.elem_vert[ep]], xphys, ap, sp_)
+        phip, gp, Jp, _ = self._side_values(ep, kp, xi_p)
+        nraw = (1.0 if sm else -1.0) * Jinvm[:, am, :]
+        nrm = np.linalg.norm(nraw, axis=1)
+        nvec = nraw / nrm[:, None]
+        W = wz * np.abs(np.linalg.det(Jp)) * nrm
+        h = min(self.volume(em), self.volume(ep)) / W.sum()
+        tau = self.tau_scale * (max(self.P[em], self.P[ep]) + 1) ** 2 / h
+        return (W, nvec, tau, (phim, np.einsum("pib,pi->pb", gm, nvec)),
+                (phip, np.einsum("pib,pi->pb", gp, nvec)))
+
+
+def test_face_gradient_mistake_caught_only_on_jittered_meshes():
+    from test_oracle_nonaffine import _consistency_residual, _dirichlet_case
+    # invisible to the affine pins: symmetry, affine consistency, uniform penalty
+    m = si.rotate_elements(si.structured_mesh(**MESH), 2)
+    assert all(_checks(FaceGradMutant(m, lam=1.1), m, np.eye(2), np.zeros(2), 1.1))
+    # caught by consistency on a jittered mesh
+    mj, _, u, f = _dirichlet_case(2, 3, (4, 6), 0.2, 21)
+    assert _rel_asym(FaceGradMutant(mj, lam=1.3).assemble()) <= 1e-13
+    assert _consistency_residual(FaceGradMutant(mj, lam=1.3), u, f) > 1e-6
+
+
+def test_plus_side_area_mistake_caught_by_3d_jittered_penalty():
+    from test_oracle_nonaffine import _indicator_energies, _penalty_expectations_3d
+    # uniform hexahedra: both sides have the same Jacobian, nothing changes
+    mu = si.rotate_elements(si.structured_mesh(3, 2, seed=2, order_range=(1, 2)), 5)
+    good = _indicator_energies(SipOracle(mu, lam=0.7))
+    assert np.allclose(_indicator_energies(PlusAreaMutant(mu, lam=0.7)), good, rtol=1e-12, atol=0)
+    # jittered hexahedra: the closed form with independent areas and volumes fails
+    mj = si.rotate_elements(si.structured_mesh(3, 2, jitter=0.25, seed=41, order_range=(1, 2)), 42)
+    expect, _, _ = _penalty_expectations_3d(mj, 0.7)
+    assert np.max(np.abs(_indicator_energies(SipOracle(mj, lam=0.7)) - expect) / expect) <= 1e-12
+    got = _indicator_energies(PlusAreaMutant(mj, lam=0.7))
+    assert np.max(np.abs(got - expect) / expect) > 1e-6
