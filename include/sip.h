@@ -9,10 +9,15 @@
  *
  * discretised with tensor Lagrange polynomials on P+1 Gauss-Lobatto-Legendre
  * nodes per direction (Table 1, Lagrange-GLL; Eq. expansion), a (P+2)-point
- * Gauss rule per direction in the volume (Eq. iproduct) and ONE Gauss rule
- * with max(P-,P+)+2 points per direction on each face, shared by both sides
+ * rule per direction in the volume (Eq. iproduct) and ONE rule with
+ * max(P-,P+)+2 points per direction on each face, shared by both sides
  * (Sec. 3.3, "shared trace space"; the mortar-equivalent point evaluation of
- * Sec. 3.3).  Boundary faces use Nitsche's weak Dirichlet condition with g = 0
+ * Sec. 3.3).  The rules are Gauss-Legendre (default: traces evaluated from the
+ * element, TracePhysEval / TraceIProduct of Sec. 3.2) or Gauss-Lobatto-Legendre
+ * (sip_options.quad_rule = SIP_RULE_GLL: the volume points include the
+ * endpoints, so a conforming trace is a gather of the boundary points and the
+ * flux goes back by a scatter, GathrInterp / ScatrInterp of Sec. 3.2 and
+ * Sec. 5.1).  Boundary faces use Nitsche's weak Dirichlet condition with g = 0
  * ([[u]] = u n, {grad u} = grad u).  Penalty:
  *   tau_F = tau_scale (max(P-,P+)+1)^2 / h_F,  h_F = min(|K-|,|K+|) / |F|.
  *
@@ -23,8 +28,8 @@
  *   i0 + N i1 (+ N^2 i2), N = P_e+1, i0 along the element's first reference
  *   axis (local vertex bit 0).  Multi-RHS arrays are [nrhs][ndof], contiguous.
  * - Quadrature-point arrays (kappa, its gradient, iproduct input) are element
- *   major with (P_e+2)^dim Gauss points per element, lexicographic, first
- *   reference axis fastest; offsets from sip_quad_offsets.
+ *   major with (P_e+2)^dim volume points per element (of the handle's rule),
+ *   lexicographic, first reference axis fastest; offsets from sip_quad_offsets.
  * - Pointers named *_dev are CUDA device pointers owned by the caller; *_host
  *   are host pointers.  `stream` is a cudaStream_t passed as void* (NULL =
  *   legacy default stream).  Work is enqueued on that stream; the library does
@@ -45,7 +50,7 @@ extern "C" {
 #endif
 
 #define SIP_OK                0
-#define SIP_ERR_ARG           1  /* invalid argument (null pointer, bad size, order outside 1..8) */
+#define SIP_ERR_ARG           1  /* invalid argument (null pointer, bad size, order outside 1..SIP_MAX_ORDER) */
 #define SIP_ERR_MESH          2  /* non-manifold face, element glued to itself, non-positive Jacobian */
 #define SIP_ERR_CUDA          3  /* a CUDA runtime call failed (message has the CUDA error string) */
 #define SIP_ERR_OOM           4  /* device allocation failed */
@@ -58,14 +63,21 @@ extern "C" {
 #define SIP_FP32 1              /* apply in single precision with single accumulation */
 
 /* Interior-face flux evaluation (sip_options.face_scheme) */
-#define SIP_FACES_SHARED    0   /* one Gauss rule per face shared by both sides (Sec. 3.3) */
+#define SIP_FACES_SHARED    0   /* one rule per face shared by both sides (Sec. 3.3) */
 #define SIP_FACES_P2P       1   /* point-to-point interpolation between the sides' own rules
                                    (Sec. 3.3 "Point-to-point interpolation", Table 2) */
+
+/* Volume and face point sets (sip_options.quad_rule); P+2 points per direction either way */
+#define SIP_RULE_GAUSS      0   /* Gauss-Legendre: traces evaluated from the element (TracePhysEval,
+                                   Sec. 3.2), lifted by TraceIProduct */
+#define SIP_RULE_GLL        1   /* Gauss-Lobatto-Legendre: the boundary points of the volume rule are the
+                                   face points, so traces are gathered and fluxes scattered back before
+                                   one IProduct (GathrInterp / ScatrInterp, Sec. 3.2, Sec. 5.1) */
 
 #define SIP_CG_FP64         0   /* plain CG, FP64 apply */
 #define SIP_CG_FP32_REFINED 1   /* FP64 iterative refinement around an FP32-apply CG */
 
-#define SIP_MAX_ORDER 8
+#define SIP_MAX_ORDER 10
 
 /* Mesh: vertex coordinates and element connectivity (read only, copied). */
 typedef struct sip_mesh {
@@ -79,7 +91,7 @@ typedef struct sip_mesh {
 
 typedef struct sip_options {
     double  tau_scale;        /* penalty factor in tau_F, default 2 */
-    int32_t qvol_extra;       /* Q = P + qvol_extra volume Gauss points; only 2 is supported */
+    int32_t qvol_extra;       /* Q = P + qvol_extra volume points; only 2 is supported */
     int32_t boundary;         /* 1: Nitsche faces on the boundary (default); 0: drop them
                                  (pure Neumann operator) */
     double  inner_rtol;       /* FP32 inner CG tolerance in SIP_CG_FP32_REFINED, default 1e-5 */
@@ -89,7 +101,7 @@ typedef struct sip_options {
     int32_t checkpoint_every; /* save (x, r, p, r.r, k) every k CG iterations; 0 = off */
     int32_t checkpoint_slots; /* ring size for checkpoints, default 8 */
     int32_t face_scheme;      /* SIP_FACES_SHARED (default) or SIP_FACES_P2P.  P2P: each side of
-                                 an interior face evaluates the flux on its OWN (P+2)-point Gauss
+                                 an interior face evaluates the flux on its OWN (P+2)-point
                                  face rule, with the other side's two trace scalars (u and
                                  grad u . n) Lagrange-interpolated from that side's own points,
                                  and lifts it on its own rule.  The operator is then symmetric
@@ -97,6 +109,12 @@ typedef struct sip_options {
                                  integrand exactly (Sec. 3.3), so P2P handles support sip_apply
                                  (and sip_apply_static_scratch) only: transpose applies, CG
                                  solves and gradients return SIP_ERR_ARG. */
+    int32_t quad_rule;        /* SIP_RULE_GAUSS (default) or SIP_RULE_GLL: the point set of every
+                                 volume and face rule (P+2 points per direction) */
+    int32_t force_interp;     /* 1: every face goes through the interpolation to its shared rule and
+                                 the projection back, also where both sides' rules coincide (the
+                                 paper's measurement of the cost of non-conforming faces, Sec. 5.2);
+                                 same operator, more work.  Default 0 */
 } sip_options;
 
 typedef struct sip_stats {
@@ -136,7 +154,7 @@ void sip_options_default(sip_options* opt);
  * mesh; the caller may free it afterwards.  opt may be NULL (defaults).
  * Errors: SIP_ERR_ARG (null pointer, dim, order outside 1..SIP_MAX_ORDER),
  * SIP_ERR_MESH (face shared by more than two elements, non-positive Jacobian
- * at a volume Gauss point). */
+ * at a volume point). */
 int  sip_plan_create(const sip_mesh* mesh, const int32_t* orders_host, const sip_options* opt,
                      sip_plan** out);
 int  sip_plan_info_get(const sip_plan* plan, sip_plan_info* out);
@@ -156,13 +174,13 @@ int  sip_quad_offsets(const sip_handle* h, int64_t* out_host /* [n_elem+1] */);
 int  sip_get_plan_info(const sip_handle* h, sip_plan_info* out);
 
 /* Coefficients of the operator. lambda >= 0 (SIP_ERR_ARG otherwise).
- * kappa_dev: [nquad] FP64 diffusivity per volume Gauss point, copied (also to
+ * kappa_dev: [nquad] FP64 diffusivity per volume point, copied (also to
  * an FP32 copy for SIP_FP32 applies); NULL resets kappa to 1. */
 int  sip_set_lambda(sip_handle* h, double lambda);
 int  sip_set_kappa(sip_handle* h, const double* kappa_dev, void* stream);
 
 /* y = A x (a1-a7: volume term by sum factorisation, trace evaluation at the
- * shared face Gauss points, SIP flux, lift to both sides without atomics; with
+ * shared face points, SIP flux, lift to both sides without atomics; with
  * face_scheme SIP_FACES_P2P, the point-to-point variant of Sec. 3.3).
  * precision SIP_FP64: x_dev, y_dev are double [nrhs][ndof];
  * SIP_FP32: float [nrhs][ndof] (FP32 arithmetic and accumulation).
@@ -228,7 +246,7 @@ int  sip_mass_dot(sip_handle* h, const double* a_dev, const double* b_dev, doubl
 /* b_i = sum_q w_q |J_q| phi_i(x_q) f_q (IProduct, Eq. iproduct). f: double [nquad]. */
 int  sip_iproduct(sip_handle* h, const double* f_dev, double* b_dev, void* stream);
 
-/* Physical coordinates of the volume Gauss points: double [nquad][dim]. */
+/* Physical coordinates of the volume points: double [nquad][dim]. */
 int  sip_quad_points(sip_handle* h, double* xq_dev, void* stream);
 
 /* Algorithmic work of one apply (per RHS) under the library's work model:

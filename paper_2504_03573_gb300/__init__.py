@@ -15,11 +15,12 @@ import numpy as np
 
 from . import _lib
 from ._lib import (SIP_CG_FP32_REFINED, SIP_CG_FP64, SIP_FACES_P2P, SIP_FACES_SHARED, SIP_FP32, SIP_FP64,
-                   SipError, check, lib,
+                   SIP_RULE_GAUSS, SIP_RULE_GLL, SipError, check, lib,
                    sip_mesh, sip_options, sip_plan_info, sip_stats, sip_work)
 
 __all__ = ["SipOperator", "plan_info", "options", "SipError", "SIP_FP64", "SIP_FP32", "SIP_CG_FP64",
-           "SIP_CG_FP32_REFINED", "SIP_FACES_SHARED", "SIP_FACES_P2P", "SipApplyFn", "SipSolveFn", "lib"]
+           "SIP_CG_FP32_REFINED", "SIP_FACES_SHARED", "SIP_FACES_P2P", "SIP_RULE_GAUSS", "SIP_RULE_GLL",
+           "SipApplyFn", "SipSolveFn", "lib"]
 
 
 def options(**kw) -> sip_options:

@@ -24,7 +24,9 @@ SIP_CG_FP64 = 0
 SIP_CG_FP32_REFINED = 1
 SIP_FACES_SHARED = 0
 SIP_FACES_P2P = 1
-SIP_MAX_ORDER = 8
+SIP_RULE_GAUSS = 0
+SIP_RULE_GLL = 1
+SIP_MAX_ORDER = 10
 SIP_STATIC_TRACE_BYTES = 16 << 20
 
 ERROR_NAMES = {1: "SIP_ERR_ARG", 2: "SIP_ERR_MESH", 3: "SIP_ERR_CUDA", 4: "SIP_ERR_OOM",
@@ -47,7 +49,8 @@ class sip_options(C.Structure):
     _fields_ = [("tau_scale", C.c_double), ("qvol_extra", C.c_int32), ("boundary", C.c_int32),
                 ("inner_rtol", C.c_double), ("max_iter", C.c_int32), ("check_every", C.c_int32),
                 ("max_refine", C.c_int32), ("checkpoint_every", C.c_int32),
-                ("checkpoint_slots", C.c_int32), ("face_scheme", C.c_int32)]
+                ("checkpoint_slots", C.c_int32), ("face_scheme", C.c_int32), ("quad_rule", C.c_int32),
+                ("force_interp", C.c_int32)]
 
 
 class sip_stats(C.Structure):

@@ -30,6 +30,16 @@
 // (grid.y); a switch on the order selects the compile-time specialisation
 // (Sec. 5.1, "separate kernels for different orders").
 //
+// Point rules: Gauss-Legendre (TracePhysEval / TraceIProduct, Sec. 3.2) or, in
+// the translation units built with SIP_TU_RULE = SIP_RULE_GLL, Gauss-Lobatto-
+// Legendre points, whose boundary points are the face points: the trace
+// kernel then gathers u on the face instead of extrapolating it, and the main
+// kernel scatters the flux (s into the mass field, c t into the gradient
+// fields) before the one transposed gradient + IProduct (GathrInterp /
+// ScatrInterp, Sec. 3.2, Sec. 5.1).  kTileForce sends every face through the
+// interpolation path, also where its rule is the element's own (identity
+// interpolation): the paper's measure of the cost of non-conforming faces.
+//
 // Template flag P2P: the point-to-point interpolation variant (Sec. 3.3), where
 // each side keeps its own face rule; the shared-rule kernels contain none of
 // its code.  Both kernels start with programmatic dependent launch in mind:
@@ -83,7 +93,7 @@ __device__ __forceinline__ void load_tables(T* tb) {
     tb[TabLayout::DD(N) + q * Q + r] = v;
   }
   for (int w = threadIdx.x; w < 4 * Q; w += blockDim.x) tb[TabLayout::LL(N) + w] = ctab<T>(tab_L(Q) + w);
-  for (int f = Q + 1; f <= kQMax; ++f) {
+  for (int f = Q; f <= kQMax; ++f) {
     const int io = c_ioff[Q][f];
     for (int w = threadIdx.x; w < f * Q; w += blockDim.x) {
       const int z = w / Q, r = w - z * Q;  // I[z][r]
@@ -166,6 +176,11 @@ __device__ __forceinline__ void tang_axes(int a, int& t0, int& t1) {
 // Q^e for e in 0..2
 template <int Q>
 __device__ __forceinline__ int qpow(int e) { return e == 0 ? 1 : (e == 1 ? Q : Q * Q); }
+
+// a face whose rule is the element's own Q-point rule and that skips the
+// interpolation path (every face goes through it under kTileForce)
+template <int Q>
+__device__ __forceinline__ bool own_rule(int qf, bool force) { return qf == Q && !force; }
 
 // ============================================================ trace kernel
 // The tile's copy of its face slots, element ids, affine flags and face list in
@@ -297,6 +312,7 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
   const int qfm = t.flags & kTileQfMask;
   const bool fine = t.flags & kTileFine;
   const bool orth = t.flags & kTileOrth;
+  const bool force = t.flags & kTileForce;
   const int npm = DIM == 2 ? qfm : qfm * qfm;
   // per element: Fq [NFACE][4][QF1] (u, du/dn_ref, two tangential derivatives), then scratch
   T* const F0 = sm + 2 * S::QV;
@@ -355,13 +371,20 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
     const int sa = qpow<Q>(ax);
     const T* u = U + el * PER + j0 * qpow<Q>(t0) + (DIM == 3 ? j1 * qpow<Q>(t1) : 0);
     T uf = 0, dn = 0;
+    if constexpr (kGatherScatter) {
+      // the face points are the volume points of this boundary plane: gather
+      uf = u[(sd ? Q - 1 : 0) * sa];
 #pragma unroll
-    for (int r = 0; r < Q; ++r) {
-      const T v = u[r * sa];
-      uf = fma(LL[sd * Q + r], v, uf);
-      dn = fma(LL[(2 + sd) * Q + r], v, dn);
+      for (int r = 0; r < Q; ++r) dn = fma(LL[(2 + sd) * Q + r], u[r * sa], dn);
+    } else {
+#pragma unroll
+      for (int r = 0; r < Q; ++r) {
+        const T v = u[r * sa];
+        uf = fma(LL[sd * Q + r], v, uf);
+        dn = fma(LL[(2 + sd) * Q + r], v, dn);
+      }
     }
-    if (orth && mt->slot(el * 2 * DIM + k).qf == Q) {
+    if (orth && own_rule<Q>(mt->slot(el * 2 * DIM + k).qf, force)) {
       emit_vals(el, k, j0, j1, uf, dn, T(0), T(0));
       continue;
     }
@@ -398,7 +421,7 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
     const int el = w / (NFACE * QF1);
     const int rem = w - el * NFACE * QF1;
     const int k = rem / QF1, j = rem - k * QF1;
-    if (mt->slot(el * 2 * DIM + k).qf != Q) continue;
+    if (!own_rule<Q>(mt->slot(el * 2 * DIM + k).qf, force)) continue;
     emit(el, k, F0 + el * PER + k * 4 * QF1, QF1, j % Q, j / Q);
   }
   // 4. faces with a finer shared rule (p-non-conforming): NSC faces per round,
@@ -418,7 +441,7 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
           const int f = r2 / qfm, z = r2 - f * qfm;
           const int k = k0 + kk;
           const int qf = mt->slot(el * 2 * DIM + k).qf;
-          if (qf == Q || z >= qf) continue;
+          if (own_rule<Q>(qf, force) || z >= qf) continue;
           const T* IT = tb + TabLayout::IT(N, qf);
           const T* src = F0 + el * PER + k * 4 * QF1 + f * QF1;
           T s = 0;
@@ -436,7 +459,7 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
           const int j1 = r3 / qfm, z0 = r3 - j1 * qfm;
           const int k = k0 + kk;
           const int qf = mt->slot(el * 2 * DIM + k).qf;
-          if (qf == Q || z0 >= qf) continue;
+          if (own_rule<Q>(qf, force) || z0 >= qf) continue;
           const T* IT = tb + TabLayout::IT(N, qf);
           const T* src = F0 + el * PER + k * 4 * QF1 + f * QF1 + j1 * Q;
           T s = 0;
@@ -453,7 +476,7 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
           const int z1 = zz / qfm, z0 = zz - z1 * qfm;
           const int k = k0 + kk;
           const int qf = mt->slot(el * 2 * DIM + k).qf;
-          if (qf == Q || z0 >= qf || z1 >= qf) continue;
+          if (own_rule<Q>(qf, force) || z0 >= qf || z1 >= qf) continue;
           const T* IT = tb + TabLayout::IT(N, qf);
           const T* src = F0 + el * PER + SC + kk * SL + f * FT + z0;
           T s = 0;
@@ -469,7 +492,7 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
         const int z0 = zz % qfm, z1 = zz / qfm;
         const int k = k0 + kk;
         const int qf = mt->slot(el * 2 * DIM + k).qf;
-        if (qf == Q || z0 >= qf || z1 >= qf) continue;
+        if (own_rule<Q>(qf, force) || z0 >= qf || z1 >= qf) continue;
         emit(el, k, F0 + el * PER + SC + kk * SL + 4 * FT, FMAX, z0, z1);
       }
       __syncthreads();
@@ -692,6 +715,7 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
   constexpr int SL = NF * (FT + FMAX);  // one slot: Ft [NF][FT], Ff [NF][FMAX]
   const int ne = t.count;
   const int qfm = t.flags & kTileQfMask;
+  const bool force = t.flags & kTileForce;
   const int npm = DIM == 2 ? qfm : qfm * qfm;
   if constexpr (DIM == 2 && dense_faces<T>()) {
     // one scratch slot per face (slot k): all fine faces at once, as dense work
@@ -728,7 +752,7 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
         const int z0 = zz % qfm, z1 = zz / qfm;
         const int k = k0 + kk;
         const int qf = mt->slot(el * 2 * DIM + k).qf;
-        if (qf == Q || z0 >= qf || z1 >= qf) continue;
+        if (own_rule<Q>(qf, force) || z0 >= qf || z1 >= qf) continue;
         face_flux<T, DIM, N, P2P>(a, mt, rhs, tb, orth, el, k, z0, z1, F0 + el * per + SC + kk * SL + NF * FT, FMAX);
       }
       __syncthreads();
@@ -740,7 +764,7 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
           const int f = r2 / Q, r = r2 - f * Q;
           const int k = k0 + kk;
           const int qf = mt->slot(el * 2 * DIM + k).qf;
-          if (qf == Q || (orth && f != 0 && f != 1 + (k >> 1))) continue;
+          if (own_rule<Q>(qf, force) || (orth && f != 0 && f != 1 + (k >> 1))) continue;
           const T* II = tb + TabLayout::II(N, qf);
           const T* src = F0 + el * per + SC + kk * SL + NF * FT + f * FMAX;
           T s = 0;
@@ -757,7 +781,7 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
           const int z1 = r3 / Q, r0 = r3 - z1 * Q;
           const int k = k0 + kk;
           const int qf = mt->slot(el * 2 * DIM + k).qf;
-          if (qf == Q || z1 >= qf || (orth && f != 0 && f != 1 + (k >> 1))) continue;
+          if (own_rule<Q>(qf, force) || z1 >= qf || (orth && f != 0 && f != 1 + (k >> 1))) continue;
           const T* II = tb + TabLayout::II(N, qf);
           const T* src = F0 + el * per + SC + kk * SL + NF * FT + f * FMAX + qf * z1;
           T s = 0;
@@ -773,7 +797,7 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
           const int r0 = r % Q, r1 = r / Q;
           const int k = k0 + kk;
           const int qf = mt->slot(el * 2 * DIM + k).qf;
-          if (qf == Q || (orth && f != 0 && f != 1 + (k >> 1))) continue;
+          if (own_rule<Q>(qf, force) || (orth && f != 0 && f != 1 + (k >> 1))) continue;
           const T* II = tb + TabLayout::II(N, qf);
           const T* src = F0 + el * per + SC + kk * SL + f * FT + r0;
           T s = 0;
@@ -794,6 +818,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   const int ne = t.count;
   const bool fine = t.flags & kTileFine;
   const bool orth = t.flags & kTileOrth;
+  const bool force = t.flags & kTileForce;
   // per element: U [QV], G_0..G_{DIM-1} [QV each], R [QV], face buffers Fq
   // [NFACE][NF][QF1] (fields s, c_0 t, .., c_{d-1} t) and scratch
   T* U = sm;
@@ -862,7 +887,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
           const int el = v / (NFACE * QF1);
           const int rem = v - el * NFACE * QF1;
           const int k = rem / QF1, j = rem - k * QF1;
-          if (mt->slot(el * 2 * DIM + k).qf != Q) continue;
+          if (!own_rule<Q>(mt->slot(el * 2 * DIM + k).qf, force)) continue;
           face_flux<T, DIM, N, P2P>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
           continue;
         }
@@ -937,7 +962,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
             const int rem = v - el * NFACE * QF1;
             k = rem / QF1;
             j = rem - k * QF1;
-            if (fine && mt->slot(el * 2 * DIM + k).qf != Q) continue;
+            if (fine && !own_rule<Q>(mt->slot(el * 2 * DIM + k).qf, force)) continue;
           }
           face_flux<T, DIM, N, P2P>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
           continue;
@@ -997,11 +1022,48 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   }
   __syncthreads();
   if (fine) lift_fine_faces<T, DIM, N, P2P>(a, t, mt, flist, rhs, tb, F0, PER, orth);
-  // face field P = s + sum_{tangential m} D_m^T (c_m t) on the face (the
-  // tangential part of the lift after the transposed gradient); c_a t stays as
-  // is and is lifted with l'(+-1)
   const T* DD = tb + TabLayout::DD(N);
-  if (!orth) {
+  if constexpr (kGatherScatter) {
+    // ScatrInterp: the face points are volume points of the element's boundary
+    // planes, so each face adds s to R and c_m t to G_m there; the one
+    // transposed gradient + IProduct below then lifts both.  One work item per
+    // volume point, summing the faces through it (no two items write the same
+    // point).
+    for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
+      const int el = w / QV, q = w - el * QV;
+      const int qc[3] = {q % Q, (q / Q) % Q, DIM == 3 ? q / (Q * Q) : 0};
+      bool edge = false;
+#pragma unroll
+      for (int ax = 0; ax < DIM; ++ax) edge = edge || qc[ax] == 0 || qc[ax] == Q - 1;
+      if (!edge) continue;
+      T* b = sm + el * PER;
+      const T* fel = F0 + el * PER;
+      T r = b[(1 + DIM) * QV + q];
+      T g[DIM];
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) g[m] = b[(1 + m) * QV + q];
+#pragma unroll
+      for (int ax = 0; ax < DIM; ++ax) {
+        const int j = DIM == 2 ? qc[1 - ax] : (ax == 0 ? qc[1] + Q * qc[2] : (ax == 1 ? qc[0] + Q * qc[2] : qc[0] + Q * qc[1]));
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+          if (qc[ax] != (sd ? Q - 1 : 0)) continue;
+          const T* fq = fel + (2 * ax + sd) * NF * QF1 + j;
+          r += fq[0];
+#pragma unroll
+          for (int m = 0; m < DIM; ++m)
+            if (!orth || m == ax) g[m] += fq[(1 + m) * QF1];
+        }
+      }
+      b[(1 + DIM) * QV + q] = r;
+#pragma unroll
+      for (int m = 0; m < DIM; ++m) b[(1 + m) * QV + q] = g[m];
+    }
+    __syncthreads();
+  } else if (!orth) {
+    // face field P = s + sum_{tangential m} D_m^T (c_m t) on the face (the
+    // tangential part of the lift after the transposed gradient); c_a t stays
+    // as is and is lifted with l'(+-1)
     for (int w = threadIdx.x; w < ne * NFACE * QF1; w += blockDim.x) {
       const int el = w / (NFACE * QF1);
       const int rem = w - el * NFACE * QF1;
@@ -1024,7 +1086,8 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
     }
     __syncthreads();
   }
-  // H = R + sum_m D_m^T G_m + sum_faces [ l(+-1) P + l'(+-1) c_a t ] (into U)
+  // H = R + sum_m D_m^T G_m + sum_faces [ l(+-1) P + l'(+-1) c_a t ] (into U);
+  // with gathered / scattered traces the faces are already in R and G
   {
     const T* LL = tb + TabLayout::LL(N);
     for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
@@ -1043,7 +1106,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
         }
       }
 #pragma unroll
-      for (int ax = 0; ax < DIM; ++ax) {
+      for (int ax = 0; ax < (kGatherScatter ? 0 : DIM); ++ax) {
         const int j = DIM == 2 ? qc[1 - ax] : (ax == 0 ? qc[1] + Q * qc[2] : (ax == 1 ? qc[0] + Q * qc[2] : qc[0] + Q * qc[1]));
 #pragma unroll
         for (int sd = 0; sd < 2; ++sd) {
@@ -1113,6 +1176,8 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
     case 7: FN(7); break;    \
     case 8: FN(8); break;    \
     case 9: FN(9); break;    \
+    case 10: FN(10); break;  \
+    case 11: FN(11); break;  \
     default: break;          \
   }
 
@@ -1133,8 +1198,11 @@ __device__ __forceinline__ void run_tiles(const ApplyArgs<T>& a, int ti0, int ti
 
 // P2P: the point-to-point interpolation variant (SIP_FACES_P2P); the shared-rule
 // kernels are compiled without any of its code.
-template <typename T, int DIM, bool P2P>
+// RULE: the translation unit's point rule (kTuRule), part of the kernel's name
+// so that the Gauss and the Gauss-Lobatto instantiations stay distinct.
+template <typename T, int DIM, bool P2P, int RULE>
 __global__ void __launch_bounds__(256) k_trace(ApplyArgs<T> a) {
+  static_assert(RULE == kTuRule, "kernel instantiated in a unit of another rule");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   grid_dep_launch_next();  // k_main may load its tables meanwhile
   const int ti0 = a.cta_off[blockIdx.x], ti1 = a.cta_off[blockIdx.x + 1];
@@ -1153,8 +1221,9 @@ __global__ void __launch_bounds__(256) k_trace(ApplyArgs<T> a) {
 #define SIP_MAIN_LAUNCH_BOUNDS 256
 #endif
 
-template <typename T, int DIM, bool P2P>
+template <typename T, int DIM, bool P2P, int RULE>
 __global__ void __launch_bounds__(SIP_MAIN_LAUNCH_BOUNDS) k_main(ApplyArgs<T> a) {
+  static_assert(RULE == kTuRule, "kernel instantiated in a unit of another rule");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ti0 = a.cta_off[blockIdx.x], ti1 = a.cta_off[blockIdx.x + 1];
   if (ti0 >= ti1) return;

@@ -1,4 +1,6 @@
-// Launch wrapper instantiated once per (dimension, precision) translation unit.
+// Launch wrapper instantiated once per (point rule, dimension, precision)
+// translation unit; the unit defines SIP_TU_RULE (default Gauss-Legendre) before
+// including this header.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -22,18 +24,18 @@
   }                                                                                               \
   cudaError_t prepare_##SUFFIX() {                                                                 \
     cudaError_t e = cudaSuccess;                                                                  \
-    for (auto fn : {k_trace<TYPE, DIM, false>, k_trace<TYPE, DIM, true>, k_main<TYPE, DIM, false>,  \
-                    k_main<TYPE, DIM, true>})                                                     \
+    for (auto fn : {k_trace<TYPE, DIM, false, kTuRule>, k_trace<TYPE, DIM, true, kTuRule>,          \
+                    k_main<TYPE, DIM, false, kTuRule>, k_main<TYPE, DIM, true, kTuRule>})                                                     \
       if (e == cudaSuccess)                                                                       \
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);    \
     return e;                                                                                     \
   }                                                                                               \
   cudaError_t occupancy_##SUFFIX(int threads, size_t smem_trace, size_t smem_main, int* blocks) { \
     int bt = 0, bm = 0;                                                                           \
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bt, k_trace<TYPE, DIM, false>,   \
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bt, k_trace<TYPE, DIM, false, kTuRule>,   \
                                                                   threads, smem_trace);           \
     if (e != cudaSuccess) return e;                                                               \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, k_main<TYPE, DIM, false>, threads,      \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, k_main<TYPE, DIM, false, kTuRule>, threads,      \
                                                       smem_main);                                 \
     *blocks = bt < bm ? bt : bm;                                                                  \
     return e;                                                                                     \
@@ -46,11 +48,11 @@
     /* programmatic dependent launch, except when events time each kernel */                      \
     const bool pdl = ev0 == nullptr;                                                              \
     if (ev0) cudaEventRecord(ev0, s);                                                             \
-    cudaError_t e = launch_dependent(a.p2p_I ? k_trace<TYPE, DIM, true> : k_trace<TYPE, DIM, false>, \
+    cudaError_t e = launch_dependent(a.p2p_I ? k_trace<TYPE, DIM, true, kTuRule> : k_trace<TYPE, DIM, false, kTuRule>, \
                                      grid, dim3(threads), smem_trace, s, pdl, a);                 \
     if (e != cudaSuccess) return e;                                                               \
     if (ev1) cudaEventRecord(ev1, s);                                                             \
-    e = launch_dependent(a.p2p_I ? k_main<TYPE, DIM, true> : k_main<TYPE, DIM, false>, grid,       \
+    e = launch_dependent(a.p2p_I ? k_main<TYPE, DIM, true, kTuRule> : k_main<TYPE, DIM, false, kTuRule>, grid, \
                          dim3(threads), smem_main, s, pdl, a);                                    \
     if (e != cudaSuccess) return e;                                                               \
     if (ev2) cudaEventRecord(ev2, s);                                                             \
@@ -58,15 +60,15 @@
   }                                                                                               \
   }
 
-#define SIP_DEFINE_AUX_TU(DIM)                                                                   \
+#define SIP_DEFINE_AUX_TU(SUFFIX, DIM)                                                           \
   namespace sip {                                                                                \
-  cudaError_t prepare_aux_##DIM##d() {                                                           \
-    return cudaFuncSetAttribute(k_aux<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+  cudaError_t prepare_aux_##SUFFIX() {                                                           \
+    return cudaFuncSetAttribute(k_aux<DIM, kTuRule>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                 200 * 1024);                                                     \
   }                                                                                              \
-  cudaError_t launch_aux_##DIM##d(const AuxArgs& a, int ntiles, size_t smem, cudaStream_t s) {   \
+  cudaError_t launch_aux_##SUFFIX(const AuxArgs& a, int ntiles, size_t smem, cudaStream_t s) {   \
     if (ntiles == 0) return cudaSuccess;                                                         \
-    k_aux<DIM><<<ntiles, 256, smem, s>>>(a);                                                     \
+    k_aux<DIM, kTuRule><<<ntiles, 256, smem, s>>>(a);                                            \
     return cudaGetLastError();                                                                   \
   }                                                                                              \
   }

@@ -6,7 +6,8 @@
 namespace sip {
 
 // ============================================================ auxiliary element kernels (FP64)
-// kappa gradient w|J| grad a . grad b, mass inner product a^T M b, IProduct.
+// kappa gradient w|J| grad a . grad b, mass inner product a^T M b, IProduct,
+// at the volume points of the translation unit's rule.
 struct AuxArgs {
   const int64_t* dof_off;
   const int64_t* quad_off;
@@ -157,8 +158,10 @@ __device__ void aux_tile(const AuxArgs& a, const Tile& t, double* sm) {
   }
 }
 
-template <int DIM>
+// RULE: the translation unit's point rule (kTuRule), part of the kernel's name.
+template <int DIM, int RULE>
 __global__ void __launch_bounds__(256) k_aux(AuxArgs a) {
+  static_assert(RULE == kTuRule, "kernel instantiated in a unit of another rule");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* sm = reinterpret_cast<double*>(smem_raw);
   const Tile t = a.tiles[blockIdx.x];
@@ -171,6 +174,8 @@ __global__ void __launch_bounds__(256) k_aux(AuxArgs a) {
     case 7: aux_tile<DIM, 7>(a, t, sm); break;
     case 8: aux_tile<DIM, 8>(a, t, sm); break;
     case 9: aux_tile<DIM, 9>(a, t, sm); break;
+    case 10: aux_tile<DIM, 10>(a, t, sm); break;
+    case 11: aux_tile<DIM, 11>(a, t, sm); break;
     default: break;
   }
 }

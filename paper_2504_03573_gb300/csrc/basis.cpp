@@ -1,7 +1,8 @@
 // Host 1D point sets and Lagrange tables (Sec. 2.1: Gauss-Lobatto-Legendre
-// nodes for the Lagrange basis of Table 1, Gauss-Legendre points for volume and
-// trace quadrature, Eq. iproduct, Fig. 1).  FP64, computed once per process and
-// copied to __constant__ memory of every kernel translation unit.
+// nodes for the Lagrange basis of Table 1; Gauss-Legendre or Gauss-Lobatto-
+// Legendre points for volume and trace quadrature, Eq. iproduct, Fig. 1).
+// FP64, computed once per process and rule and copied to __constant__ memory of
+// the kernel translation units of that rule.
 #include <cmath>
 #include <vector>
 
@@ -98,18 +99,23 @@ double lagrange_deriv(const std::vector<double>& nodes, int j, double x) {
   return s;
 }
 
-void fill_tables(std::vector<double>& tab) {
+void point_rule(int rule, int q, std::vector<double>& x, std::vector<double>& w) {
+  if (rule == SIP_RULE_GLL) gauss_lobatto(q, x, w);
+  else gauss_legendre(q, x, w);
+}
+
+void fill_tables(int rule, std::vector<double>& tab) {
   tab.assign(kTabSize, 0.0);
   std::vector<double> xg, wg, xl, wl, xf, wf;
   for (int N = kNMin; N <= kNMax; ++N) {
     const int Q = N + 1;
     gauss_lobatto(N, xl, wl);
-    gauss_legendre(Q, xg, wg);
+    point_rule(rule, Q, xg, wg);
     for (int q = 0; q < Q; ++q)
       for (int i = 0; i < N; ++i) tab[tab_B(N) + q * N + i] = lagrange(xl, i, xg[q]);
   }
   for (int Q = kQMin; Q <= kQMax; ++Q) {
-    gauss_legendre(Q, xg, wg);
+    point_rule(rule, Q, xg, wg);
     for (int q = 0; q < Q; ++q)
       for (int r = 0; r < Q; ++r) tab[tab_D(Q) + q * Q + r] = lagrange_deriv(xg, r, xg[q]);
     for (int r = 0; r < Q; ++r) {
@@ -118,8 +124,8 @@ void fill_tables(std::vector<double>& tab) {
       tab[tab_L(Q) + 2 * Q + r] = lagrange_deriv(xg, r, -1.0);
       tab[tab_L(Q) + 3 * Q + r] = lagrange_deriv(xg, r, 1.0);
     }
-    for (int F = Q + 1; F <= kQMax; ++F) {
-      gauss_legendre(F, xf, wf);
+    for (int F = Q; F <= kQMax; ++F) {
+      point_rule(rule, F, xf, wf);
       for (int z = 0; z < F; ++z)
         for (int r = 0; r < Q; ++r) tab[tab_I(Q, F) + z * Q + r] = lagrange(xg, r, xf[z]);
     }

@@ -41,24 +41,57 @@ int apply_epb(int dim, int n, int precision, int threads) {
   return std::max(1, std::min(std::min(epb, room), kMaxEpb));
 }
 
-cudaError_t upload_tables_2d_f64(const double*, const float*, const int*, const double*, const float*);
-cudaError_t upload_tables_2d_f32(const double*, const float*, const int*, const double*, const float*);
-cudaError_t upload_tables_3d_f64(const double*, const float*, const int*, const double*, const float*);
-cudaError_t upload_tables_3d_f32(const double*, const float*, const int*, const double*, const float*);
-cudaError_t prepare_2d_f64();
-cudaError_t prepare_2d_f32();
-cudaError_t prepare_3d_f64();
-cudaError_t prepare_3d_f32();
+// Per (point rule, dimension, precision) translation unit: table upload, kernel
+// attributes, occupancy and the apply launch (apply_[gll_]{2d,3d}_{f64,f32}.cu).
+#define SIP_DECLARE_APPLY_TU(SUFFIX, TYPE)                                                            \
+  cudaError_t upload_tables_##SUFFIX(const double*, const float*, const int*, const double*, const float*); \
+  cudaError_t prepare_##SUFFIX();                                                                      \
+  cudaError_t occupancy_##SUFFIX(int, size_t, size_t, int*);                                           \
+  cudaError_t launch_apply_##SUFFIX(const ApplyArgs<TYPE>&, int, int, int, size_t, size_t, cudaStream_t, \
+                                    cudaEvent_t, cudaEvent_t, cudaEvent_t);
+SIP_DECLARE_APPLY_TU(2d_f64, double)
+SIP_DECLARE_APPLY_TU(2d_f32, float)
+SIP_DECLARE_APPLY_TU(3d_f64, double)
+SIP_DECLARE_APPLY_TU(3d_f32, float)
+SIP_DECLARE_APPLY_TU(gll_2d_f64, double)
+SIP_DECLARE_APPLY_TU(gll_2d_f32, float)
+SIP_DECLARE_APPLY_TU(gll_3d_f64, double)
+SIP_DECLARE_APPLY_TU(gll_3d_f32, float)
+#undef SIP_DECLARE_APPLY_TU
 cudaError_t prepare_aux_2d();
 cudaError_t prepare_aux_3d();
-cudaError_t occupancy_2d_f64(int, size_t, size_t, int*);
-cudaError_t occupancy_2d_f32(int, size_t, size_t, int*);
-cudaError_t occupancy_3d_f64(int, size_t, size_t, int*);
-cudaError_t occupancy_3d_f32(int, size_t, size_t, int*);
-cudaError_t launch_apply_2d_f64(const ApplyArgs<double>&, int, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
-cudaError_t launch_apply_3d_f64(const ApplyArgs<double>&, int, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
-cudaError_t launch_apply_2d_f32(const ApplyArgs<float>&, int, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
-cudaError_t launch_apply_3d_f32(const ApplyArgs<float>&, int, int, int, size_t, size_t, cudaStream_t, cudaEvent_t, cudaEvent_t, cudaEvent_t);
+cudaError_t prepare_aux_gll_2d();
+cudaError_t prepare_aux_gll_3d();
+
+// the unit of (rule, dim, precision): index [rule][dim - 2][precision]
+using UploadFn = cudaError_t (*)(const double*, const float*, const int*, const double*, const float*);
+using PrepareFn = cudaError_t (*)();
+using OccupancyFn = cudaError_t (*)(int, size_t, size_t, int*);
+static const UploadFn kUpload[2][2][2] = {{{upload_tables_2d_f64, upload_tables_2d_f32}, {upload_tables_3d_f64, upload_tables_3d_f32}},
+                                          {{upload_tables_gll_2d_f64, upload_tables_gll_2d_f32},
+                                           {upload_tables_gll_3d_f64, upload_tables_gll_3d_f32}}};
+static const PrepareFn kPrepare[2][2][2] = {{{prepare_2d_f64, prepare_2d_f32}, {prepare_3d_f64, prepare_3d_f32}},
+                                            {{prepare_gll_2d_f64, prepare_gll_2d_f32}, {prepare_gll_3d_f64, prepare_gll_3d_f32}}};
+static const OccupancyFn kOccupancy[2][2][2] = {
+    {{occupancy_2d_f64, occupancy_2d_f32}, {occupancy_3d_f64, occupancy_3d_f32}},
+    {{occupancy_gll_2d_f64, occupancy_gll_2d_f32}, {occupancy_gll_3d_f64, occupancy_gll_3d_f32}}};
+
+static cudaError_t launch_apply(int rule, int dim, const ApplyArgs<double>& a, int nctas, int nrhs, int threads,
+                                size_t st, size_t sm, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, cudaEvent_t e2) {
+  if (rule == SIP_RULE_GLL)
+    return dim == 2 ? launch_apply_gll_2d_f64(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2)
+                    : launch_apply_gll_3d_f64(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2);
+  return dim == 2 ? launch_apply_2d_f64(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2)
+                  : launch_apply_3d_f64(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2);
+}
+static cudaError_t launch_apply(int rule, int dim, const ApplyArgs<float>& a, int nctas, int nrhs, int threads,
+                                size_t st, size_t sm, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, cudaEvent_t e2) {
+  if (rule == SIP_RULE_GLL)
+    return dim == 2 ? launch_apply_gll_2d_f32(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2)
+                    : launch_apply_gll_3d_f32(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2);
+  return dim == 2 ? launch_apply_2d_f32(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2)
+                  : launch_apply_3d_f32(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2);
+}
 
 namespace {
 
@@ -83,26 +116,32 @@ std::vector<float> to_float(const std::vector<T>& v) {
 int ensure_tables(int dev) {
   if (dev < 0 || dev >= kMaxDevices) return fail(SIP_ERR_CUDA, "device index out of range");
   if (g_tables_uploaded[dev]) return SIP_OK;
-  std::vector<double> tab;
-  fill_tables(tab);
-  std::vector<float> tabf = to_float(tab);
-  int ioff[kQMax + 1][kQMax + 1];
-  for (int q = 0; q <= kQMax; ++q)
-    for (int f = 0; f <= kQMax; ++f) ioff[q][f] = (q >= kQMin && f > q) ? tab_I(q, f) : 0;
-  double gwd[kQMax + 1][kQMax] = {};
-  float gwf[kQMax + 1][kQMax] = {};
-  for (int q = 1; q <= kQMax; ++q) {
-    std::vector<double> gx, gw;
-    gauss_legendre(q, gx, gw);
-    for (int z = 0; z < q; ++z) { gwd[q][z] = gw[z]; gwf[q][z] = (float)gw[z]; }
-  }
   cudaError_t e;
-  if ((e = upload_tables_2d_f64(tab.data(), tabf.data(), &ioff[0][0], &gwd[0][0], &gwf[0][0])) != cudaSuccess) return cuda_fail(e, "tables");
-  if ((e = upload_tables_2d_f32(tab.data(), tabf.data(), &ioff[0][0], &gwd[0][0], &gwf[0][0])) != cudaSuccess) return cuda_fail(e, "tables");
-  if ((e = upload_tables_3d_f64(tab.data(), tabf.data(), &ioff[0][0], &gwd[0][0], &gwf[0][0])) != cudaSuccess) return cuda_fail(e, "tables");
-  if ((e = upload_tables_3d_f32(tab.data(), tabf.data(), &ioff[0][0], &gwd[0][0], &gwf[0][0])) != cudaSuccess) return cuda_fail(e, "tables");
+  for (int rule : {SIP_RULE_GAUSS, SIP_RULE_GLL}) {
+    std::vector<double> tab;
+    fill_tables(rule, tab);
+    std::vector<float> tabf = to_float(tab);
+    int ioff[kQMax + 1][kQMax + 1];
+    for (int q = 0; q <= kQMax; ++q)
+      for (int f = 0; f <= kQMax; ++f) ioff[q][f] = (q >= kQMin && f >= q) ? tab_I(q, f) : 0;
+    double gwd[kQMax + 1][kQMax] = {};
+    float gwf[kQMax + 1][kQMax] = {};
+    for (int q = 2; q <= kQMax; ++q) {
+      std::vector<double> gx, gw;
+      point_rule(rule, q, gx, gw);
+      for (int z = 0; z < q; ++z) { gwd[q][z] = gw[z]; gwf[q][z] = (float)gw[z]; }
+    }
+    for (int d = 0; d < 2; ++d)
+      for (int pr = 0; pr < 2; ++pr)
+        if ((e = kUpload[rule][d][pr](tab.data(), tabf.data(), &ioff[0][0], &gwd[0][0], &gwf[0][0])) != cudaSuccess)
+          return cuda_fail(e, "tables");
+  }
   // dynamic shared-memory limits, set once per device (never during a stream capture)
-  for (auto fn : {prepare_2d_f64, prepare_2d_f32, prepare_3d_f64, prepare_3d_f32, prepare_aux_2d, prepare_aux_3d})
+  for (int rule = 0; rule < 2; ++rule)
+    for (int d = 0; d < 2; ++d)
+      for (int pr = 0; pr < 2; ++pr)
+        if ((e = kPrepare[rule][d][pr]()) != cudaSuccess) return cuda_fail(e, "kernel attributes");
+  for (auto fn : {prepare_aux_2d, prepare_aux_3d, prepare_aux_gll_2d, prepare_aux_gll_3d})
     if ((e = fn()) != cudaSuccess) return cuda_fail(e, "kernel attributes");
   g_tables_uploaded[dev] = true;
   return SIP_OK;
@@ -167,12 +206,7 @@ int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_p
   if (ntile == 0) return SIP_OK;
   int occ = 0, nsm = 0;
   cudaError_t e;
-  if (p.dim == 2)
-    e = precision == SIP_FP64 ? occupancy_2d_f64(threads, s.smem_t, s.smem_m, &occ)
-                              : occupancy_2d_f32(threads, s.smem_t, s.smem_m, &occ);
-  else
-    e = precision == SIP_FP64 ? occupancy_3d_f64(threads, s.smem_t, s.smem_m, &occ)
-                              : occupancy_3d_f32(threads, s.smem_t, s.smem_m, &occ);
+  e = kOccupancy[p.opt.quad_rule][p.dim - 2][precision == SIP_FP64 ? 0 : 1](threads, s.smem_t, s.smem_m, &occ);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy");
   occ = std::max(1, occ);
@@ -289,16 +323,14 @@ int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t
     a.tiles = tiles_d;
     a.cta_off = cta_d;
     a.flists = flist_d;
-    e = h->plan.dim == 2 ? launch_apply_2d_f64(a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2)
-                         : launch_apply_3d_f64(a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2);
+    e = launch_apply(h->plan.opt.quad_rule, h->plan.dim, a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2);
   } else {
     float* tr = scratch_override ? (float*)scratch_override : (float*)h->trace_d;
     auto a = make_args<float>(h, (const float*)x, (float*)y, tr, nullptr, transpose);
     a.tiles = tiles_d;
     a.cta_off = cta_d;
     a.flists = flist_d;
-    e = h->plan.dim == 2 ? launch_apply_2d_f32(a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2)
-                         : launch_apply_3d_f32(a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2);
+    e = launch_apply(h->plan.opt.quad_rule, h->plan.dim, a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2);
   }
   if (e != cudaSuccess) return cuda_fail(e, "apply launch");
   h->timed_pending = h->timing;
@@ -341,6 +373,8 @@ void sip_options_default(sip_options* o) {
   o->checkpoint_every = 0;
   o->checkpoint_slots = 8;
   o->face_scheme = SIP_FACES_SHARED;
+  o->quad_rule = SIP_RULE_GAUSS;
+  o->force_interp = 0;
 }
 
 struct sip_plan {
@@ -442,15 +476,16 @@ int sip_create(const sip_mesh* mesh, const int32_t* orders, double lambda, const
   UP(h->gf.tau, tf);
   UP(h->xq, p.xq);
   if (h->p2p()) {
-    // Lagrange interpolation from every f-point Gauss rule to every t-point one:
-    // block (f, t) at (f (kQMax+1) + t) kQMax^2, entry [z][r] = l_{f,r}(xi_{t,z})
+    // Lagrange interpolation from every f-point rule to every t-point one (the
+    // handle's point rule): block (f, t) at (f (kQMax+1) + t) kQMax^2, entry
+    // [z][r] = l_{f,r}(xi_{t,z})
     const size_t blk = (size_t)kQMax * kQMax;
     std::vector<double> I((size_t)(kQMax + 1) * (kQMax + 1) * blk, 0.0);
     std::vector<double> xf, wf, xt, wt;
     for (int f = kQMin; f <= kQMax; ++f) {
-      gauss_legendre(f, xf, wf);
+      point_rule(p.opt.quad_rule, f, xf, wf);
       for (int t = kQMin; t <= kQMax; ++t) {
-        gauss_legendre(t, xt, wt);
+        point_rule(p.opt.quad_rule, t, xt, wt);
         double* B = &I[((size_t)f * (kQMax + 1) + t) * blk];
         for (int z = 0; z < t; ++z)
           for (int r = 0; r < f; ++r) B[z * kQMax + r] = lagrange(xf, r, xt[z]);

@@ -47,6 +47,17 @@ struct ApplyArgs {
 
 constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 
+// The point rule of this translation unit's tables and kernels (volume and face
+// points, P + 2 per direction): Gauss-Legendre unless the unit defines
+// SIP_TU_RULE before including this header.  With Gauss-Lobatto-Legendre points
+// the boundary points of the volume rule are the face points: traces are
+// gathered and fluxes scattered back (GathrInterp / ScatrInterp, Sec. 3.2).
+#ifndef SIP_TU_RULE
+#define SIP_TU_RULE SIP_RULE_GAUSS
+#endif
+constexpr int kTuRule = SIP_TU_RULE;
+constexpr bool kGatherScatter = kTuRule == SIP_RULE_GLL;
+
 // Programmatic dependent launch: a kernel launched with programmatic stream
 // serialisation (launch_dependent below) may start while the kernel before it
 // in the stream is still running.  Everything a kernel does before
@@ -81,7 +92,7 @@ inline cudaError_t launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, s
 static __constant__ double c_tab_d[kTabSize];
 static __constant__ float c_tab_f[kTabSize];
 static __constant__ int c_ioff[kQMax + 1][kQMax + 1];
-static __constant__ double c_gw_d[kQMax + 1][kQMax];  // Gauss weights of the q-point rule
+static __constant__ double c_gw_d[kQMax + 1][kQMax];  // weights of the q-point rule
 static __constant__ float c_gw_f[kQMax + 1][kQMax];
 
 template <typename T>

@@ -19,11 +19,12 @@ namespace sip {
 
 namespace {
 
-// Gauss rules of every size the plan uses, computed once
-struct GaussRules {
+// point rules (Gauss-Legendre or Gauss-Lobatto-Legendre) of every size the plan
+// uses, computed once
+struct PointRules {
   std::vector<double> x[kQMax + 1], w[kQMax + 1];
-  GaussRules() {
-    for (int q = 1; q <= kQMax; ++q) gauss_legendre(q, x[q], w[q]);
+  explicit PointRules(int rule) {
+    for (int q = 2; q <= kQMax; ++q) point_rule(rule, q, x[q], w[q]);
   }
 };
 
@@ -153,6 +154,15 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
   if (opt_in) opt = *opt_in; else sip_options_default(&opt);
   if (opt.qvol_extra != 2) { err = "only qvol_extra = 2 (Q = P + 2) is supported"; return SIP_ERR_ARG; }
   if (!(opt.tau_scale > 0.0)) { err = "tau_scale must be > 0"; return SIP_ERR_ARG; }
+  if (opt.quad_rule != SIP_RULE_GAUSS && opt.quad_rule != SIP_RULE_GLL) {
+    err = "quad_rule must be SIP_RULE_GAUSS or SIP_RULE_GLL";
+    return SIP_ERR_ARG;
+  }
+  if (opt.force_interp != 0 && opt.force_interp != 1) { err = "force_interp must be 0 or 1"; return SIP_ERR_ARG; }
+  if (opt.force_interp && opt.face_scheme != SIP_FACES_SHARED) {
+    err = "force_interp applies to the shared-rule face scheme only";
+    return SIP_ERR_ARG;
+  }
   if (opt.face_scheme != SIP_FACES_SHARED && opt.face_scheme != SIP_FACES_P2P) {
     err = "face_scheme must be SIP_FACES_SHARED or SIP_FACES_P2P";
     return SIP_ERR_ARG;
@@ -194,7 +204,7 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
         ev[(e * nc + c) * dim + i] = mesh->vert[mesh->elem_vert[e * nc + c] * dim + i];
 
   // ---- volume geometry (elements in parallel)
-  const GaussRules rules;
+  const PointRules rules(opt.quad_rule);
   const int nG = dim == 2 ? 4 : 7;
   p.vgoff.assign(E + 1, 0);
   for (int64_t e = 0; e < E; ++e) p.vgoff[e + 1] = p.vgoff[e] + (int64_t)nG * (p.quad_off[e + 1] - p.quad_off[e]);
@@ -586,6 +596,8 @@ void element_flops(const Plan& p, int64_t e, double& ft, double& fm) {
   // one sum-factorised interpolation GLL -> Gauss
   const double interp = 2.0 * (d == 2 ? (N * N * Q + N * Q * Q) : (N * N * N * Q + N * N * Q * Q + N * Q * Q * Q));
   const double grad = 2.0 * d * QV * Q;
+  const bool gll = p.opt.quad_rule == SIP_RULE_GLL;  // traces gathered, fluxes scattered
+  const bool force = p.opt.force_interp != 0;
   ft = interp;
   fm = grad + (2.0 * d * d + d + 2.0) * QV + grad + interp;  // gradient, pointwise, D^T, B^T
   for (int k = 0; k < 2 * d; ++k) {
@@ -595,15 +607,20 @@ void element_flops(const Plan& p, int64_t e, double& ft, double& fm) {
     const double np = d == 2 ? qf : qf * qf;
     const double nfl_t = orth ? 2.0 : 1.0 + d, nfl_m = orth ? 2.0 : 1.0 + d;
     double interp_t = 0.0, interp_m = 0.0;
-    if (sl.qf != (int)Q) {
+    if (sl.qf != (int)Q || force) {
       const double per_field = 2.0 * (d == 2 ? qf * Q : (Q * qf * Q + qf * qf * Q));
       interp_t = nfl_t * per_field;
       interp_m = nfl_m * per_field;
     }
-    ft += 2.0 * 2.0 * QF1 * Q + (orth ? 0.0 : 2.0 * (d - 1) * QF1 * Q) + interp_t + 2.0 * (orth ? 1.0 : d) * np;
-    // flux, projection, tangential transposed derivative on the face (P), and the
-    // lift l(+-1) P + l'(+-1) c_a t at every Gauss point
-    fm += 12.0 * np + (orth ? 1.0 : d) * np + interp_m + (orth ? 0.0 : 2.0 * (d - 1) * Q * QF1) + 2.0 * 2.0 * QV;
+    // value (extrapolated, or gathered from the boundary plane) and normal
+    // derivative at the element's own face points, tangential derivatives,
+    // interpolation to the shared rule, c . grad
+    ft += (gll ? 2.0 : 4.0) * QF1 * Q + (orth ? 0.0 : 2.0 * (d - 1) * QF1 * Q) + interp_t + 2.0 * (orth ? 1.0 : d) * np;
+    // flux and projection; then either the scatter into the boundary plane
+    // (1 + (1 or d) adds per point) or the tangential transposed derivative on the
+    // face (P) and the lift l(+-1) P + l'(+-1) c_a t at every volume point
+    fm += 12.0 * np + (orth ? 1.0 : d) * np + interp_m +
+          (gll ? (1.0 + (orth ? 1.0 : d)) * QF1 : (orth ? 0.0 : 2.0 * (d - 1) * Q * QF1) + 2.0 * 2.0 * QV);
     // point-to-point interpolation of this side's two trace scalars from its own
     // rule to the other side's oq-point rule
     const int oq = face_oq(sl.flags);
@@ -618,6 +635,7 @@ namespace {
 Tile make_tile(const Plan& p, int n, int64_t s0, int64_t s1, std::vector<uint16_t>& fl) {
   int qfm = n + 1;
   bool orth = true;
+  const bool force = p.opt.force_interp != 0;
   std::vector<uint16_t> conf, fine;
   for (int64_t s = s0; s < s1; ++s)
     for (int f = 0; f < 2 * p.dim; ++f) {
@@ -625,7 +643,7 @@ Tile make_tile(const Plan& p, int n, int64_t s0, int64_t s1, std::vector<uint16_
       qfm = std::max(qfm, (int)sl.qf);
       orth = orth && (sl.flags & kFaceOrth);
       const uint16_t e = (uint16_t)((s - s0) | (f << 5) | (sl.qf << 8));
-      (sl.qf == n + 1 ? conf : fine).push_back(e);
+      (sl.qf == n + 1 && !force ? conf : fine).push_back(e);
     }
   std::stable_sort(fine.begin(), fine.end(), [](uint16_t a, uint16_t b) { return fl_qf(a) < fl_qf(b); });
   std::vector<std::pair<int, int>> groups;  // (qf, count)
@@ -643,7 +661,7 @@ Tile make_tile(const Plan& p, int n, int64_t s0, int64_t s1, std::vector<uint16_
   }
   fl.insert(fl.end(), conf.begin(), conf.end());
   fl.insert(fl.end(), fine.begin(), fine.end());
-  const int flags = qfm | (qfm > n + 1 ? kTileFine : 0) | (orth ? kTileOrth : 0);
+  const int flags = qfm | (qfm > n + 1 || force ? kTileFine : 0) | (orth ? kTileOrth : 0) | (force ? kTileForce : 0);
   return Tile{n, (int32_t)s0, (int32_t)(s1 - s0), flags, off};
 }
 

@@ -10,18 +10,21 @@
 
 namespace sip {
 
-constexpr int kMaxOrder = SIP_MAX_ORDER;  // P in 1..8
+constexpr int kMaxOrder = SIP_MAX_ORDER;  // P in 1..10
 constexpr int kNMin = 2;                  // N = P + 1
-constexpr int kNMax = kMaxOrder + 1;      // 9
+constexpr int kNMax = kMaxOrder + 1;      // 11
 constexpr int kQMin = kNMin + 1;          // Q = P + 2 (qvol_extra = 2)
-constexpr int kQMax = kNMax + 1;          // 10; also the largest face rule
+constexpr int kQMax = kNMax + 1;          // 12; also the largest face rule
 
 // ---------------------------------------------------------------------------
 // 1D table layout, identical on host (filling) and device (__constant__ reads).
-//   B_N   [Q][N]  B[q][i]  = l^GLL_N,i (xi^G_Q,q)       (interpolation GLL -> Gauss)
-//   D_Q   [Q][Q]  D[q][r]  = l^G_Q,r ' (xi^G_Q,q)        (Gauss collocation derivative)
-//   L_Q   [4][Q]  rows l_r(-1), l_r(+1), l_r'(-1), l_r'(+1) of the Gauss-Q Lagrange basis
-//   I_Q,F [F][Q]  I[z][r]  = l^G_Q,r (xi^G_F,z), F in Q+1..kQMax (face rule interpolation)
+// One set per point rule R (Gauss-Legendre or Gauss-Lobatto-Legendre, chosen per
+// handle; each kernel translation unit holds the set of its rule):
+//   B_N   [Q][N]  B[q][i]  = l^GLL_N,i (xi^R_Q,q)       (interpolation nodes -> rule points)
+//   D_Q   [Q][Q]  D[q][r]  = l^R_Q,r ' (xi^R_Q,q)        (collocation derivative)
+//   L_Q   [4][Q]  rows l_r(-1), l_r(+1), l_r'(-1), l_r'(+1) of the rule's Lagrange basis
+//   I_Q,F [F][Q]  I[z][r]  = l^R_Q,r (xi^R_F,z), F in Q..kQMax (face rule interpolation;
+//                 F = Q is the identity, used when interpolation is forced on every face)
 // with Q = N + 1.
 // ---------------------------------------------------------------------------
 constexpr int tab_B(int N) {
@@ -45,7 +48,7 @@ constexpr int kTabLEnd = tab_L(kQMax + 1);
 constexpr int tab_I(int Q, int F) {
   int off = kTabLEnd;
   for (int q = kQMin; q <= kQMax; ++q)
-    for (int f = q + 1; f <= kQMax; ++f) {
+    for (int f = q; f <= kQMax; ++f) {
       if (q == Q && f == F) return off;
       off += f * q;
     }
@@ -59,13 +62,13 @@ constexpr int kTabSize = tab_I(kQMax + 1, kQMax + 2);
 //
 // Per-CTA table block for one order (N, Q = N + 1), laid out so that a warp whose
 // lanes compute consecutive outputs reads consecutive addresses:
-//   BT [N][Q]  B[q][i] at i*Q + q      forward interpolation GLL -> Gauss
+//   BT [N][Q]  B[q][i] at i*Q + q      forward interpolation nodes -> rule points
 //   BB [Q][N]  B[q][i] at q*N + i      transposed interpolation
 //   DT [Q][Q]  D[q][r] at r*Q + q      collocation derivative
 //   DD [Q][Q]  D[q][r] at q*Q + r      transposed derivative
 //   LL [4][Q]  l(-1), l(+1), l'(-1), l'(+1)
-//   for F = Q+1 .. kQMax:  IT_F [Q][F] (I[z][r] at r*F + z), II_F [F][Q] (I[z][r] at z*Q + r)
-//   for F = Q .. kQMax:    GW_F [F] Gauss weights
+//   for F = Q .. kQMax:    IT_F [Q][F] (I[z][r] at r*F + z), II_F [F][Q] (I[z][r] at z*Q + r)
+//   for F = Q .. kQMax:    GW_F [F] weights of the F-point rule
 // ---------------------------------------------------------------------------
 struct TabLayout {
   static constexpr int BT(int) { return 0; }
@@ -75,11 +78,11 @@ struct TabLayout {
   static constexpr int LL(int n) { return DD(n) + (n + 1) * (n + 1); }
   static constexpr int IT(int n, int f) {
     int o = LL(n) + 4 * (n + 1);
-    for (int g = n + 2; g < f; ++g) o += 2 * g * (n + 1);
+    for (int g = n + 1; g < f; ++g) o += 2 * g * (n + 1);
     return o;
   }
   static constexpr int II(int n, int f) { return IT(n, f) + f * (n + 1); }
-  // Gauss weights of the F-point rules, F = Q .. kQMax (affine geometry)
+  // weights of the F-point rules, F = Q .. kQMax (affine geometry)
   static constexpr int GW(int n, int f) {
     int o = IT(n, kQMax + 1);
     for (int g = n + 1; g < f; ++g) o += g;
@@ -129,15 +132,18 @@ struct FaceSlot {  // 8 bytes
 };
 
 constexpr int kTileQfMask = 0xff;  // bits 0-7: largest face rule of the tile
-constexpr int kTileFine = 1 << 8;  // some face of the tile has a finer rule than Q
+constexpr int kTileFine = 1 << 8;  // some face of the tile goes through the interpolation path
+                                   // (a finer shared rule than Q, or kTileForce)
 constexpr int kTileOrth = 1 << 9;  // every face of the tile is orthogonal (kFaceOrth)
+constexpr int kTileForce = 1 << 10;  // every face goes through the shared-rule interpolation
+                                     // path, also where its rule is the element's own
 constexpr int kMaxEpb = 32;        // elements per tile, at most
 
 struct Tile {
   int32_t n;       // nodes per direction (P + 1) of every element of the tile
   int32_t start;   // first index into the order-sorted element list
   int32_t count;   // elements in the tile
-  int32_t flags;   // kTileQfMask | kTileFine | kTileOrth
+  int32_t flags;   // kTileQfMask | kTileFine | kTileOrth | kTileForce
   int32_t flist;   // offset of the tile's face list (16-bit words)
 };
 
@@ -197,9 +203,11 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
 // host 1D rules (own implementation, FP64)
 void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w);
 void gauss_lobatto(int n, std::vector<double>& x, std::vector<double>& w);
+// the q-point rule of the volume and face points: SIP_RULE_GAUSS or SIP_RULE_GLL
+void point_rule(int rule, int q, std::vector<double>& x, std::vector<double>& w);
 double lagrange(const std::vector<double>& nodes, int j, double x);
 double lagrange_deriv(const std::vector<double>& nodes, int j, double x);
-void fill_tables(std::vector<double>& tab);
+void fill_tables(int rule, std::vector<double>& tab);
 
 // elements per tile for the apply kernels (host choice), per-element flops, and
 // the tiles with the CTA that runs each (tiles cta_off[b] .. cta_off[b+1]-1, one

@@ -24,6 +24,8 @@ namespace sip {
 
 cudaError_t launch_aux_2d(const AuxArgs&, int, size_t, cudaStream_t);
 cudaError_t launch_aux_3d(const AuxArgs&, int, size_t, cudaStream_t);
+cudaError_t launch_aux_gll_2d(const AuxArgs&, int, size_t, cudaStream_t);
+cudaError_t launch_aux_gll_3d(const AuxArgs&, int, size_t, cudaStream_t);
 
 namespace {
 
@@ -673,7 +675,9 @@ int launch_aux(sip_handle* h, AuxArgs& a, cudaStream_t s) {
   a.eaff = h->eaff;
   a.tiles = h->tiles_d[0];
   const int nt = (int)h->tiles_h[0].size();
-  cudaError_t e = h->plan.dim == 2 ? launch_aux_2d(a, nt, aux_smem(h), s) : launch_aux_3d(a, nt, aux_smem(h), s);
+  const bool gll = h->plan.opt.quad_rule == SIP_RULE_GLL;
+  cudaError_t e = h->plan.dim == 2 ? (gll ? launch_aux_gll_2d : launch_aux_2d)(a, nt, aux_smem(h), s)
+                                   : (gll ? launch_aux_gll_3d : launch_aux_3d)(a, nt, aux_smem(h), s);
   return e == cudaSuccess ? SIP_OK : cuda_fail(e, "aux kernel");
 }
 

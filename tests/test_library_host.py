@@ -103,13 +103,17 @@ def test_errors(pkg):
     with pytest.raises(pkg.SipError) as e:
         pkg.plan_info(2, m.vert, m.elem_vert, bad)
     assert e.value.code == 1
-    bad[3] = 9
+    bad[3] = pkg._lib.SIP_MAX_ORDER + 1
     with pytest.raises(pkg.SipError) as e:
         pkg.plan_info(2, m.vert, m.elem_vert, bad)
     assert e.value.code == 1
     with pytest.raises(pkg.SipError) as e:
         pkg.plan_info(2, m.vert, m.elem_vert, m.orders, pkg.options(qvol_extra=3))
     assert e.value.code == 1
+    for bad_opt in (dict(quad_rule=2), dict(force_interp=2), dict(force_interp=1, face_scheme=pkg.SIP_FACES_P2P)):
+        with pytest.raises(pkg.SipError) as e:
+            pkg.plan_info(2, m.vert, m.elem_vert, m.orders, pkg.options(**bad_opt))
+        assert e.value.code == 1
     # inverted element: swap two corners -> non-positive Jacobian
     ev = m.elem_vert.copy()
     ev[5, [0, 1]] = ev[5, [1, 0]]
