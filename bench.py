@@ -8,14 +8,16 @@ One step = one FP64 apply y = A x (trace kernel + main kernel) on inputs
 already resident in HBM; the L2 cache is flushed (a 256 MiB write) before every
 timed step, outside the timed events.  value = DOFs / second summed over
 ranks (GDoF/s).  The JSON line also carries the FP32 apply, the CG solves to a
-1e-10 relative residual (FP64 CG and FP32-apply CG in FP64 refinement), the
-roofline of the dominant kernel, the end-to-end number through the public API
-with host buffers, clocks sampled during the timed region and the oracle's
-throughput on the host cores.
+1e-10 relative residual (FP64 CG and FP32-apply CG in FP64 refinement) on this
+workload and on the 32^3 hex workload (the precision comparison), the
+rooflines of the main kernels against peaks measured on this GPU, the
+end-to-end number through the public API with host buffers, clocks sampled
+during the timed region and the oracle's throughput on all host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
-                  [--faces shared|p2p] [--tiling FILE | --save-tiling FILE] [--no-cg] [--no-cpu]
-  python bench.py --sweep orders|dofs      (hex throughput sweeps, one JSON line per mesh)
+                  [--faces shared|p2p] [--rule gauss|gll] [--force-interp]
+                  [--tiling FILE | --save-tiling FILE] [--no-cg] [--no-cpu] [--no-precision-config]
+  python bench.py --sweep orders|dofs|traces   (hex throughput sweeps, one JSON line per mesh)
 
 The batched 24^3 workload applies to (and solves for) its 32 right-hand sides in
 one call; its GDoF/s count every right-hand side's DOFs.
@@ -38,21 +40,17 @@ sys.path.insert(0, ROOT)
 import sip_inputs as si  # noqa: E402
 
 WORKLOAD = "c2_2d_64x64_jitter_p2to6"
+PRECISION_WORKLOAD = "c3_3d_32cube_p4"
 METRIC = "SIP apply GDoF/s (FP64 vs FP32-refined) and CG time to 1e-10 residual"
-
-# FP64 arithmetic peak of one GB300: 1.25 TFLOP/s dense (vendor figure; the FP64
-# units of this part are a small fraction of B200's).  FP32: 152 SMs x 128 lanes
-# x 2 flop x 2.07 GHz = 80.5 TFLOP/s.
-FP64_PEAK_TFLOPS = 1.25
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # right-hand sides per apply: the batched 24^3 workload applies to a batch of 32
 # N(0,1) vectors (seed 4) in one launch pair; the others to one vector (seed 0)
 NRHS = {"c4_3d_24cube_jitter_p2to7": 32}
 
-# DRAM bytes (read + write) per launch of the FP64 main kernel, from one ncu capture
-# of that workload with the current kernels (profiles/apply_<workload>.md)
-NCU_MAIN_TRAFFIC = {"c2_2d_64x64_jitter_p2to6": 10.929664e6, "c3_3d_32cube_p4": 183.096576e6 + 22.797568e6}
+# DRAM bytes (read + write) per launch of the FP64 main kernel, from one ncu
+# capture of that workload with the current kernels; None where no capture of
+# the current kernels exists
+NCU_MAIN_TRAFFIC: dict[str, float] = {}
 
 
 def peaks():
@@ -99,7 +97,7 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join("/tmp", f"sip_clocks_{os.getpid()}.csv")
+        self.path = os.path.join("/tmp", f"sip_clocks_{os.getpid()}_{id(self)}.csv")
 
     def __enter__(self):
         try:
@@ -144,44 +142,109 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_apply_rate(mesh, budget_s=12.0, seed=0, nrhs=1):
-    """The oracle as it stands on a bounded sample: rows of A for a prefix of a
-    shuffled element list, built from the local blocks and applied to x (nrhs
-    columns), until the time budget is spent.  Returns (DOF/s counted per
-    right-hand side, dofs done, elements, seconds, cores)."""
+# ---------------------------------------------------------------- oracle baseline on the host cores
+# The oracle as it stands (one process per host core, each building rows of A for
+# its share of the elements from the local blocks and applying them to x), on a
+# bounded sample of the workload; rate = DOF-columns of all workers / wall time.
+
+_ORC = {}
+
+
+def _oracle_worker_init(mesh, nrhs):
     from oracle import SipOracle
     orc = SipOracle(mesh, lam=mesh.lam)
     x = si.random_vector(orc.ndof, 0) if nrhs == 1 else si.random_rhs_batch(nrhs, orc.ndof, 4).T.copy()
-    order = np.random.default_rng(seed).permutation(mesh.n_elem)
+    _ORC["orc"], _ORC["x"], _ORC["nrhs"] = orc, x, nrhs
+
+
+def _oracle_worker_run(elems, budget_s):
+    orc, x, nrhs = _ORC["orc"], _ORC["x"], _ORC["nrhs"]
     t0 = time.perf_counter()
-    c0 = time.process_time()
     done, nel = 0, 0
-    for i in range(0, mesh.n_elem, 8):
-        els = order[i:i + 8]
-        R = orc.rows_for_elements(els)
+    for i in range(0, len(elems), 4):
+        R = orc.rows_for_elements(elems[i:i + 4])
         _ = R @ x
         done += R.shape[0] * nrhs
-        nel += len(els)
+        nel += len(elems[i:i + 4])
         if time.perf_counter() - t0 > budget_s:
             break
-    dt = time.perf_counter() - t0
-    cores = (time.process_time() - c0) / dt     # threads actually busy, on average
-    return done / dt, done, nel, dt, cores
+    return done, nel, time.perf_counter() - t0
+
+
+class OraclePool:
+    """One spawned worker process per host core (spawned, so that it is safe
+    after CUDA has been initialised), each holding the oracle of the workload."""
+
+    def __init__(self, mesh, nrhs, workers=None):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        self.workers = workers or len(os.sched_getaffinity(0))
+        self.mesh, self.nrhs = mesh, nrhs
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"          # one thread per worker process: the pool supplies the parallelism
+        try:
+            self.ex = cf.ProcessPoolExecutor(self.workers, mp_context=mp.get_context("spawn"),
+                                             initializer=_oracle_worker_init, initargs=(mesh, nrhs))
+            list(self.ex.map(_oracle_worker_run, [[0]] * self.workers, [0.0] * self.workers))  # warm the workers
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def run(self, budget_s, seed):
+        """One bounded run: every worker takes its share of a random element
+        order and works for about budget_s.  Returns (DOF-columns/s, DOF-columns,
+        elements, wall seconds)."""
+        order = np.random.default_rng(seed).permutation(self.mesh.n_elem).tolist()
+        shares = [order[w::self.workers] for w in range(self.workers)]
+        t0 = time.perf_counter()
+        res = list(self.ex.map(_oracle_worker_run, shares, [budget_s] * self.workers))
+        wall = time.perf_counter() - t0
+        done = sum(r[0] for r in res)
+        return done / wall, done, sum(r[1] for r in res), wall
+
+    def close(self):
+        self.ex.shutdown()
+
+
+def oracle_baseline(mesh, nrhs, runs=5, budget_s=3.0):
+    """Median of `runs` bounded runs of the oracle on all host cores."""
+    pool = OraclePool(mesh, nrhs)
+    try:
+        rs = [pool.run(budget_s, seed=k) for k in range(runs)]
+    finally:
+        pool.close()
+    med = sorted(rs, key=lambda r: r[0])[len(rs) // 2]
+    return {"value": med[0] / 1e9, "unit": "GDoF/s", "cores": pool.workers, "kind": "oracle",
+            "sample": f"median of {runs} runs; each: {pool.workers} worker processes (one per host core) build "
+                      f"rows of A from local blocks for their share of a random element order and apply them, "
+                      f"about {budget_s:.0f} s; median run {med[2]} of {mesh.n_elem} elements, "
+                      f"{med[1]} DOF-columns ({nrhs} right-hand side(s)) in {med[3]:.1f} s"}
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands, on all host cores (one
+    worker process per core), each step a bounded run on the same workload."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     mesh = si.workload(args.workload)
     nrhs = NRHS.get(args.workload, 1)
-    budget = max(1.0, 60.0 / max(1, args.steps + args.warmup))
-    rates = []
-    for k in range(args.warmup + args.steps):
-        r, done, nel, dt, cores = oracle_apply_rate(mesh, budget_s=budget, seed=k, nrhs=nrhs)
-        if k >= args.warmup:
-            rates.append((r, done, nel, dt, cores))
+    budget = max(1.0, min(6.0, 90.0 / max(1, args.steps + args.warmup)))
+    pool = OraclePool(mesh, nrhs)
+    try:
+        rates = []
+        for k in range(args.warmup + args.steps):
+            r = pool.run(budget, seed=k)
+            if k >= args.warmup:
+                rates.append(r)
+    finally:
+        pool.close()
     val = statistics.median(r[0] for r in rates) / 1e9
+    med = sorted(rates, key=lambda r: r[0])[len(rates) // 2]
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "GDoF/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup,
@@ -189,14 +252,53 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "nrhs": nrhs, "precision": "fp64", "l2": "n/a (host)"},
-        "cpu_baseline": {"value": val, "unit": "GDoF/s", "cores": round(max(r[4] for r in rates), 2),
-                         "kind": "oracle",
-                         "sample": f"rows of {rates[0][2]} elements ({rates[0][1]} DOF-columns) per step, "
-                                   f"{budget:.0f} s budget; cores = CPU time / wall time"},
+        "cpu_baseline": {"value": val, "unit": "GDoF/s", "cores": pool.workers, "kind": "oracle",
+                         "sample": f"per step: {pool.workers} worker processes (one per host core) build rows "
+                                   f"of A from local blocks for their share of a random element order and "
+                                   f"apply them for about {budget:.0f} s (median step: {med[2]} elements, "
+                                   f"{med[1]} DOF-columns)"},
         "e2e": {"value": val, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
+
+
+def _handle_options(g, args):
+    kw = {}
+    if args.faces == "p2p":
+        kw["face_scheme"] = g.SIP_FACES_P2P
+    if args.rule == "gll":
+        kw["quad_rule"] = g.SIP_RULE_GLL
+    if args.force_interp:
+        kw["force_interp"] = 1
+    return g.options(**kw) if kw else None
+
+
+def timed_cg(g, op, bvec, nrhs, rtol=1e-10):
+    """FP64 CG and FP32-apply CG in FP64 refinement to rtol: wall time of the
+    second of two identical solves (the first captures the CUDA graphs; a
+    32-column batch stops its first solve early, one batched solve being long)."""
+    import torch
+    warm_rtol = rtol if nrhs == 1 else 1e-4
+    res = {}
+    for name, mode in (("fp64", g.SIP_CG_FP64), ("fp32_refined", g.SIP_CG_FP32_REFINED)):
+        op.cg_solve(bvec, mode=mode, rtol=warm_rtol)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st = op.cg_solve(bvec, mode=mode, rtol=rtol)
+        torch.cuda.synchronize()
+        res[name] = {"seconds": time.perf_counter() - t0, "nrhs": nrhs, "iterations": st["iterations"],
+                     "refinements": st["refinements"], "rel_residual": st["rel_residual"]}
+    res["speedup_fp32_refined"] = res["fp64"]["seconds"] / res["fp32_refined"]["seconds"]
+    return res
+
+
+def manufactured_rhs(op, mesh):
+    """Load vector of the manufactured solution prod_k sin(pi x_k)."""
+    import torch
+    xq = op.quad_points()
+    f = (mesh.lam + mesh.dim * np.pi ** 2) * torch.prod(torch.sin(np.pi * xq), dim=1)
+    return op.iproduct(f.contiguous())
 
 
 def run_gb300(args):
@@ -215,7 +317,7 @@ def run_gb300(args):
 
     mesh = si.workload(args.workload)
     p2p = args.faces == "p2p"
-    op = g.SipOperator.from_mesh(mesh, opts=g.options(face_scheme=g.SIP_FACES_P2P) if p2p else None)
+    op = g.SipOperator.from_mesh(mesh, opts=_handle_options(g, args))
     n = op.ndof
     nrhs = NRHS.get(args.workload, 1)
     if p2p:
@@ -270,6 +372,12 @@ def run_gb300(args):
         ms = [a.elapsed_time(b) for a, b in evs]
         return ms, kt, wall
 
+    # ---- arithmetic peaks of this GPU, measured by the library (FMA chains on every SM)
+    with ClockSampler(local) as clk_peak:
+        fp64_peak = g.fp_peak(g.SIP_FP64, 1 << 14)
+        fp32_peak = g.fp_peak(g.SIP_FP32, 1 << 18)
+    clocks_peak = clk_peak.summary()
+
     # ---- headline: FP64 apply (the two kernels back to back, as the solver runs them)
     with ClockSampler(local) as clk:
         ms, _, wall = timed_applies(x, y, args.steps, args.warmup, label="timed_fp64")
@@ -286,7 +394,7 @@ def run_gb300(args):
     t32 = sum(ms32) / len(ms32) / 1e3
     _, kt32, _ = timed_applies(x32, y32, args.steps, 0, kernel_times=True, label="kernels_fp32")
 
-    # ---- roofline of the dominant kernel (the main kernel), FP64
+    # ---- rooflines of the dominant kernel (the main kernel)
     w64 = op.work_model(g.SIP_FP64)
     w32 = op.work_model(g.SIP_FP32)
     trace_ms = statistics.mean(a for a, _ in kt)
@@ -295,14 +403,27 @@ def run_gb300(args):
     trace32_ms = statistics.mean(a for a, _ in kt32)
     pk = peaks()
     ach = nrhs * w64["flops_main"] / (main_ms / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None if p2p else NCU_MAIN_TRAFFIC.get(args.workload),
-            "kernel": f"k_main<double,{mesh.dim},{'true' if p2p else 'false'}>",
-            "peak_src": "FP64 vendor figure 1.25 TFLOP/s (dense)",
+    apply_tf = nrhs * (w64["flops_main"] + w64["flops_trace"]) / t_step / 1e12
+    bytes64 = nrhs * (w64["bytes_x"] + w64["bytes_y"]) + w64["bytes_geometry"]
+    roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": ach / fp64_peak,
+            "traffic": None if (p2p or args.rule != "gauss" or args.force_interp) else NCU_MAIN_TRAFFIC.get(args.workload),
+            "kernel": f"k_main<double,{mesh.dim},{'true' if p2p else 'false'},{1 if args.rule == 'gll' else 0}>",
+            "peak_src": "measured (sip_fp_peak: FP64 FMA chains on every SM, CUDA events), of measured",
             "kernel_ms": main_ms, "trace_kernel_ms": trace_ms,
-            "hbm_frac": (nrhs * (w64["bytes_x"] + w64["bytes_y"] + w64["bytes_trace"]) + w64["bytes_geometry"])
-            / ((main_ms + trace_ms) / 1e3) / (pk["hbm_gbs"] * 1e9)}
+            "whole_apply": {"achieved": apply_tf, "frac": apply_tf / fp64_peak,
+                            "note": "trace + main flops of the work model / headline apply time"},
+            "hbm_frac": bytes64 / t_step / (pk["hbm_gbs"] * 1e9)}
     ach32 = nrhs * w32["flops_main"] / (main32_ms / 1e3) / 1e12
+    bytes32 = nrhs * (w32["bytes_x"] + w32["bytes_y"]) + w32["bytes_geometry"]
+    roof32 = {"bound": "hbm" if mesh.n_elem and nrhs == 1 and args.workload in ("c2_2d_64x64_jitter_p2to6",)
+              else "alu",
+              "hbm": {"achieved": bytes32 / t32 / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                      "frac": bytes32 / t32 / (pk["hbm_gbs"] * 1e9),
+                      "bytes": bytes32, "note": "x, y and volume / face geometry per apply / apply time"},
+              "alu": {"achieved": ach32, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach32 / fp32_peak,
+                      "kernel": "main", "kernel_ms": main32_ms},
+              "peak_src": "HBM: MEASURED_PEAKS.json; FP32: sip_fp_peak, of measured"}
 
     # ---- end to end through the C ABI with host buffers: sip_apply_host copies x
     # in, applies and copies y out, all inside the timed region
@@ -323,37 +444,29 @@ def run_gb300(args):
     barrier()
     e2e_val = world * nrhs * n / (statistics.mean(e2e_ms) / 1e3) / 1e9
 
-    # ---- CG solves to 1e-10 (manufactured right-hand side)
+    # ---- CG solves to 1e-10 (manufactured right-hand side, or the 32 N(0,1) columns)
     cg = None
     if not args.no_cg:
-        if nrhs == 1:
-            # manufactured right-hand side of sin(pi x) sin(pi y) (sin(pi z))
-            xq = op.quad_points()
-            f = (mesh.lam + mesh.dim * np.pi ** 2) * torch.prod(torch.sin(np.pi * xq), dim=1)
-            bvec = op.iproduct(f.contiguous())
-        else:
-            bvec = x   # the batch of N(0,1) right-hand sides
-        # warm-up solve (graph capture); the 32-column batch stops it early, since
-        # one full batched solve takes about a minute
-        warm_rtol = 1e-10 if nrhs == 1 else 1e-4
-        res = {}
-        for name, mode in (("fp64", g.SIP_CG_FP64), ("fp32_refined", g.SIP_CG_FP32_REFINED)):
-            op.cg_solve(bvec, mode=mode, rtol=warm_rtol)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            _, st = op.cg_solve(bvec, mode=mode, rtol=1e-10)
-            torch.cuda.synchronize()
-            res[name] = {"seconds": time.perf_counter() - t0, "nrhs": nrhs, "iterations": st["iterations"],
-                         "refinements": st["refinements"], "rel_residual": st["rel_residual"]}
-        res["speedup_fp32_refined"] = res["fp64"]["seconds"] / res["fp32_refined"]["seconds"]
-        cg = res
+        bvec = manufactured_rhs(op, mesh) if nrhs == 1 else x
+        cg = timed_cg(g, op, bvec, nrhs)
+    del op
+    torch.cuda.empty_cache()
+
+    # ---- the precision comparison on the 32^3 hex workload: FP64 CG against
+    # FP32-apply CG in FP64 refinement, both to a 1e-10 relative residual
+    prec_cfg = None
+    if rank == 0 and world == 1 and not args.no_precision_config and not p2p and args.workload != PRECISION_WORKLOAD:
+        m3 = si.workload(PRECISION_WORKLOAD)
+        op3 = g.SipOperator.from_mesh(m3, opts=_handle_options(g, args))
+        for p in (g.SIP_FP64, g.SIP_FP32):
+            op3.autotune(p, reps=3)
+        prec_cfg = {"workload": PRECISION_WORKLOAD, "ndof": op3.ndof, **timed_cg(g, op3, manufactured_rhs(op3, m3), 1)}
+        del op3
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        r, done, nel, dt, cores = oracle_apply_rate(mesh, budget_s=args.cpu_budget, nrhs=nrhs)
-        cpu = {"value": r / 1e9, "unit": "GDoF/s", "cores": round(cores, 2), "kind": "oracle",
-               "sample": f"rows of {nel} of {mesh.n_elem} elements ({done} DOF-columns, {nrhs} right-hand "
-                         f"side(s)) built from local blocks and applied, {dt:.1f} s; cores = CPU time / wall time"}
+        cpu = oracle_baseline(mesh, nrhs)
 
     if rank == 0:
         line = {
@@ -361,15 +474,16 @@ def run_gb300(args):
             "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "ndof": n, "nrhs": nrhs, "n_elem": mesh.n_elem, "precision": "fp64",
-                       "faces": args.faces,
+                       "faces": args.faces, "rule": args.rule, "force_interp": bool(args.force_interp),
                        "l2": "flushed before every step (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single",
                        "tiling": tiling},
             "fp32_apply": {"value": world * nrhs * n / t32 / 1e9, "unit": "GDoF/s", "ms_per_step": t32 * 1e3,
-                           "main_kernel_ms": main32_ms, "trace_kernel_ms": trace32_ms,
-                           "main_tflops": ach32, "main_frac_of_fp32_peak": ach32 / FP32_PEAK_TFLOPS},
+                           "main_kernel_ms": main32_ms, "trace_kernel_ms": trace32_ms, "roofline": roof32},
             "cg": cg,
+            "precision_config": prec_cfg,
             "roofline": roof,
+            "peaks_measured": {"fp64_tflops": fp64_peak, "fp32_tflops": fp32_peak, "clocks": clocks_peak},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "GDoF/s", "h2d_bytes_per_step": 8 * nrhs * n,
                     "d2h_bytes_per_step": 8 * nrhs * n},
@@ -384,58 +498,93 @@ def run_gb300(args):
     return 0
 
 
-def run_sweep(args):
-    """Throughput sweeps shaped like the paper's CPU measurements (Sec. 5.2):
-    uniform hex meshes of [0,1]^3 (affine elements, one order each), FP64 and
-    FP32 applies, one JSON line per mesh.
+def _time_apply(op, prec, steps, warmup, flush, g):
+    """Median apply time (CUDA events, L2 flushed before every apply) and the
+    per-kernel medians of a second pass with the library's events."""
+    import torch
+    stream = torch.cuda.current_stream()
+    dt = torch.float64 if prec == g.SIP_FP64 else torch.float32
+    x = torch.tensor(si.random_vector(op.ndof, 0), device="cuda", dtype=dt)
+    y = torch.empty_like(x)
+    for _ in range(warmup):
+        op.apply(x, out=y)
+    ms = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        op.apply(x, out=y)
+        b.record(stream)
+        ms.append((a, b))
+    torch.cuda.synchronize()
+    t = statistics.median(a.elapsed_time(b) for a, b in ms) / 1e3
+    op.set_timing(True)
+    kt = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        op.apply(x, out=y)
+        kt.append(op.last_kernel_ms())
+    op.set_timing(False)
+    return t, statistics.median(m for _, m in kt), statistics.median(tr for tr, _ in kt)
 
-    orders: P = 1..8 at about 1.1e7 DOFs each (the paper's sub-operator study
-            uses 1.1e7 DOFs per order);
-    dofs:   P = 4 from about 1e4 to 1e8 DOFs (the paper's size sweep)."""
+
+def run_sweep(args):
+    """Throughput sweeps shaped like the paper's CPU measurements (Sec. 5.2),
+    on uniform hex meshes of [0,1]^3 (affine elements, one order each), one JSON
+    line per mesh:
+
+    orders: P = 1..10 at about 1.1e7 DOFs each (the paper's sub-operator study
+            uses 1.1e7 DOFs per order), FP64 and FP32;
+    dofs:   P = 4 from about 1e4 to 1e8 DOFs (the paper's size sweep), FP64 and FP32;
+    traces: the trace schemes on the same mesh (Sec. 5.2's forced-interpolation
+            comparison): Gauss points (traces evaluated from the element),
+            Gauss-Lobatto points (traces gathered, fluxes scattered), and each
+            with interpolation forced on every face; P = 2, 4, 6 at about 4e6
+            DOFs and the 64x64 jittered quads, FP64 and FP32."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     import paper_2504_03573_gb300 as g
+    fp64_peak = g.fp_peak(g.SIP_FP64, 1 << 14)
+    fp32_peak = g.fp_peak(g.SIP_FP32, 1 << 18)
+    gauss = dict()
+    variants = {"gauss": gauss}
     if args.sweep == "orders":
-        cases = [(p, max(2, round(1.1e7 ** (1 / 3) / (p + 1)))) for p in range(1, 9)]
-    else:
+        cases = [(p, max(2, round(1.1e7 ** (1 / 3) / (p + 1)))) for p in range(1, 11)]
+    elif args.sweep == "dofs":
         cases = [(4, n) for n in (4, 8, 16, 24, 32, 48, 64, 90)]
+    else:
+        cases = [(p, round(4e6 ** (1 / 3) / (p + 1))) for p in (2, 4, 6)] + [("c2", None)]
+        variants = {"gauss": gauss, "gauss_forced": dict(force_interp=1),
+                    "gll_gather": dict(quad_rule=g.SIP_RULE_GLL),
+                    "gll_forced": dict(quad_rule=g.SIP_RULE_GLL, force_interp=1)}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
     for p, n in cases:
-        mesh = si.structured_mesh(3, n, order=p)
-        op = g.SipOperator.from_mesh(mesh)
-        line = {"sweep": args.sweep, "order": p, "n": n, "n_elem": mesh.n_elem, "ndof": op.ndof,
-                "unit": "GDoF/s", "l2": "flushed before every step (256 MiB write)"}
-        for name, prec, dt in (("fp64", g.SIP_FP64, torch.float64), ("fp32", g.SIP_FP32, torch.float32)):
-            op.autotune(prec, reps=3)
-            x = torch.tensor(si.random_vector(op.ndof, 0), device="cuda", dtype=dt)
-            y = torch.empty_like(x)
-            for _ in range(args.warmup):
-                op.apply(x, out=y)
-            op.set_timing(True)
-            ms, kt = [], []
-            for i in range(args.steps):
-                flush.fill_(float(i))
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                op.apply(x, out=y)
-                b.record(stream)
-                kt.append(op.last_kernel_ms())
-                ms.append((a, b))
-            torch.cuda.synchronize()
-            op.set_timing(False)
-            t = statistics.median(a.elapsed_time(b) for a, b in ms) / 1e3
-            main_ms = statistics.median(m for _, m in kt)
-            w = op.work_model(prec)
-            line[name] = {"value": op.ndof / t / 1e9, "ms_per_apply": t * 1e3, "main_kernel_ms": main_ms,
-                          "trace_kernel_ms": statistics.median(tr for tr, _ in kt),
-                          "main_tflops": w["flops_main"] / (main_ms / 1e3) / 1e12}
-        line["fp64"]["main_frac_of_fp64_peak"] = line["fp64"]["main_tflops"] / FP64_PEAK_TFLOPS
-        line["fp32"]["main_frac_of_fp32_peak"] = line["fp32"]["main_tflops"] / FP32_PEAK_TFLOPS
+        mesh = si.workload(WORKLOAD) if p == "c2" else si.structured_mesh(3, n, order=p)
+        line = {"sweep": args.sweep, "order": p, "n": n, "n_elem": mesh.n_elem,
+                "unit": "GDoF/s", "l2": "flushed before every step (256 MiB write)",
+                "peaks_measured_tflops": {"fp64": fp64_peak, "fp32": fp32_peak}}
+        for vname, kw in variants.items():
+            op = g.SipOperator.from_mesh(mesh, opts=g.options(**kw) if kw else None)
+            line["ndof"] = op.ndof
+            res = {}
+            for name, prec, peak in (("fp64", g.SIP_FP64, fp64_peak), ("fp32", g.SIP_FP32, fp32_peak)):
+                op.autotune(prec, reps=3)
+                t, main_ms, trace_ms = _time_apply(op, prec, args.steps, args.warmup, flush, g)
+                w = op.work_model(prec)
+                res[name] = {"value": op.ndof / t / 1e9, "ms_per_apply": t * 1e3, "main_kernel_ms": main_ms,
+                             "trace_kernel_ms": trace_ms,
+                             "main_tflops": w["flops_main"] / (main_ms / 1e3) / 1e12,
+                             "apply_tflops": (w["flops_main"] + w["flops_trace"]) / t / 1e12}
+                res[name]["main_frac_of_peak"] = res[name]["main_tflops"] / peak
+                res[name]["apply_frac_of_peak"] = res[name]["apply_tflops"] / peak
+            if len(variants) == 1:
+                line.update(res)
+            else:
+                line[vname] = res
+            del op
+            torch.cuda.empty_cache()
         print(json.dumps(line), flush=True)
-        del op
-        torch.cuda.empty_cache()
     return 0
 
 
@@ -451,11 +600,17 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--tiling", default=None, help="install the schedule saved by --save-tiling instead of tuning")
     ap.add_argument("--save-tiling", default=None, help="write the schedule in use to this JSON file")
-    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-precision-config", action="store_true",
+                    help="skip the FP64 vs FP32-refined CG comparison on the 32^3 hex workload")
+    ap.add_argument("--rule", default="gauss", choices=["gauss", "gll"],
+                    help="volume and face points: Gauss-Legendre (traces evaluated from the element) or "
+                         "Gauss-Lobatto-Legendre (traces gathered, fluxes scattered)")
+    ap.add_argument("--force-interp", action="store_true",
+                    help="interpolate to the shared rule on every face, also conforming ones")
     ap.add_argument("--faces", default="shared", choices=["shared", "p2p"],
                     help="interior-face flux: one shared rule per face (the method) or point-to-point "
                          "interpolation between the two sides' own rules (the comparison variant)")
-    ap.add_argument("--sweep", default=None, choices=["orders", "dofs"],
+    ap.add_argument("--sweep", default=None, choices=["orders", "dofs", "traces"],
                     help="throughput sweep on uniform hex meshes instead of the benchmark line")
     args = ap.parse_args()
     if args.warmup < 3:

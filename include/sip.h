@@ -333,6 +333,16 @@ int  sip_last_kernel_ms(sip_handle* h, float* trace_ms, float* main_ms);
 int  sip_apply_static_scratch(sip_handle* h, int precision, const void* x_dev, void* y_dev, int nrhs,
                               void* stream);
 
+/* Measured arithmetic peak of the current device's FP64 (precision SIP_FP64) or
+ * FP32 (SIP_FP32) units in TFLOP/s: 8 independent FMA chains of `iters` steps in
+ * every thread of as many 256-thread CTAs as fit on the device at once, timed
+ * with CUDA events on `stream` (best of three launches after one warm-up; an
+ * FMA counts 2 flops).  The denominator of the apply's roofline: the paper
+ * states its CPU efficiency against the machine's peak (Sec. 5.2), this measures
+ * the GPU's.  Allocates a small device buffer and synchronises the stream.
+ * Errors: SIP_ERR_ARG (null output, iters < 1, precision), SIP_ERR_CUDA. */
+int  sip_fp_peak(int precision, int iters, void* stream, double* tflops_out);
+
 const char* sip_last_error(void);
 
 #ifdef __cplusplus

@@ -18,7 +18,7 @@ from ._lib import (SIP_CG_FP32_REFINED, SIP_CG_FP64, SIP_FACES_P2P, SIP_FACES_SH
                    SIP_RULE_GAUSS, SIP_RULE_GLL, SipError, check, lib,
                    sip_mesh, sip_options, sip_plan_info, sip_stats, sip_work)
 
-__all__ = ["SipOperator", "plan_info", "options", "SipError", "SIP_FP64", "SIP_FP32", "SIP_CG_FP64",
+__all__ = ["SipOperator", "plan_info", "options", "fp_peak", "SipError", "SIP_FP64", "SIP_FP32", "SIP_CG_FP64",
            "SIP_CG_FP32_REFINED", "SIP_FACES_SHARED", "SIP_FACES_P2P", "SIP_RULE_GAUSS", "SIP_RULE_GLL",
            "SipApplyFn", "SipSolveFn", "lib"]
 
@@ -31,6 +31,14 @@ def options(**kw) -> sip_options:
             raise KeyError(k)
         setattr(o, k, v)
     return o
+
+
+def fp_peak(precision=SIP_FP64, iters=1 << 14) -> float:
+    """Measured FP64 / FP32 arithmetic peak of the current GPU, TFLOP/s
+    (sip_fp_peak: FMA chains on every SM, CUDA-event timed)."""
+    out = C.c_double()
+    check(lib.sip_fp_peak(int(precision), int(iters), _stream(), C.byref(out)))
+    return float(out.value)
 
 
 def _mesh_struct(dim, vert, elem_vert):

@@ -129,6 +129,7 @@ SIGNATURES = {
     "sip_get_tiling": (_I, [_H, _I, C.POINTER(sip_tiling)]),
     "sip_set_tiling": (_I, [_H, _I, C.POINTER(sip_tiling)]),
     "sip_apply_static_scratch": (_I, [_H, _I, _P, _P, _I, _P]),
+    "sip_fp_peak": (_I, [_I, _I, _P, C.POINTER(_D)]),
     "sip_last_error": (C.c_char_p, []),
 }
 

@@ -76,9 +76,11 @@ struct Shape {
   static constexpr int PER_MAIN = per_elem_main(DIM, N);
 };
 
-// Copy this order's 1D tables from __constant__ into the CTA's table block.
+// Copy this order's 1D tables from __constant__ into the CTA's table block: the
+// face-rule interpolations up to the finest rule fmax of the CTA's tiles (from
+// the identity F = Q on when interpolation is forced), the weights up to fmax.
 template <typename T, int N>
-__device__ __forceinline__ void load_tables(T* tb) {
+__device__ __forceinline__ void load_tables(T* tb, int fmax, bool force) {
   constexpr int Q = N + 1;
   for (int w = threadIdx.x; w < N * Q; w += blockDim.x) {
     const int q = w / N, i = w - q * N;  // B[q][i]
@@ -93,7 +95,7 @@ __device__ __forceinline__ void load_tables(T* tb) {
     tb[TabLayout::DD(N) + q * Q + r] = v;
   }
   for (int w = threadIdx.x; w < 4 * Q; w += blockDim.x) tb[TabLayout::LL(N) + w] = ctab<T>(tab_L(Q) + w);
-  for (int f = Q; f <= kQMax; ++f) {
+  for (int f = force ? Q : Q + 1; f <= fmax; ++f) {
     const int io = c_ioff[Q][f];
     for (int w = threadIdx.x; w < f * Q; w += blockDim.x) {
       const int z = w / Q, r = w - z * Q;  // I[z][r]
@@ -102,7 +104,7 @@ __device__ __forceinline__ void load_tables(T* tb) {
       tb[TabLayout::II(N, f) + z * Q + r] = v;
     }
   }
-  for (int f = Q; f <= kQMax; ++f)
+  for (int f = Q; f <= fmax; ++f)
     for (int z = threadIdx.x; z < f; z += blockDim.x) tb[TabLayout::GW(N, f) + z] = cgw<T>(f, z);
   __syncthreads();
 }
@@ -183,35 +185,43 @@ template <int Q>
 __device__ __forceinline__ bool own_rule(int qf, bool force) { return qf == Q && !force; }
 
 // ============================================================ trace kernel
-// The tile's copy of its face slots, element ids, affine flags and face list in
-// shared memory (meta_bytes(DIM, count, list length), after the table block).
+// The tile's element and slot descriptors in shared memory (meta_bytes(DIM),
+// after the table block): element ids, DOF / geometry / volume-point offsets,
+// face slots with their trace and geometry offsets and penalties.
 template <int DIM>
 struct TileMeta {
-  FaceSlot slot_[kMaxEpb * 6];
-  int32_t eid_[kMaxEpb];
-  int8_t aff_[kMaxEpb];
-  __device__ __forceinline__ const FaceSlot& slot(int i) const { return slot_[i]; }
-  __device__ __forceinline__ FaceSlot& slot(int i) { return slot_[i]; }
-  __device__ __forceinline__ int eid(int el) const { return eid_[el]; }
-  __device__ __forceinline__ int aff(int el) const { return aff_[el]; }
+  ElemDesc e_[kMaxEpb];
+  SlotDesc s_[kMaxEpb * 2 * DIM];
+  __device__ __forceinline__ const FaceSlot& slot(int i) const { return s_[i].slot; }
+  __device__ __forceinline__ int64_t troff(int i) const { return s_[i].troff; }
+  __device__ __forceinline__ int64_t goff(int i) const { return s_[i].goff; }
+  __device__ __forceinline__ double tau(int i) const { return s_[i].tau; }
+  __device__ __forceinline__ int eid(int el) const { return e_[el].eid; }
+  __device__ __forceinline__ int aff(int el) const { return e_[el].aff; }
+  __device__ __forceinline__ int64_t dof(int el) const { return e_[el].dof_off; }
+  __device__ __forceinline__ int64_t vgo(int el) const { return e_[el].vgoff; }
+  __device__ __forceinline__ int64_t qoff(int el) const { return e_[el].quad_off; }
 };
-static_assert(sizeof(TileMeta<3>) <= kMetaBytes, "tile meta exceeds its shared-memory block");
+static_assert(sizeof(TileMeta<2>) <= meta_bytes(2) && sizeof(TileMeta<3>) <= meta_bytes(3),
+              "tile meta exceeds its shared-memory block");
 
-// list: where to copy the tile's face list (nullptr: not needed; copied only
-// where some face has a finer rule)
+// Copy the tile's descriptors (two contiguous blocks, 16-byte vector loads) and,
+// where the tile has faces on the interpolation path and `list` is given, its
+// face list.
 template <int DIM>
-__device__ __forceinline__ void load_meta(const int32_t* elist, const FaceSlot* slots, const int8_t* eaff,
-                                          const uint16_t* flists, const Tile& t, TileMeta<DIM>* mt, uint16_t* list) {
+__device__ __forceinline__ void load_meta(const ElemDesc* desc_e, const SlotDesc* desc_s, const uint16_t* flists,
+                                          const Tile& t, TileMeta<DIM>* mt, uint16_t* list) {
   const uint16_t* fl = flists + t.flist;
   const int len = list && (t.flags & kTileFine) ? 3 + 2 * fl[2] + fl[0] + fl[1] : 0;
-  for (int w = threadIdx.x; w < t.count * 2 * DIM; w += blockDim.x) {
-    const int el = w / (2 * DIM), k = w - el * 2 * DIM;
-    const int e = elist[t.start + el];
-    if (k == 0) {
-      mt->eid_[el] = e;
-      mt->aff_[el] = eaff[e];
-    }
-    mt->slot_[el * 2 * DIM + k] = slots[(int64_t)e * 2 * DIM + k];
+  constexpr int VE = sizeof(ElemDesc) / 16, VS = sizeof(SlotDesc) / 16;
+  const uint4* ge = reinterpret_cast<const uint4*>(desc_e + t.start);
+  const uint4* gs = reinterpret_cast<const uint4*>(desc_s + (int64_t)t.start * 2 * DIM);
+  uint4* se = reinterpret_cast<uint4*>(mt->e_);
+  uint4* ss = reinterpret_cast<uint4*>(mt->s_);
+  const int ne = t.count * VE, ns = t.count * 2 * DIM * VS;
+  for (int w = threadIdx.x; w < ne + ns; w += blockDim.x) {
+    if (w < ne) se[w] = ge[w];
+    else ss[w - ne] = gs[w - ne];
   }
   for (int w = threadIdx.x; w < len; w += blockDim.x) list[w] = fl[w];
 }
@@ -287,9 +297,9 @@ struct FaceGeoP2P {
 };
 // npm: points of the minus side's own rule
 template <typename T, int DIM>
-__device__ __forceinline__ FaceGeoP2P<T> face_geo_p2p(const ApplyArgs<T>& a, const FaceSlot& sl, int npts, int npm,
-                                                      int zc, T w) {
-  const T* g = a.fgeo + a.f_goff[sl.face];
+__device__ __forceinline__ FaceGeoP2P<T> face_geo_p2p(const ApplyArgs<T>& a, const FaceSlot& sl, int64_t goff, int npts,
+                                                      int npm, int zc, T w) {
+  const T* g = a.fgeo + goff;
   const bool aff = (sl.flags & kFaceAffine) != 0;
   if (aff) return FaceGeoP2P<T>{g, g, npts, zc, sl.side, DIM, true, w};
   if (sl.flags & kFaceBnd) return FaceGeoP2P<T>{g, g + npts, npts, zc, 0, DIM, false, w};
@@ -320,13 +330,14 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
   // normal derivative c . grad_ref u from (u, du/dn_ref, tangential derivatives)
   // and store both at canonical point zc
   auto emit_vals = [&](int el, int k, int z0, int z1, T uv, T dn, T d0, T d1) {
-    const FaceSlot sl = mt->slot(el * 2 * DIM + k);
+    const int si = el * 2 * DIM + k;
+    const FaceSlot sl = mt->slot(si);
     const int qf = sl.qf, ax = k >> 1;
     const int npts = DIM == 2 ? qf : qf * qf;
     const int zc = canon(DIM, sl.side, sl.orient, qf, z0, z1);
     if constexpr (P2P) {
       const int npm = face_npts<DIM>(sl.side ? face_oq(sl.flags) : qf);
-      const FaceGeoP2P<T> fg = face_geo_p2p<T, DIM>(a, sl, npts, npm, zc, T(0));
+      const FaceGeoP2P<T> fg = face_geo_p2p<T, DIM>(a, sl, mt->goff(si), npts, npm, zc, T(0));
       T g = fg.c(ax) * dn;
       if (!orth) {
         int t0, t1;
@@ -334,11 +345,11 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
         g += fg.c(t0) * d0;
         if constexpr (DIM == 3) g += fg.c(t1) * d1;
       }
-      T* tr = a.trace + rhs * a.trace_stride + 4 * a.f_troff[sl.face] + p2p_own_block(sl.side, npm) + zc;
+      T* tr = a.trace + rhs * a.trace_stride + 4 * mt->troff(si) + p2p_own_block(sl.side, npm) + zc;
       tr[0] = uv;
       tr[npts] = g;
     } else {
-      FaceGeo<T> fg{a.fgeo + a.f_goff[sl.face], npts, zc, sl.side, DIM, (sl.flags & kFaceAffine) != 0, T(0)};
+      FaceGeo<T> fg{a.fgeo + mt->goff(si), npts, zc, sl.side, DIM, (sl.flags & kFaceAffine) != 0, T(0)};
       T g = fg.c(ax) * dn;
       if (!orth) {
         int t0, t1;
@@ -346,7 +357,7 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
         g += fg.c(t0) * d0;
         if constexpr (DIM == 3) g += fg.c(t1) * d1;
       }
-      T* tr = a.trace + rhs * a.trace_stride + 4 * a.f_troff[sl.face] + (int64_t)(2 * sl.side) * npts + zc;
+      T* tr = a.trace + rhs * a.trace_stride + 4 * mt->troff(si) + (int64_t)(2 * sl.side) * npts + zc;
       tr[0] = uv;
       tr[npts] = g;
     }
@@ -519,7 +530,7 @@ __device__ __forceinline__ void p2p_send(const ApplyArgs<T>& a, const Tile& t, c
     const int npo = face_npts<DIM>(oq);
     if ((sl.flags & kFaceBnd) || oq == Q || z >= npo) continue;
     const int npm = sl.side ? npo : NP;
-    T* base = a.trace + rhs * a.trace_stride + 4 * a.f_troff[sl.face];
+    T* base = a.trace + rhs * a.trace_stride + 4 * mt->troff(el * 2 * DIM + k);
     const T* src = base + (int64_t)sl.side * 4 * npm;                // own [u][g], Q points
     T* dst = base + (sl.side ? 0 : (int64_t)4 * npm) + 2 * npo;      // the other side's [u~][g~]
     const T* I = a.p2p_I + (Q * (kQMax + 1) + oq) * (kQMax * kQMax);  // Q-point rule -> oq-point rule
@@ -557,7 +568,7 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
   using S = Shape<DIM, N>;
   constexpr int PER = S::PER_TRACE;
   const int ne = t.count;
-  load_meta<DIM>(a.elist, a.slots, a.eaff, a.flists, t, mt, nullptr);
+  load_meta<DIM>(a.desc_e, a.desc_s, a.flists, t, mt, nullptr);
   __syncthreads();
   // one output per thread (2D, and FP64 in 3D: more parallel work for the narrow
   // FP64 pipe) or one line per thread with the matrices as constant-bank operands
@@ -569,7 +580,7 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
     const T* BT = tb + TabLayout::BT(N);
     T* bA = sm;
     T* bB = sm + S::QV;
-    auto gx = [&](int el) { return a.x + rhs * a.ndof + a.dof_off[mt->eid(el)]; };
+    auto gx = [&](int el) { return a.x + rhs * a.ndof + mt->dof(el); };
     if constexpr (DIM == 2) {
       cpt_io<T, N, N, 1, 0, Q, false>(gx, [&](int el) { return bB + el * PER; }, ne, BT);
       __syncthreads();
@@ -588,7 +599,7 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
   } else {
     for (int w = threadIdx.x; w < ne * S::NV; w += blockDim.x) {
       const int el = w / S::NV, i = w - el * S::NV;
-      sm[el * PER + i] = a.x[rhs * a.ndof + a.dof_off[mt->eid(el)] + i];
+      sm[el * PER + i] = a.x[rhs * a.ndof + mt->dof(el) + i];
     }
     __syncthreads();
     U = to_gauss<T, DIM, N>(sm, sm + S::QV, PER, ne);
@@ -596,7 +607,7 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
   if (a.ug) {
     for (int w = threadIdx.x; w < ne * S::QV; w += blockDim.x) {
       const int el = w / S::QV, q = w - el * S::QV;
-      a.ug[rhs * a.nquad + a.quad_off[mt->eid(el)] + q] = U[el * PER + q];
+      a.ug[rhs * a.nquad + mt->qoff(el) + q] = U[el * PER + q];
     }
   }
   trace_all_faces<T, DIM, N, P2P>(a, t, mt, rhs, tb, sm, U);
@@ -618,18 +629,19 @@ __device__ __forceinline__ void face_flux(const ApplyArgs<T>& a, const TileMeta<
     face_flux_p2p<T, DIM, N>(a, mt, rhs, tb, orth, el, k, z0, z1, dst, fs);
     return;
   }
-  const FaceSlot sl = mt->slot(el * 2 * DIM + k);
+  const int si = el * 2 * DIM + k;
+  const FaceSlot sl = mt->slot(si);
   const int qf = sl.qf, ax = k >> 1;
   const int npts = DIM == 2 ? qf : qf * qf;
   const int z = z0 + qf * z1;
   const int zc = canon(DIM, sl.side, sl.orient, qf, z0, z1);
-  const T* tr = a.trace + rhs * a.trace_stride + 4 * a.f_troff[sl.face] + zc;
+  const T* tr = a.trace + rhs * a.trace_stride + 4 * mt->troff(si) + zc;
   const bool faff = (sl.flags & kFaceAffine) != 0;
   const T* GWf = tb + TabLayout::GW(N, qf);
   const T wz = faff ? (DIM == 2 ? GWf[zc] : GWf[zc % qf] * GWf[zc / qf]) : T(0);
-  FaceGeo<T> fg{a.fgeo + a.f_goff[sl.face], npts, zc, sl.side, DIM, faff, wz};
+  FaceGeo<T> fg{a.fgeo + mt->goff(si), npts, zc, sl.side, DIM, faff, wz};
   const T W = fg.W();
-  const T tau = a.f_tau[sl.face];
+  const T tau = (T)mt->tau(si);
   const T uo = tr[(int64_t)(2 * sl.side) * npts];
   const T go_ = tr[(int64_t)(2 * sl.side + 1) * npts];
   T s, tt;
@@ -665,7 +677,8 @@ __device__ __forceinline__ void face_flux(const ApplyArgs<T>& a, const TileMeta<
 template <typename T, int DIM, int N>
 __device__ __forceinline__ void face_flux_p2p(const ApplyArgs<T>& a, const TileMeta<DIM>* mt, int rhs, const T* tb,
                                               bool orth, int el, int k, int z0, int z1, T* dst, int fs) {
-  const FaceSlot sl = mt->slot(el * 2 * DIM + k);
+  const int si = el * 2 * DIM + k;
+  const FaceSlot sl = mt->slot(si);
   const int qf = sl.qf, ax = k >> 1;
   const int npts = DIM == 2 ? qf : qf * qf;
   const int z = z0 + qf * z1;
@@ -675,11 +688,11 @@ __device__ __forceinline__ void face_flux_p2p(const ApplyArgs<T>& a, const TileM
   const bool faff = (sl.flags & kFaceAffine) != 0;
   const T* GWf = tb + TabLayout::GW(N, qf);
   const T wz = faff ? (DIM == 2 ? GWf[zc] : GWf[zc % qf] * GWf[zc / qf]) : T(0);
-  const FaceGeoP2P<T> fg = face_geo_p2p<T, DIM>(a, sl, npts, npm, zc, wz);
-  const T* trf = a.trace + rhs * a.trace_stride + 4 * a.f_troff[sl.face];
+  const FaceGeoP2P<T> fg = face_geo_p2p<T, DIM>(a, sl, mt->goff(si), npts, npm, zc, wz);
+  const T* trf = a.trace + rhs * a.trace_stride + 4 * mt->troff(si);
   const T* tr = trf + p2p_own_block(sl.side, npm) + zc;
   const T W = fg.W();
-  const T tau = a.f_tau[sl.face];
+  const T tau = (T)mt->tau(si);
   const T uo = tr[0];
   const T go_ = tr[npts];
   T s, tt;
@@ -829,19 +842,19 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   T* const F0 = sm + (2 + DIM) * QV;
   // the face list follows the element buffers (kFaceListBytes, FP64 only)
   uint16_t* flist = dense_faces<T>() ? reinterpret_cast<uint16_t*>(sm + ne * PER) : nullptr;
-  load_meta<DIM>(a.elist, a.slots, a.eaff, a.flists, t, mt, flist);
+  load_meta<DIM>(a.desc_e, a.desc_s, a.flists, t, mt, flist);
   __syncthreads();
   if (a.ug) {
     for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
       const int el = w / QV, q = w - el * QV;
-      U[el * PER + q] = a.ug[rhs * a.nquad + a.quad_off[mt->eid(el)] + q];
+      U[el * PER + q] = a.ug[rhs * a.nquad + mt->qoff(el) + q];
     }
     __syncthreads();
   } else {
     // recompute the Gauss values: 2D G0 -> G1 -> U, 3D G0 -> G1 -> G2 -> U
     for (int w = threadIdx.x; w < ne * NV; w += blockDim.x) {
       const int el = w / NV, i = w - el * NV;
-      G0[el * PER + i] = a.x[rhs * a.ndof + a.dof_off[mt->eid(el)] + i];
+      G0[el * PER + i] = a.x[rhs * a.ndof + mt->dof(el) + i];
     }
     __syncthreads();
     const T* BT = tb + TabLayout::BT(N);
@@ -892,7 +905,6 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
           continue;
         }
         const int el = w / QV, q = w - el * QV;
-        const int e = mt->eid(el);
         T* b = sm + el * PER;
         T g[DIM];
         if constexpr (line_mode<T, DIM>()) {
@@ -914,7 +926,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
         // Gauss weight.  The gradient is scaled first (kappa, weight), so that each
         // multiply that is 1 is skipped.
         const bool eaf = mt->aff(el) != 0;
-        const T* geo = a.vgeo + a.vgoff[e] + (eaf ? 0 : q);
+        const T* geo = a.vgeo + mt->vgo(el) + (eaf ? 0 : q);
         const int gs = eaf ? 1 : QV;
         T lwj = a.lambda * geo[DIM == 2 ? 3 * gs : 6 * gs];
         if (eaf || a.kappa) {
@@ -926,7 +938,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
             lwj *= wq;
             wk = wq;
           }
-          if (a.kappa) wk = eaf ? wk * a.kappa[a.quad_off[e] + q] : a.kappa[a.quad_off[e] + q];
+          if (a.kappa) wk = eaf ? wk * a.kappa[mt->qoff(el) + q] : a.kappa[mt->qoff(el) + q];
   #pragma unroll
           for (int m = 0; m < DIM; ++m) g[m] *= wk;
         }
@@ -968,7 +980,6 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
           continue;
         }
         const int el = w / QV, q = w - el * QV;
-        const int e = mt->eid(el);
         T* b = sm + el * PER;
         T g[DIM];
         if constexpr (line_mode<T, DIM>()) {
@@ -990,7 +1001,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
         // Gauss weight.  The gradient is scaled first (kappa, weight), so that each
         // multiply that is 1 is skipped.
         const bool eaf = mt->aff(el) != 0;
-        const T* geo = a.vgeo + a.vgoff[e] + (eaf ? 0 : q);
+        const T* geo = a.vgeo + mt->vgo(el) + (eaf ? 0 : q);
         const int gs = eaf ? 1 : QV;
         T lwj = a.lambda * geo[DIM == 2 ? 3 * gs : 6 * gs];
         if (eaf || a.kappa) {
@@ -1002,7 +1013,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
             lwj *= wq;
             wk = wq;
           }
-          if (a.kappa) wk = eaf ? wk * a.kappa[a.quad_off[e] + q] : a.kappa[a.quad_off[e] + q];
+          if (a.kappa) wk = eaf ? wk * a.kappa[mt->qoff(el) + q] : a.kappa[mt->qoff(el) + q];
   #pragma unroll
           for (int m = 0; m < DIM; ++m) g[m] *= wk;
         }
@@ -1129,7 +1140,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   }
   // y = (B^T x B^T (x B^T)) H; the last contraction writes y in global memory
   const T* BB = tb + TabLayout::BB(N);
-  auto gy = [&](int el) { return a.y + rhs * a.ndof + a.dof_off[mt->eid(el)]; };
+  auto gy = [&](int el) { return a.y + rhs * a.ndof + mt->dof(el); };
   T* res = nullptr;
   if constexpr (DIM == 2) {
     cpt<T, Q, Q, 1, 0, N, false>(U, G0, PER, ne, BB);
@@ -1154,7 +1165,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
     __syncthreads();
     for (int w = threadIdx.x; w < ne * NV; w += blockDim.x) {
       const int el = w / NV, i = w - el * NV;
-      a.y[rhs * a.ndof + a.dof_off[mt->eid(el)] + i] = res[el * PER + i];
+      a.y[rhs * a.ndof + mt->dof(el) + i] = res[el * PER + i];
     }
   } else {
     (void)res;
@@ -1162,8 +1173,8 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   }
 }
 
-// Shared memory of a CTA: [table block of its order (table_block_bytes)][tile
-// meta (kMetaBytes)][elements].  A CTA runs a list of tiles of one order (its share
+// Shared memory of a CTA: [table block of its order up to the finest face rule
+// of its tiles (table_block_bytes)][tile meta (meta_bytes)][elements].  A CTA runs a list of tiles of one order (its share
 // of the launch, tiles cta_off[b] .. cta_off[b+1]-1) one after the other, with the
 // order's tables loaded once.
 #define SIP_ORDER_SWITCH(FN) \
@@ -1183,10 +1194,19 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
 
 template <typename T, int DIM, int N, bool MAIN, bool P2P>
 __device__ __forceinline__ void run_tiles(const ApplyArgs<T>& a, int ti0, int ti1, int rhs, unsigned char* smem_raw) {
+  // finest face rule of the CTA's tiles: the extent of its table block
+  int fmax = N + 1;
+  bool force = false;
+  for (int ti = ti0; ti < ti1; ++ti) {
+    const int fl = a.tiles[ti].flags;
+    fmax = max(fmax, fl & kTileQfMask);
+    force = force || (fl & kTileForce);
+  }
+  const int tbytes = table_block_bytes(sizeof(T), N, fmax);
   T* tb = reinterpret_cast<T*>(smem_raw);
-  TileMeta<DIM>* mt = reinterpret_cast<TileMeta<DIM>*>(smem_raw + table_block_bytes(sizeof(T), N));
-  T* sm = reinterpret_cast<T*>(smem_raw + table_block_bytes(sizeof(T), N) + kMetaBytes);
-  load_tables<T, N>(tb);
+  TileMeta<DIM>* mt = reinterpret_cast<TileMeta<DIM>*>(smem_raw + tbytes);
+  T* sm = reinterpret_cast<T*>(smem_raw + tbytes + meta_bytes(DIM));
+  load_tables<T, N>(tb, fmax, force);
   grid_dep_wait();  // before anything that another kernel writes
   for (int ti = ti0; ti < ti1; ++ti) {
     if (ti > ti0) __syncthreads();  // the previous tile's last stage still reads shared memory

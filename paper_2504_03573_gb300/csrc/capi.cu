@@ -184,13 +184,22 @@ int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_p
                   Schedule& s) {
   const Plan& p = h->plan;
   const int es = precision == SIP_FP32 ? 4 : 8;
+  // per CTA: its table block (up to the finest face rule of its tiles, as the
+  // kernels compute it), the tile meta and its largest tile
   auto size_smem = [&]() {
     s.smem_t = s.smem_m = 0;
-    for (const Tile& t : s.tiles) {
-      const size_t fixed = (size_t)table_block_bytes(es, t.n) + kMetaBytes;
-      s.smem_t = std::max(s.smem_t, fixed + (size_t)t.count * per_elem_trace(p.dim, t.n) * es);
-      s.smem_m = std::max(s.smem_m, fixed + (size_t)t.count * per_elem_main(p.dim, t.n) * es +
-                                        (precision == SIP_FP64 ? kFaceListBytes : 0));
+    for (size_t c = 0; c + 1 < s.cta_off.size(); ++c) {
+      if (s.cta_off[c] == s.cta_off[c + 1]) continue;
+      const int n = s.tiles[s.cta_off[c]].n;
+      int fmax = n + 1;
+      for (int32_t ti = s.cta_off[c]; ti < s.cta_off[c + 1]; ++ti) fmax = std::max(fmax, s.tiles[ti].flags & kTileQfMask);
+      const size_t fixed = (size_t)table_block_bytes(es, n, fmax) + meta_bytes(p.dim);
+      for (int32_t ti = s.cta_off[c]; ti < s.cta_off[c + 1]; ++ti) {
+        const Tile& t = s.tiles[ti];
+        s.smem_t = std::max(s.smem_t, fixed + (size_t)t.count * per_elem_trace(p.dim, t.n) * es);
+        s.smem_m = std::max(s.smem_m, fixed + (size_t)t.count * per_elem_main(p.dim, t.n) * es +
+                                          (precision == SIP_FP64 ? kFaceListBytes : 0));
+      }
     }
   };
   // one CTA per tile of the largest size epb allows: the tile count and shared
@@ -292,6 +301,8 @@ ApplyArgs<T> make_args(sip_handle* h, const T* x, T* y, T* trace, T* ug, int tra
   a.fgeo = g.fgeo;
   a.elist = h->elist;
   a.eaff = h->eaff;
+  a.desc_e = h->desc_e;
+  a.desc_s = h->desc_s;
   a.tiles = h->tiles_d[std::is_same<T, float>::value ? 1 : 0];
   a.cta_off = h->cta_d[std::is_same<T, float>::value ? 1 : 0];
   a.flists = h->flist_d[std::is_same<T, float>::value ? 1 : 0];
@@ -467,6 +478,8 @@ int sip_create(const sip_mesh* mesh, const int32_t* orders, double lambda, const
   UP(h->slots, p.slots);
   UP(h->elist, p.elist);
   UP(h->eaff, p.affine);
+  UP(h->desc_e, p.desc_e);
+  UP(h->desc_s, p.desc_s);
   UP(h->gd.vgeo, p.vgeo);
   UP(h->gd.fgeo, p.fgeo);
   UP(h->gd.tau, p.f_tau);

@@ -30,6 +30,8 @@ struct ApplyArgs {
   const int32_t* cta_off;  // CTA b runs tiles cta_off[b] .. cta_off[b+1]-1 (one order)
   const uint16_t* flists;  // face lists of the tiles (Tile::flist)
   const int8_t* eaff;      // per element: 1 if its volume geometry is stored as constants
+  const ElemDesc* desc_e;  // per position of the order-sorted element list
+  const SlotDesc* desc_s;  // [position][2 dim]
   const T* x;
   T* y;
   T* trace;

@@ -56,6 +56,8 @@ struct sip_handle {
   sip::FaceSlot* slots = nullptr;
   int32_t* elist = nullptr;
   int8_t* eaff = nullptr;
+  sip::ElemDesc* desc_e = nullptr;   // element / slot descriptors in elist order
+  sip::SlotDesc* desc_s = nullptr;
   sip::Tile* tiles_d[2] = {nullptr, nullptr};   // per precision (FP64, FP32)
   std::vector<sip::Tile> tiles_h[2];
   int32_t* cta_d[2] = {nullptr, nullptr};       // CTA b runs tiles cta_off[b] .. cta_off[b+1]-1

@@ -583,6 +583,16 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
   std::iota(p.elist.begin(), p.elist.end(), 0);
   std::stable_sort(p.elist.begin(), p.elist.end(),
                    [&](int32_t a, int32_t b) { return p.P[a] < p.P[b]; });
+  p.desc_e.resize(E);
+  p.desc_s.resize((size_t)E * nf);
+  for (int64_t i = 0; i < E; ++i) {
+    const int32_t e = p.elist[i];
+    p.desc_e[i] = ElemDesc{p.dof_off[e], p.vgoff[e], p.quad_off[e], e, (int32_t)p.affine[e]};
+    for (int k = 0; k < nf; ++k) {
+      const FaceSlot& sl = p.slots[(size_t)e * nf + k];
+      p.desc_s[(size_t)i * nf + k] = SlotDesc{sl, p.f_troff[sl.face], p.f_goff[sl.face], p.f_tau[sl.face]};
+    }
+  }
   return SIP_OK;
 }
 

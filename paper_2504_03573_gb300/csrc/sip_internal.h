@@ -67,8 +67,10 @@ constexpr int kTabSize = tab_I(kQMax + 1, kQMax + 2);
 //   DT [Q][Q]  D[q][r] at r*Q + q      collocation derivative
 //   DD [Q][Q]  D[q][r] at q*Q + r      transposed derivative
 //   LL [4][Q]  l(-1), l(+1), l'(-1), l'(+1)
-//   for F = Q .. kQMax:    IT_F [Q][F] (I[z][r] at r*F + z), II_F [F][Q] (I[z][r] at z*Q + r)
 //   for F = Q .. kQMax:    GW_F [F] weights of the F-point rule
+//   for F = Q .. kQMax:    IT_F [Q][F] (I[z][r] at r*F + z), II_F [F][Q] (I[z][r] at z*Q + r)
+// A CTA holds (and loads) the block only up to the finest face rule fmax of its
+// tiles: the element buffers follow at table_block_bytes(bytes, n, fmax).
 // ---------------------------------------------------------------------------
 struct TabLayout {
   static constexpr int BT(int) { return 0; }
@@ -76,19 +78,20 @@ struct TabLayout {
   static constexpr int DT(int n) { return 2 * n * (n + 1); }
   static constexpr int DD(int n) { return DT(n) + (n + 1) * (n + 1); }
   static constexpr int LL(int n) { return DD(n) + (n + 1) * (n + 1); }
-  static constexpr int IT(int n, int f) {
+  // weights of the F-point rules, F = Q .. kQMax (affine geometry)
+  static constexpr int GW(int n, int f) {
     int o = LL(n) + 4 * (n + 1);
+    for (int g = n + 1; g < f; ++g) o += g;
+    return o;
+  }
+  static constexpr int IT(int n, int f) {
+    int o = GW(n, kQMax + 1);
     for (int g = n + 1; g < f; ++g) o += 2 * g * (n + 1);
     return o;
   }
   static constexpr int II(int n, int f) { return IT(n, f) + f * (n + 1); }
-  // weights of the F-point rules, F = Q .. kQMax (affine geometry)
-  static constexpr int GW(int n, int f) {
-    int o = IT(n, kQMax + 1);
-    for (int g = n + 1; g < f; ++g) o += g;
-    return o;
-  }
-  static constexpr int size(int n) { return GW(n, kQMax + 1); }
+  // entries up to and including the interpolation to the fmax-point rule
+  static constexpr int size(int n, int fmax) { return IT(n, fmax + 1); }
 };
 
 constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * cpow(b, e - 1); }
@@ -105,8 +108,11 @@ constexpr int face_buf(int dim, int n, int fields) {
 }
 constexpr int per_elem_trace(int dim, int n) { return 2 * cpow(n + 1, dim) + face_buf(dim, n, 4); }
 constexpr int per_elem_main(int dim, int n) { return (2 + dim) * cpow(n + 1, dim) + face_buf(dim, n, 1 + dim); }
-// bytes of the CTA's table block (padded to 16) that precedes the element buffers
-constexpr int table_block_bytes(int bytes_per, int n) { return ((TabLayout::size(n) * bytes_per + 15) / 16) * 16; }
+// bytes of the CTA's table block (padded to 16) that precedes the element buffers,
+// for tiles whose finest face rule is fmax (at most kQMax)
+constexpr int table_block_bytes(int bytes_per, int n, int fmax = kQMax) {
+  return ((TabLayout::size(n, fmax) * bytes_per + 15) / 16) * 16;
+}
 
 // ---------------------------------------------------------------------------
 // Per element local face slot (2*dim per element; local face k = 2*axis + side).
@@ -156,10 +162,29 @@ constexpr int fl_el(int e) { return e & 31; }
 constexpr int fl_k(int e) { return (e >> 5) & 7; }
 constexpr int fl_qf(int e) { return e >> 8; }
 
-// per-tile copy of the face slots, element ids and affine flags, after the table
-// block (a fixed size, so that the element buffers that follow sit at a
-// compile-time offset); the face list, where used, follows the element buffers
-constexpr int kMetaBytes = ((kMaxEpb * (6 * (int)sizeof(FaceSlot) + 4 + 1) + 15) / 16) * 16;
+// What the kernels look up per element and per face slot, packed in the order of
+// the order-sorted element list (elist), so that a tile's descriptors are two
+// contiguous blocks read with one round of coalesced loads instead of chains of
+// dependent lookups (element id -> offsets, face id -> offsets and penalty).
+struct ElemDesc {     // 32 bytes
+  int64_t dof_off;    // first DOF of the element
+  int64_t vgoff;      // volume geometry offset
+  int64_t quad_off;   // first volume point (kappa, Gauss-point values)
+  int32_t eid;        // element id
+  int32_t aff;        // 1: volume geometry stored as constants
+};
+struct SlotDesc {     // 32 bytes
+  FaceSlot slot;      // the element's local face slot
+  int64_t troff;      // trace offset of the face (points)
+  int64_t goff;       // face geometry offset
+  double tau;         // penalty of the face
+};
+static_assert(sizeof(ElemDesc) == 32 && sizeof(SlotDesc) == 32, "descriptor layout");
+
+// per-tile copy of the element and slot descriptors in shared memory, after the
+// table block; the face list, where used, follows the element buffers
+constexpr int meta_bytes(int dim) { return kMaxEpb * (int)sizeof(ElemDesc) + kMaxEpb * 2 * dim * (int)sizeof(SlotDesc); }
+constexpr int kMetaBytes = meta_bytes(3);
 constexpr int kFaceListBytes = ((2 * kFaceListMax + 15) / 16) * 16;
 
 // Host plan: everything the device needs, in FP64.
@@ -194,6 +219,9 @@ struct Plan {
   std::vector<FaceSlot> slots;   // [E][2 dim]
   // elements sorted by order (stable); tiles are cut from this list per precision
   std::vector<int32_t> elist;
+  // descriptors in elist order: [E] and [E][2 dim]
+  std::vector<ElemDesc> desc_e;
+  std::vector<SlotDesc> desc_s;
   int64_t orient_hist[8] = {0};
 };
 

@@ -209,6 +209,7 @@ void sip_handle::release() {
   ck_x.clear(); ck_r.clear(); ck_p.clear();
   if (solve_stream) cudaStreamDestroy(solve_stream);
   cudaFree(dof_off); cudaFree(quad_off); cudaFree(vgoff); cudaFree(f_troff); cudaFree(f_goff);
+  cudaFree(desc_e); cudaFree(desc_s);
   cudaFree(slots); cudaFree(elist); cudaFree(eaff); cudaFree(tiles_d[0]); cudaFree(tiles_d[1]); cudaFree(cta_d[0]); cudaFree(cta_d[1]); cudaFree(flist_d[0]); cudaFree(flist_d[1]); cudaFree(xq);
   cudaFree(gd.vgeo); cudaFree(gd.fgeo); cudaFree(gd.tau); cudaFree(gd.kappa);
   cudaFree(gf.vgeo); cudaFree(gf.fgeo); cudaFree(gf.tau); cudaFree(gf.kappa);
