@@ -98,7 +98,7 @@ typedef struct sip_options {
     int32_t max_iter;         /* CG iteration cap (total inner iterations), default 20000 */
     int32_t check_every;      /* CG iterations per captured graph launch, default 16 */
     int32_t max_refine;       /* outer refinement steps cap, default 30 */
-    int32_t checkpoint_every; /* save (x, r, p, r.r, k) every k CG iterations; 0 = off */
+    int32_t checkpoint_every; /* save the CG state every k iterations (sip_cg_checkpoint_*); 0 = off */
     int32_t checkpoint_slots; /* ring size for checkpoints, default 8 */
     int32_t face_scheme;      /* SIP_FACES_SHARED (default) or SIP_FACES_P2P.  P2P: each side of
                                  an interior face evaluates the flux on its OWN (P+2)-point
@@ -222,10 +222,44 @@ int  sip_cg_solve(sip_handle* h, int mode, const double* b_dev, double* x_dev, i
 int  sip_cg_solve_transpose(sip_handle* h, int mode, const double* b_dev, double* x_dev, int nrhs,
                             double rtol, sip_stats* stats, void* stream);
 
-/* Checkpoints of the most recent FP64 solve (options.checkpoint_every > 0,
- * nrhs = 1): number stored, and copy-out of slot i (0 = oldest kept) into
- * caller device buffers x, r, p [ndof] plus host scalars rr and k. */
+/* Checkpoints of the most recent solve (options.checkpoint_every > 0): every
+ * checkpoint_every iterations of the running CG recurrence, for any nrhs, the
+ * solver copies its state into a ring of checkpoint_slots entries (device
+ * memory owned by the handle, grown to nrhs * ndof * 3 doubles per entry):
+ * FP64 CG: x, r, p (FP64) and the per-RHS scalars; SIP_CG_FP32_REFINED: the FP64
+ * iterate and the FP32 recurrence's r, p and scalars (taken at the graph-chunk
+ * boundaries, checkpoint_every rounded up to whole check_every chunks; the FP64
+ * CG that may finish such a solve checkpoints as FP64 CG).  The adjoint solve
+ * of the backward pass needs none of them (it uses the converged u); they let a
+ * caller resume or audit a solve.
+ * sip_cg_checkpoint_count: entries kept (the oldest is slot 0). */
 int  sip_cg_checkpoint_count(const sip_handle* h);
+
+typedef struct sip_checkpoint_info {
+    int32_t iteration;    /* iterations of the recurrence done when it was taken */
+    int32_t refinements;  /* outer refinements done (FP32-refined recurrence) */
+    int32_t restarts;     /* residual replacements done (FP64 recurrence) */
+    int32_t mode;         /* SIP_CG_FP64 or SIP_CG_FP32_REFINED: which recurrence */
+    int32_t nrhs;
+    int32_t transpose;    /* 1: taken in sip_cg_solve_transpose */
+} sip_checkpoint_info;
+int  sip_cg_checkpoint_info(const sip_handle* h, int slot, sip_checkpoint_info* out);
+
+/* The checkpoint's FP64 iterate into x_dev (double [nrhs][ndof]), on stream. */
+int  sip_cg_checkpoint_iterate(sip_handle* h, int slot, double* x_dev, void* stream);
+
+/* Continues the recurrence of checkpoint `slot` for `iters` iterations exactly
+ * as the solve ran it (same kernels, graph chunks and, for FP64 CG, the same
+ * per-RHS convergence masking between chunks; no residual replacement or
+ * refinement) and writes the resulting FP64 iterate into x_dev [nrhs][ndof].
+ * Where the solve did no replacement or refinement in those iterations, the
+ * result equals the later checkpoint's iterate bit for bit.  Uses the handle's
+ * solver workspace (not the ring) and synchronises the stream.
+ * Errors: SIP_ERR_ARG (slot out of range, iters < 0, SIP_FACES_P2P handle). */
+int  sip_cg_checkpoint_replay(sip_handle* h, int slot, int iters, double* x_dev, void* stream);
+
+/* FP64 single-RHS checkpoints only: copy-out of slot i into caller device
+ * buffers x, r, p [ndof] plus host scalars rr and k (SIP_ERR_ARG for others). */
 int  sip_cg_checkpoint_get(sip_handle* h, int slot, double* x_dev, double* r_dev, double* p_dev,
                            double* rr_host, int* iter_host, void* stream);
 /* Runs `iters` FP64 CG iterations starting from a state (x, r, p, rr) and
@@ -288,7 +322,7 @@ typedef struct sip_tiling {
                                        fit, at most the tiles per SM that epb gives; larger
                                        values are capped at the occupancy) */
     int32_t persistent;             /* 1: each CTA runs several tiles */
-    int32_t threads;                /* threads per CTA: 64, 128 or 256 (set: 0 = 256) */
+    int32_t threads;                /* threads per CTA: 32, 64, 128 or 256 (set: 0 = 256) */
     int64_t ntiles, nctas;          /* get only: tiles and CTAs per right-hand side */
 } sip_tiling;
 

@@ -472,11 +472,11 @@ class SipOracle:
             out[self.off[e]:self.off[e + 1]] = u(x)
         return out
 
-    def kappa_gradient(self, ybar, x):
+    def kappa_gradient(self, ybar, x, elements=None):
         """d(ybar^T A(kappa) x)/d kappa_q = w_q |J_q| grad ybar_h(x_q) . grad x_h(x_q),
-        one array of Q_e^d values per element."""
+        one array of Q_e^d values per element (of ``elements``, default all)."""
         out = []
-        for e in range(self.E):
+        for e in (range(self.E) if elements is None else elements):
             _, _, g, _, wdet = self._element_geometry(e)
             s = slice(self.off[e], self.off[e + 1])
             gy = np.einsum("pib,b->pi", g, ybar[s])

@@ -223,9 +223,29 @@ class SipOperator:
         check(lib.sip_quad_points(self._h, _ptr(xq), _stream()))
         return xq
 
-    # ---- checkpoints of the last FP64 solve
+    # ---- checkpoints of the last solve
     def checkpoint_count(self):
         return int(lib.sip_cg_checkpoint_count(self._h))
+
+    def checkpoint_info(self, slot) -> dict:
+        info = _lib.sip_checkpoint_info()
+        check(lib.sip_cg_checkpoint_info(self._h, int(slot), C.byref(info)))
+        return info.as_dict()
+
+    def _iterate_tensor(self, nrhs):
+        torch = _torch()
+        shape = (self.ndof,) if nrhs == 1 else (nrhs, self.ndof)
+        return torch.empty(shape, dtype=torch.float64, device="cuda")
+
+    def checkpoint_iterate(self, slot):
+        x = self._iterate_tensor(self.checkpoint_info(slot)["nrhs"])
+        check(lib.sip_cg_checkpoint_iterate(self._h, int(slot), _ptr(x), _stream()))
+        return x
+
+    def checkpoint_replay(self, slot, iters):
+        x = self._iterate_tensor(self.checkpoint_info(slot)["nrhs"])
+        check(lib.sip_cg_checkpoint_replay(self._h, int(slot), int(iters), _ptr(x), _stream()))
+        return x
 
     def checkpoint(self, slot):
         torch = _torch()
@@ -256,7 +276,7 @@ class SipOperator:
     def set_tiling(self, precision=SIP_FP64, epb_by_order=None, ctas_per_sm=0, persistent=False, threads=256):
         """Install elements per tile by order (None or 0 entries: default), the
         CTAs per SM the schedule is balanced for (0: automatic), whether CTAs run
-        several tiles each, and the threads per CTA (64, 128 or 256)."""
+        several tiles each, and the threads per CTA (32, 64, 128 or 256)."""
         t = _lib.sip_tiling()
         if epb_by_order is not None:
             if len(epb_by_order) != _lib.SIP_MAX_ORDER + 1:

@@ -82,6 +82,14 @@ class sip_tiling(C.Structure):
                 ("threads", C.c_int32), ("ntiles", C.c_int64), ("nctas", C.c_int64)]
 
 
+class sip_checkpoint_info(C.Structure):
+    _fields_ = [("iteration", C.c_int32), ("refinements", C.c_int32), ("restarts", C.c_int32),
+                ("mode", C.c_int32), ("nrhs", C.c_int32), ("transpose", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class sip_work(C.Structure):
     _fields_ = [("flops_trace", C.c_double), ("flops_main", C.c_double), ("bytes_x", C.c_double),
                 ("bytes_y", C.c_double), ("bytes_geometry", C.c_double), ("bytes_trace", C.c_double)]
@@ -118,6 +126,9 @@ SIGNATURES = {
     "sip_cg_checkpoint_count": (_I, [_H]),
     "sip_cg_checkpoint_get": (_I, [_H, _I, _P, _P, _P, C.POINTER(_D), C.POINTER(_I), _P]),
     "sip_cg_replay": (_I, [_H, _P, _P, _P, C.POINTER(_D), _I, _P]),
+    "sip_cg_checkpoint_info": (_I, [_H, _I, C.POINTER(sip_checkpoint_info)]),
+    "sip_cg_checkpoint_iterate": (_I, [_H, _I, _P, _P]),
+    "sip_cg_checkpoint_replay": (_I, [_H, _I, _I, _P, _P]),
     "sip_grad_kappa": (_I, [_H, _P, _P, _P, _I, _P]),
     "sip_mass_dot": (_I, [_H, _P, _P, _P, _P]),
     "sip_iproduct": (_I, [_H, _P, _P, _P]),

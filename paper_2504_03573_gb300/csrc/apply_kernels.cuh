@@ -190,8 +190,8 @@ __device__ __forceinline__ bool own_rule(int qf, bool force) { return qf == Q &&
 // face slots with their trace and geometry offsets and penalties.
 template <int DIM>
 struct TileMeta {
-  ElemDesc e_[kMaxEpb];
-  SlotDesc s_[kMaxEpb * 2 * DIM];
+  ElemDesc* e_;  // [cmax] in shared memory
+  SlotDesc* s_;  // [cmax][2 DIM] in shared memory
   __device__ __forceinline__ const FaceSlot& slot(int i) const { return s_[i].slot; }
   __device__ __forceinline__ int64_t troff(int i) const { return s_[i].troff; }
   __device__ __forceinline__ int64_t goff(int i) const { return s_[i].goff; }
@@ -202,8 +202,6 @@ struct TileMeta {
   __device__ __forceinline__ int64_t vgo(int el) const { return e_[el].vgoff; }
   __device__ __forceinline__ int64_t qoff(int el) const { return e_[el].quad_off; }
 };
-static_assert(sizeof(TileMeta<2>) <= meta_bytes(2) && sizeof(TileMeta<3>) <= meta_bytes(3),
-              "tile meta exceeds its shared-memory block");
 
 // Copy the tile's descriptors (two contiguous blocks, 16-byte vector loads) and,
 // where the tile has faces on the interpolation path and `list` is given, its
@@ -1174,7 +1172,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
 }
 
 // Shared memory of a CTA: [table block of its order up to the finest face rule
-// of its tiles (table_block_bytes)][tile meta (meta_bytes)][elements].  A CTA runs a list of tiles of one order (its share
+// of its tiles (table_block_bytes)][descriptors of its largest tile (meta_bytes)][elements].  A CTA runs a list of tiles of one order (its share
 // of the launch, tiles cta_off[b] .. cta_off[b+1]-1) one after the other, with the
 // order's tables loaded once.
 #define SIP_ORDER_SWITCH(FN) \
@@ -1194,18 +1192,23 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
 
 template <typename T, int DIM, int N, bool MAIN, bool P2P>
 __device__ __forceinline__ void run_tiles(const ApplyArgs<T>& a, int ti0, int ti1, int rhs, unsigned char* smem_raw) {
-  // finest face rule of the CTA's tiles: the extent of its table block
-  int fmax = N + 1;
+  // finest face rule and largest tile of the CTA's tiles: the extents of its
+  // table block and descriptor block
+  int fmax = N + 1, cmax = 1;
   bool force = false;
   for (int ti = ti0; ti < ti1; ++ti) {
-    const int fl = a.tiles[ti].flags;
-    fmax = max(fmax, fl & kTileQfMask);
-    force = force || (fl & kTileForce);
+    const Tile t = a.tiles[ti];
+    fmax = max(fmax, t.flags & kTileQfMask);
+    cmax = max(cmax, t.count);
+    force = force || (t.flags & kTileForce);
   }
   const int tbytes = table_block_bytes(sizeof(T), N, fmax);
   T* tb = reinterpret_cast<T*>(smem_raw);
-  TileMeta<DIM>* mt = reinterpret_cast<TileMeta<DIM>*>(smem_raw + tbytes);
-  T* sm = reinterpret_cast<T*>(smem_raw + tbytes + meta_bytes(DIM));
+  TileMeta<DIM> meta;
+  meta.e_ = reinterpret_cast<ElemDesc*>(smem_raw + tbytes);
+  meta.s_ = reinterpret_cast<SlotDesc*>(meta.e_ + cmax);
+  TileMeta<DIM>* mt = &meta;
+  T* sm = reinterpret_cast<T*>(smem_raw + tbytes + meta_bytes(DIM, cmax));
   load_tables<T, N>(tb, fmax, force);
   grid_dep_wait();  // before anything that another kernel writes
   for (int ti = ti0; ti < ti1; ++ti) {

@@ -112,7 +112,7 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
   //    the schedule is balanced for, with one tile per CTA or persistent CTAs
   int best_epb[kNMax + 2];
   std::memcpy(best_epb, cur, sizeof(cur));
-  for (int threads : {256, 128, 64}) {
+  for (int threads : {256, 128, 64, 32}) {
     int scaled[kNMax + 2] = {};
     for (int n : orders) scaled[n] = std::max(1, cur[n] * threads / 256);
     for (int pers = 0; pers < 2 && rc == SIP_OK; ++pers)

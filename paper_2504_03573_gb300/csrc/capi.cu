@@ -191,9 +191,12 @@ int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_p
     for (size_t c = 0; c + 1 < s.cta_off.size(); ++c) {
       if (s.cta_off[c] == s.cta_off[c + 1]) continue;
       const int n = s.tiles[s.cta_off[c]].n;
-      int fmax = n + 1;
-      for (int32_t ti = s.cta_off[c]; ti < s.cta_off[c + 1]; ++ti) fmax = std::max(fmax, s.tiles[ti].flags & kTileQfMask);
-      const size_t fixed = (size_t)table_block_bytes(es, n, fmax) + meta_bytes(p.dim);
+      int fmax = n + 1, cmax = 1;
+      for (int32_t ti = s.cta_off[c]; ti < s.cta_off[c + 1]; ++ti) {
+        fmax = std::max(fmax, s.tiles[ti].flags & kTileQfMask);
+        cmax = std::max(cmax, (int)s.tiles[ti].count);
+      }
+      const size_t fixed = (size_t)table_block_bytes(es, n, fmax) + meta_bytes(p.dim, cmax);
       for (int32_t ti = s.cta_off[c]; ti < s.cta_off[c + 1]; ++ti) {
         const Tile& t = s.tiles[ti];
         s.smem_t = std::max(s.smem_t, fixed + (size_t)t.count * per_elem_trace(p.dim, t.n) * es);
@@ -204,7 +207,8 @@ int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_p
   };
   // one CTA per tile of the largest size epb allows: the tile count and shared
   // memory bound the rest (a CTA's tiles are never larger)
-  if (threads != 64 && threads != 128 && threads != 256) return fail(SIP_ERR_ARG, "threads per CTA must be 64, 128 or 256");
+  if (threads != 32 && threads != 64 && threads != 128 && threads != 256)
+    return fail(SIP_ERR_ARG, "threads per CTA must be 32, 64, 128 or 256");
   build_tiles(p, precision, epb, threads, 0, false, s.tiles, s.cta_off, s.flists);
   size_smem();
   s.per_sm = 1;

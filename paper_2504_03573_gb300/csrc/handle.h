@@ -21,6 +21,24 @@ struct DevGeom {
   T* kappa = nullptr;
 };
 
+// One checkpoint of a CG recurrence: everything needed to continue it bit for
+// bit.  FP64 CG: x, r, p in FP64.  FP32-apply CG in FP64 refinement: the FP64
+// iterate x and the FP32 recurrence vectors r, p.  Vectors [nrhs][ndof].
+struct Checkpoint {
+  void* x = nullptr;
+  void* r = nullptr;
+  void* p = nullptr;
+  size_t cap = 0;              // bytes allocated for each of x, r, p
+  std::vector<double> scal;    // the recurrence's per-RHS scalars
+  std::vector<double> tol;     // per-RHS stopping tolerance of the recurrence
+  int iter = 0;                // CG iterations done when it was taken
+  int refinements = 0;         // outer refinements done (FP32-refined mode)
+  int restarts = 0;            // residual replacements done (FP64 mode)
+  int mode = 0;                // SIP_CG_FP64 or SIP_CG_FP32_REFINED (the recurrence's kind)
+  int nrhs = 0;
+  int transpose = 0;
+};
+
 // CG workspace for one (vector type, nrhs) configuration
 struct CgWork {
   int nrhs = 0;
@@ -103,10 +121,8 @@ struct sip_handle {
   double* red = nullptr;     // reduction partials for aux kernels
   double* scal_host = nullptr;
   int work_nrhs = 0;
-  // checkpoints (FP64 CG, nrhs = 1)
-  std::vector<double*> ck_x, ck_r, ck_p;
-  std::vector<double> ck_rr;
-  std::vector<int> ck_iter;
+  // checkpoints of the last solve (a ring of checkpoint_slots entries)
+  std::vector<sip::Checkpoint> ck;
   int ck_count = 0, ck_next = 0;
   void release();
 };

@@ -182,8 +182,11 @@ struct SlotDesc {     // 32 bytes
 static_assert(sizeof(ElemDesc) == 32 && sizeof(SlotDesc) == 32, "descriptor layout");
 
 // per-tile copy of the element and slot descriptors in shared memory, after the
-// table block; the face list, where used, follows the element buffers
-constexpr int meta_bytes(int dim) { return kMaxEpb * (int)sizeof(ElemDesc) + kMaxEpb * 2 * dim * (int)sizeof(SlotDesc); }
+// table block, sized for the largest tile (cmax elements) of the CTA; the face
+// list, where used, follows the element buffers
+constexpr int meta_bytes(int dim, int cmax = kMaxEpb) {
+  return cmax * ((int)sizeof(ElemDesc) + 2 * dim * (int)sizeof(SlotDesc));
+}
 constexpr int kMetaBytes = meta_bytes(3);
 constexpr int kFaceListBytes = ((2 * kFaceListMax + 15) / 16) * 16;
 

@@ -203,10 +203,8 @@ void sip_handle::release() {
   cg32.release();
   cudaFree(r64); cudaFree(x64); cudaFree(xbak); cudaFree(red);
   if (scal_host) cudaFreeHost(scal_host);
-  for (auto* p : ck_x) cudaFree(p);
-  for (auto* p : ck_r) cudaFree(p);
-  for (auto* p : ck_p) cudaFree(p);
-  ck_x.clear(); ck_r.clear(); ck_p.clear();
+  for (auto& c : ck) { cudaFree(c.x); cudaFree(c.r); cudaFree(c.p); }
+  ck.clear();
   if (solve_stream) cudaStreamDestroy(solve_stream);
   cudaFree(dof_off); cudaFree(quad_off); cudaFree(vgoff); cudaFree(f_troff); cudaFree(f_goff);
   cudaFree(desc_e); cudaFree(desc_s);
@@ -351,12 +349,62 @@ int write_scal(sip_handle* h, CgWork& W, int nrhs, cudaStream_t s) {
   return e == cudaSuccess ? SIP_OK : cuda_fail(e, "CG scalars upload");
 }
 
+// Save the recurrence state (x FP64; r, p of element size es; the per-RHS scalars,
+// already on the host in scal_host) into the next slot of the checkpoint ring.
+int save_checkpoint(sip_handle* h, const void* x, const void* r, const void* p, size_t es, int nrhs, int mode,
+                    int transpose, int iter, int refinements, int restarts, const std::vector<double>& tol,
+                    cudaStream_t s) {
+  const int ns = std::max(1, h->plan.opt.checkpoint_slots);
+  if ((int)h->ck.size() != ns) {
+    for (auto& c : h->ck) { cudaFree(c.x); cudaFree(c.r); cudaFree(c.p); }
+    h->ck.assign(ns, Checkpoint{});
+    h->ck_count = h->ck_next = 0;
+  }
+  Checkpoint& c = h->ck[h->ck_next];
+  const size_t n = (size_t)h->plan.ndof * nrhs;
+  const size_t need = n * sizeof(double);
+  if (c.cap < need) {
+    cudaFree(c.x); cudaFree(c.r); cudaFree(c.p);
+    c.x = c.r = c.p = nullptr;
+    c.cap = 0;
+    cudaError_t e = cudaMalloc(&c.x, need);
+    if (e == cudaSuccess) e = cudaMalloc(&c.r, need);
+    if (e == cudaSuccess) e = cudaMalloc(&c.p, need);
+    if (e != cudaSuccess) return cuda_fail(e, "checkpoint ring");
+    c.cap = need;
+  }
+  cudaMemcpyAsync(c.x, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(c.r, r, n * es, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(c.p, p, n * es, cudaMemcpyDeviceToDevice, s);
+  c.scal.assign(h->scal_host, h->scal_host + kScal * nrhs);
+  c.tol = tol;
+  c.iter = iter;
+  c.refinements = refinements;
+  c.restarts = restarts;
+  c.mode = mode;
+  c.nrhs = nrhs;
+  c.transpose = transpose;
+  h->ck_next = (h->ck_next + 1) % ns;
+  h->ck_count = std::min(h->ck_count + 1, ns);
+  return SIP_OK;
+}
+
+// Checkpointing of the FP64 recurrence inside cg_loop: iteration and restart
+// counts of the solve at the loop's start.
+struct CkCtx {
+  bool on = false;
+  int iter0 = 0;
+  int restarts = 0;
+};
+
 // Inner CG loop from the state already in W (r, p, x, scal with RR and ACTIVE set).
-// Runs until every active RHS has sqrt(rr) <= tol[rhs], or `budget` iterations.
+// Runs until every active RHS has sqrt(rr) <= tol[rhs], or `budget` iterations,
+// in chunks of `chunk` iterations (a captured graph each) with the convergence
+// test between chunks; ck.on saves a checkpoint after every full chunk.
 template <typename T>
 int cg_loop(sip_handle* h, CgWork& W, int nrhs, int prec, int transpose, const std::vector<double>& tol,
-            int budget, int* iters_done, cudaStream_t s, bool checkpoint) {
-  const int chunk = std::max(1, checkpoint ? h->plan.opt.checkpoint_every : h->plan.opt.check_every);
+            int budget, int* iters_done, cudaStream_t s, int chunk, const CkCtx& ck) {
+  chunk = std::max(1, chunk);
   int done = 0;
   while (true) {
     int status = 0;
@@ -378,18 +426,13 @@ int cg_loop(sip_handle* h, CgWork& W, int nrhs, int prec, int transpose, const s
     rc = run_iters<T>(h, W, nrhs, prec, transpose, it, s, it == chunk);
     if (rc) return rc;
     done += it;
-    if (checkpoint && it == chunk && !h->ck_x.empty()) {
-      const int slot = h->ck_next;
-      const size_t bytes = sizeof(double) * h->plan.ndof;
-      cudaMemcpyAsync(h->ck_x[slot], W.x, bytes, cudaMemcpyDeviceToDevice, s);
-      cudaMemcpyAsync(h->ck_r[slot], W.r, bytes, cudaMemcpyDeviceToDevice, s);
-      cudaMemcpyAsync(h->ck_p[slot], W.p, bytes, cudaMemcpyDeviceToDevice, s);
-      cudaMemcpyAsync(&h->scal_host[kScal * 1022], W.scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s);
-      cudaStreamSynchronize(s);
-      h->ck_rr[slot] = h->scal_host[kScal * 1022];
-      h->ck_iter[slot] = *iters_done + done;
-      h->ck_next = (slot + 1) % (int)h->ck_x.size();
-      h->ck_count = std::min(h->ck_count + 1, (int)h->ck_x.size());
+    if (ck.on && it == chunk) {
+      int status = 0;
+      rc = read_scal(h, W, nrhs, s, &status);
+      if (rc == SIP_OK)
+        rc = save_checkpoint(h, W.x, W.r, W.p, sizeof(T), nrhs, SIP_CG_FP64, transpose, *iters_done + done, 0,
+                             ck.restarts, tol, s);
+      if (rc) return rc;
     }
   }
   *iters_done += done;
@@ -450,21 +493,9 @@ int solve_impl(sip_handle* h, int mode, const double* b, double* x_out, int nrhs
   double worst = 0.0;
   h->ck_count = 0;
   h->ck_next = 0;
-  const bool ckpt = h->plan.opt.checkpoint_every > 0 && nrhs == 1 && mode == SIP_CG_FP64;
-  if (ckpt && (int)h->ck_x.size() != std::max(1, h->plan.opt.checkpoint_slots)) {
-    for (auto* p : h->ck_x) cudaFree(p);
-    for (auto* p : h->ck_r) cudaFree(p);
-    for (auto* p : h->ck_p) cudaFree(p);
-    const int ns = std::max(1, h->plan.opt.checkpoint_slots);
-    h->ck_x.assign(ns, nullptr); h->ck_r.assign(ns, nullptr); h->ck_p.assign(ns, nullptr);
-    h->ck_rr.assign(ns, 0.0); h->ck_iter.assign(ns, 0);
-    for (int i = 0; i < ns; ++i) {
-      cudaError_t e = cudaMalloc((void**)&h->ck_x[i], sizeof(double) * n);
-      if (e == cudaSuccess) e = cudaMalloc((void**)&h->ck_r[i], sizeof(double) * n);
-      if (e == cudaSuccess) e = cudaMalloc((void**)&h->ck_p[i], sizeof(double) * n);
-      if (e != cudaSuccess) { cudaEventDestroy(evu); return cuda_fail(e, "checkpoint ring"); }
-    }
-  }
+  // checkpoints every checkpoint_every iterations of whichever recurrence runs
+  // (FP64 CG, or the FP32 recurrence of the refined mode), any number of RHS
+  const bool ckpt = h->plan.opt.checkpoint_every > 0;
   // FP64 CG from the state (W.x, W.r = b - A W.x, rr) until the true residual meets tol
   auto fp64_cg = [&](const std::vector<double>& r0n2) -> int {
     cudaMemcpyAsync(W.p, W.r, bytes, cudaMemcpyDeviceToDevice, s);
@@ -480,7 +511,9 @@ int solve_impl(sip_handle* h, int mode, const double* b, double* x_out, int nrhs
     int rc2 = write_scal(h, W, nrhs, s);
     int restarts = 0;
     while (rc2 == SIP_OK) {
-      rc2 = cg_loop<double>(h, W, nrhs, SIP_FP64, transpose, tol, max_iter - st.iterations, &st.iterations, s, ckpt);
+      const CkCtx ck{ckpt, st.iterations, restarts};
+      const int chunk = ckpt ? h->plan.opt.checkpoint_every : h->plan.opt.check_every;
+      rc2 = cg_loop<double>(h, W, nrhs, SIP_FP64, transpose, tol, max_iter - st.iterations, &st.iterations, s, chunk, ck);
       if (rc2) break;
       // true residual r64 = b - A x
       rc2 = apply_any(h, SIP_FP64, W.x, h->r64, nrhs, s, transpose, nullptr);
@@ -549,6 +582,9 @@ int solve_impl(sip_handle* h, int mode, const double* b, double* x_out, int nrhs
     std::vector<double> rmax(nrhs);
     for (int r = 0; r < nrhs; ++r) rmax[r] = std::sqrt(bn2[r]);
     const int chunk = std::max(1, h->plan.opt.check_every);
+    // the FP32 recurrence is checkpointed at chunk boundaries, every
+    // checkpoint_every iterations rounded up to whole chunks
+    const int ck_every_chunks = std::max(1, (h->plan.opt.checkpoint_every + chunk - 1) / chunk);
     int total = 0;
     bool all_conv = false;
     double best = 1e300;   // best worst-case true residual so far
@@ -570,6 +606,11 @@ int solve_impl(sip_handle* h, int mode, const double* b, double* x_out, int nrhs
         rc = read_scal(h, V, nrhs, s, &status);
         if (rc) break;
         if (status & (ST_NONFINITE | ST_BREAKDOWN)) { broke = true; break; }
+        if (ckpt && (total / chunk) % ck_every_chunks == 0) {
+          rc = save_checkpoint(h, h->x64, V.r, V.p, sizeof(float), nrhs, SIP_CG_FP32_REFINED, transpose, total,
+                               st.refinements, 0, tol, s);
+          if (rc) break;
+        }
         for (int r = 0; r < nrhs; ++r) {
           const double* sc = h->scal_host + r * kScal;
           if (sc[S_ACTIVE] == 0.0) continue;
@@ -703,21 +744,104 @@ int sip_cg_solve_transpose(sip_handle* h, int mode, const double* b, double* x, 
 
 int sip_cg_checkpoint_count(const sip_handle* h) { return h ? h->ck_count : -1; }
 
+static const Checkpoint* checkpoint_at(const sip_handle* h, int slot) {
+  if (slot < 0 || slot >= h->ck_count) return nullptr;
+  const int ns = (int)h->ck.size();
+  return &h->ck[(h->ck_next - h->ck_count + slot + 2 * ns) % ns];
+}
+
 int sip_cg_checkpoint_get(sip_handle* h, int slot, double* x, double* r, double* p, double* rr_host, int* iter_host,
                           void* stream) {
   if (!h || !x || !r || !p || !rr_host || !iter_host) return fail(SIP_ERR_ARG, "null argument");
-  if (slot < 0 || slot >= h->ck_count) return fail(SIP_ERR_ARG, "checkpoint slot out of range");
-  const int ns = (int)h->ck_x.size();
-  const int idx = (h->ck_next - h->ck_count + slot + 2 * ns) % ns;
+  const Checkpoint* c = checkpoint_at(h, slot);
+  if (!c) return fail(SIP_ERR_ARG, "checkpoint slot out of range");
+  if (c->mode != SIP_CG_FP64 || c->nrhs != 1)
+    return fail(SIP_ERR_ARG, "sip_cg_checkpoint_get copies FP64 single-RHS states; use sip_cg_checkpoint_replay");
   const size_t bytes = sizeof(double) * h->plan.ndof;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaMemcpyAsync(x, h->ck_x[idx], bytes, cudaMemcpyDeviceToDevice, s);
-  cudaMemcpyAsync(r, h->ck_r[idx], bytes, cudaMemcpyDeviceToDevice, s);
-  cudaMemcpyAsync(p, h->ck_p[idx], bytes, cudaMemcpyDeviceToDevice, s);
-  *rr_host = h->ck_rr[idx];
-  *iter_host = h->ck_iter[idx];
+  cudaMemcpyAsync(x, c->x, bytes, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(r, c->r, bytes, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(p, c->p, bytes, cudaMemcpyDeviceToDevice, s);
+  *rr_host = c->scal[S_RR];
+  *iter_host = c->iter;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SIP_OK : cuda_fail(e, "checkpoint copy");
+}
+
+int sip_cg_checkpoint_info(const sip_handle* h, int slot, sip_checkpoint_info* out) {
+  if (!h || !out) return fail(SIP_ERR_ARG, "null argument");
+  const Checkpoint* c = checkpoint_at(h, slot);
+  if (!c) return fail(SIP_ERR_ARG, "checkpoint slot out of range");
+  out->iteration = c->iter;
+  out->refinements = c->refinements;
+  out->restarts = c->restarts;
+  out->mode = c->mode;
+  out->nrhs = c->nrhs;
+  out->transpose = c->transpose;
+  return SIP_OK;
+}
+
+int sip_cg_checkpoint_iterate(sip_handle* h, int slot, double* x_dev, void* stream) {
+  if (!h || !x_dev) return fail(SIP_ERR_ARG, "null argument");
+  const Checkpoint* c = checkpoint_at(h, slot);
+  if (!c) return fail(SIP_ERR_ARG, "checkpoint slot out of range");
+  cudaError_t e = cudaMemcpyAsync(x_dev, c->x, sizeof(double) * h->plan.ndof * c->nrhs, cudaMemcpyDeviceToDevice,
+                                  (cudaStream_t)stream);
+  return e == cudaSuccess ? SIP_OK : cuda_fail(e, "checkpoint copy");
+}
+
+int sip_cg_checkpoint_replay(sip_handle* h, int slot, int iters, double* x_dev, void* stream) {
+  NvtxRange range("sip_cg_checkpoint_replay");
+  if (!h || !x_dev || iters < 0) return fail(SIP_ERR_ARG, "bad argument");
+  if (h->p2p()) return fail(SIP_ERR_ARG, "CG needs the symmetric shared-rule operator (face_scheme SIP_FACES_SHARED)");
+  const Checkpoint* cp = checkpoint_at(h, slot);
+  if (!cp) return fail(SIP_ERR_ARG, "checkpoint slot out of range");
+  const Checkpoint c = *cp;  // the ring is not touched, but keep the fields stable
+  const int nrhs = c.nrhs;
+  int rc = ensure_solver(h, nrhs);
+  if (rc) return rc;
+  cudaStream_t s = h->solve_stream;
+  cudaStream_t user = (cudaStream_t)stream;
+  cudaEvent_t ev;
+  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  cudaEventRecord(ev, user);
+  cudaStreamWaitEvent(s, ev, 0);
+  const size_t n = (size_t)h->plan.ndof * nrhs;
+  const bool fp64 = c.mode == SIP_CG_FP64;
+  CgWork& W = fp64 ? h->cg64 : h->cg32;
+  rc = ensure_cg(h, W, fp64 ? sizeof(double) : sizeof(float), nrhs);
+  if (rc == SIP_OK) {
+    const size_t es = fp64 ? sizeof(double) : sizeof(float);
+    double* xit = fp64 ? (double*)W.x : h->x64;
+    cudaMemcpyAsync(xit, c.x, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(W.r, c.r, n * es, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(W.p, c.p, n * es, cudaMemcpyDeviceToDevice, s);
+    std::copy(c.scal.begin(), c.scal.end(), h->scal_host);
+    int zero = 0;
+    cudaMemcpyAsync(W.status, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
+    rc = write_scal(h, W, nrhs, s);
+    if (rc == SIP_OK && fp64) {
+      // the FP64 recurrence, chunked and masked as during the solve
+      int done = 0;
+      rc = cg_loop<double>(h, W, nrhs, SIP_FP64, c.transpose, c.tol, iters, &done, s,
+                           h->plan.opt.checkpoint_every, CkCtx{});
+    } else if (rc == SIP_OK) {
+      // the FP32 recurrence of the refined mode (FP64 iterate), in chunks
+      const int chunk = std::max(1, h->plan.opt.check_every);
+      W.xext = h->x64;
+      for (int done = 0; done < iters && rc == SIP_OK; done += chunk)
+        rc = run_iters<float>(h, W, nrhs, SIP_FP32, c.transpose, std::min(chunk, iters - done), s,
+                              iters - done >= chunk);
+      W.xext = nullptr;
+    }
+    if (rc == SIP_OK) cudaMemcpyAsync(x_dev, xit, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  }
+  cudaEventRecord(ev, s);
+  cudaStreamWaitEvent(user, ev, 0);
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaEventDestroy(ev);
+  if (rc) return rc;
+  return e == cudaSuccess ? SIP_OK : cuda_fail(e, "checkpoint replay");
 }
 
 int sip_cg_replay(sip_handle* h, double* x, double* r, double* p, double* rr_host, int iters, void* stream) {

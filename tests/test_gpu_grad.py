@@ -3,8 +3,9 @@
 Against the oracle (kappa in the volume term, kappa gradient, mass matrix,
 load vector, quadrature points) and against central finite differences of
 GPU solves for the gradients through the CG solve (the 16^3 hexes with P = 5
-and a smoothed log-normal kappa, and a small analogue that the oracle solves
-directly)."""
+and a smoothed log-normal kappa, where the kappa gradient is also compared
+with the oracle's formula on sampled elements, and a small analogue that the
+oracle solves directly)."""
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
@@ -154,6 +155,16 @@ def test_solve_gradients_fd_full_c5(pkg):
     loss.backward()
     assert op.checkpoint_count() > 0
     gk, gl, gb = kt.grad.clone(), float(lt.grad), bt.grad.clone()
+    # the oracle's kappa gradient -w|J| grad psi . grad u on sampled elements, with
+    # the GPU's u and adjoint psi (= dL/db, exactly the psi the backward used)
+    orc = SipOracle(m)
+    psi, u_np = gb.cpu().numpy(), u.detach().cpu().numpy()
+    qoff = np.concatenate([[0], np.cumsum((m.orders + 2) ** 3)])
+    sample = sorted(set(np.random.default_rng(21).choice(m.n_elem, 24, replace=False).tolist()) | {0, m.n_elem - 1})
+    ref = orc.kappa_gradient(psi, u_np, elements=sample)
+    gk_np = gk.cpu().numpy()
+    for e, r in zip(sample, ref):
+        assert rel(gk_np[qoff[e]:qoff[e + 1]], -r) <= 1e-10, e
     eps = 1e-6
     rng = np.random.default_rng(20)
     ndir = 20

@@ -105,6 +105,36 @@ def test_checkpoint_replay_bit_exact(pkg):
     assert torch.equal(x, x2)
 
 
+@pytest.mark.parametrize("mode,nrhs", [(1, 1), (0, 4), (1, 4)])
+def test_checkpoint_replay_refined_and_batched(pkg, mode, nrhs):
+    """Checkpoints of the FP32 recurrence of the refined solve and of batched
+    solves: continuing a checkpoint's recurrence to the next checkpoint (no
+    refinement or residual replacement in between) reproduces that
+    checkpoint's FP64 iterate bit for bit, and checkpointing leaves the
+    solution unchanged."""
+    import torch
+    m = MESH_2D
+    orc = SipOracle(m)
+    b = sine_rhs(orc, 2)
+    B = torch.tensor(b if nrhs == 1 else si.random_rhs_batch(nrhs, orc.ndof, 7), device="cuda")
+    op = pkg.SipOperator(m.dim, m.vert, m.elem_vert, m.orders, 1.0,
+                         pkg.options(checkpoint_every=16, checkpoint_slots=256))
+    x, st = op.cg_solve(B, mode=mode, rtol=1e-10)
+    n = op.checkpoint_count()
+    assert n >= 3 and st["checkpoints"] == n
+    info = [op.checkpoint_info(i) for i in range(n)]
+    assert all(c["nrhs"] == nrhs for c in info)
+    keys = ("mode", "refinements", "restarts")
+    pairs = [(i, i + 1) for i in range(n - 1)
+             if all(info[i][k] == info[i + 1][k] for k in keys) and info[i]["mode"] == mode]
+    assert len(pairs) >= 2
+    for i, j in pairs[:4]:
+        xr = op.checkpoint_replay(i, info[j]["iteration"] - info[i]["iteration"])
+        assert torch.equal(xr, op.checkpoint_iterate(j)), (i, j, info[i], info[j])
+    x2, _ = pkg.SipOperator.from_mesh(m).cg_solve(B, mode=mode, rtol=1e-10)
+    assert torch.equal(x, x2)
+
+
 def test_error_paths(pkg):
     import torch
     m = si.workload("c1_2d_4x4_p3")
