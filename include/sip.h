@@ -28,7 +28,8 @@
  *   i0 + N i1 (+ N^2 i2), N = P_e+1, i0 along the element's first reference
  *   axis (local vertex bit 0).  Multi-RHS arrays are [nrhs][ndof], contiguous.
  * - Quadrature-point arrays (kappa, its gradient, iproduct input) are element
- *   major with (P_e+2)^dim volume points per element (of the handle's rule),
+ *   major with Q_e^dim volume points per element (Q_e = P_e + 2 unless
+ *   sip_options.qorders says otherwise; points of the handle's rule),
  *   lexicographic, first reference axis fastest; offsets from sip_quad_offsets.
  * - Pointers named *_dev are CUDA device pointers owned by the caller; *_host
  *   are host pointers.  `stream` is a cudaStream_t passed as void* (NULL =
@@ -115,6 +116,15 @@ typedef struct sip_options {
                                  the projection back, also where both sides' rules coincide (the
                                  paper's measurement of the cost of non-conforming faces, Sec. 5.2);
                                  same operator, more work.  Default 0 */
+    const int32_t* qorders;   /* NULL (default): P + 2 volume points per direction in every element.
+                                 Else host [n_elem]: the points per direction of each element (read
+                                 by sip_plan_create / sip_create, not kept).  P + 2 always; with
+                                 SIP_RULE_GLL also (P, Q) = (1, 4), (1, 5), (2, 5): elements with the
+                                 coefficients of one order and the points of a higher one, such as
+                                 the transition layer of Sec. 3.3 (P2Q5 in the paper's counts,
+                                 between P4Q5 and P2Q3) and Table 2's P3Q5.  Faces integrate on
+                                 max(Q-, Q+) points (shared rule) or each side's own Q (P2P).
+                                 Other values: SIP_ERR_ARG */
 } sip_options;
 
 typedef struct sip_stats {

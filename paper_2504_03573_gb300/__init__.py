@@ -24,11 +24,18 @@ __all__ = ["SipOperator", "plan_info", "options", "fp_peak", "SipError", "SIP_FP
 
 
 def options(**kw) -> sip_options:
+    """sip_options with the library's defaults and the given fields;
+    qorders (points per direction of each element) is kept alive with the
+    struct."""
     o = sip_options()
     lib.sip_options_default(C.byref(o))
     for k, v in kw.items():
         if not hasattr(o, k):
             raise KeyError(k)
+        if k == "qorders" and v is not None:
+            arr = np.ascontiguousarray(v, dtype=np.int32)
+            o._qorders = arr
+            v = arr.ctypes.data_as(C.POINTER(C.c_int32))
         setattr(o, k, v)
     return o
 

@@ -50,7 +50,7 @@ class sip_options(C.Structure):
                 ("inner_rtol", C.c_double), ("max_iter", C.c_int32), ("check_every", C.c_int32),
                 ("max_refine", C.c_int32), ("checkpoint_every", C.c_int32),
                 ("checkpoint_slots", C.c_int32), ("face_scheme", C.c_int32), ("quad_rule", C.c_int32),
-                ("force_interp", C.c_int32)]
+                ("force_interp", C.c_int32), ("qorders", C.POINTER(C.c_int32))]
 
 
 class sip_stats(C.Structure):

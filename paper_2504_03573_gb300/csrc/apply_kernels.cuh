@@ -63,49 +63,48 @@ template <typename T>
 __host__ __device__ constexpr bool dense_faces() { return std::is_same<T, double>::value; }
 
 // ---- per-order compile-time shape
-template <int DIM, int N>
+template <int DIM, int N, int Q_>
 struct Shape {
-  static constexpr int Q = N + 1;
+  static constexpr int Q = Q_;
   static constexpr int NV = cpow(N, DIM);
   static constexpr int QV = cpow(Q, DIM);
   static constexpr int QF1 = cpow(Q, DIM - 1);       // own points on one face
   static constexpr int FMAX = cpow(kQMax, DIM - 1);  // points on one face at the finest rule
   static constexpr int FT = DIM == 3 ? kQMax * Q : 0;
   static constexpr int NFACE = 2 * DIM;
-  static constexpr int PER_TRACE = per_elem_trace(DIM, N);
-  static constexpr int PER_MAIN = per_elem_main(DIM, N);
+  static constexpr int PER_TRACE = per_elem_trace(DIM, N, Q_);
+  static constexpr int PER_MAIN = per_elem_main(DIM, N, Q_);
 };
 
 // Copy this order's 1D tables from __constant__ into the CTA's table block: the
 // face-rule interpolations up to the finest rule fmax of the CTA's tiles (from
 // the identity F = Q on when interpolation is forced), the weights up to fmax.
-template <typename T, int N>
+template <typename T, int N, int Q>
 __device__ __forceinline__ void load_tables(T* tb, int fmax, bool force) {
-  constexpr int Q = N + 1;
   for (int w = threadIdx.x; w < N * Q; w += blockDim.x) {
     const int q = w / N, i = w - q * N;  // B[q][i]
-    const T v = ctab<T>(tab_B(N) + w);
-    tb[TabLayout::BT(N) + i * Q + q] = v;
-    tb[TabLayout::BB(N) + q * N + i] = v;
+    const T v = ctab<T>(tab_B(N, Q) + w);
+    tb[TabLayout::BT(N, Q) + i * Q + q] = v;
+    tb[TabLayout::BB(N, Q) + q * N + i] = v;
   }
   for (int w = threadIdx.x; w < Q * Q; w += blockDim.x) {
     const int q = w / Q, r = w - q * Q;  // D[q][r]
     const T v = ctab<T>(tab_D(Q) + w);
-    tb[TabLayout::DT(N) + r * Q + q] = v;
-    tb[TabLayout::DD(N) + q * Q + r] = v;
+    tb[TabLayout::DT(N, Q) + r * Q + q] = v;
+    tb[TabLayout::DD(N, Q) + q * Q + r] = v;
   }
-  for (int w = threadIdx.x; w < 4 * Q; w += blockDim.x) tb[TabLayout::LL(N) + w] = ctab<T>(tab_L(Q) + w);
+  for (int w = threadIdx.x; w < 4 * Q; w += blockDim.x) tb[TabLayout::LL(N, Q) + w] = ctab<T>(tab_L(Q) + w);
   for (int f = force ? Q : Q + 1; f <= fmax; ++f) {
     const int io = c_ioff[Q][f];
     for (int w = threadIdx.x; w < f * Q; w += blockDim.x) {
       const int z = w / Q, r = w - z * Q;  // I[z][r]
       const T v = ctab<T>(io + w);
-      tb[TabLayout::IT(N, f) + r * f + z] = v;
-      tb[TabLayout::II(N, f) + z * Q + r] = v;
+      tb[TabLayout::IT(N, Q, f) + r * f + z] = v;
+      tb[TabLayout::II(N, Q, f) + z * Q + r] = v;
     }
   }
   for (int f = Q; f <= fmax; ++f)
-    for (int z = threadIdx.x; z < f; z += blockDim.x) tb[TabLayout::GW(N, f) + z] = cgw<T>(f, z);
+    for (int z = threadIdx.x; z < f; z += blockDim.x) tb[TabLayout::GW(N, Q, f) + z] = cgw<T>(f, z);
   __syncthreads();
 }
 
@@ -147,10 +146,9 @@ __device__ __forceinline__ void cpt(const T* __restrict__ in, T* __restrict__ ou
 
 // GLL coefficients in bA (N^DIM) -> Gauss values (Q^DIM); bB scratch.  Returns
 // the buffer holding the result.
-template <typename T, int DIM, int N>
+template <typename T, int DIM, int N, int Q>
 __device__ __forceinline__ T* interp_to_gauss(T* bA, T* bB, int stride, int ne, const T* tb) {
-  constexpr int Q = N + 1;
-  const T* BT = tb + TabLayout::BT(N);
+  const T* BT = tb + TabLayout::BT(N, Q);
   if constexpr (DIM == 2) {
     cpt<T, N, N, 1, 0, Q, false>(bA, bB, stride, ne, BT);
     __syncthreads();
@@ -311,11 +309,11 @@ __device__ __forceinline__ int64_t p2p_own_block(int side, int npm) { return (in
 // faces (shared rule = own Q points) go straight from the per-face buffer to the
 // trace; faces with a finer shared rule are interpolated one face at a time in
 // the element's scratch.
-template <typename T, int DIM, int N, bool P2P>
+template <typename T, int DIM, int N, int Q, bool P2P>
 __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Tile& t, const TileMeta<DIM>* mt, int rhs,
                                                 const T* tb, T* sm, const T* U) {
-  using S = Shape<DIM, N>;
-  constexpr int Q = S::Q, QF1 = S::QF1, FMAX = S::FMAX, FT = S::FT, NFACE = S::NFACE, PER = S::PER_TRACE;
+  using S = Shape<DIM, N, Q>;
+  constexpr int QF1 = S::QF1, FMAX = S::FMAX, FT = S::FT, NFACE = S::NFACE, PER = S::PER_TRACE;
   const int ne = t.count;
   const int qfm = t.flags & kTileQfMask;
   const bool fine = t.flags & kTileFine;
@@ -365,8 +363,8 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
     emit_vals(el, k, z0, z1, src[z], src[fs + z], orth ? T(0) : src[2 * fs + z],
               (DIM == 3 && !orth) ? src[3 * fs + z] : T(0));
   };
-  const T* LL = tb + TabLayout::LL(N);
-  const T* DT = tb + TabLayout::DT(N);
+  const T* LL = tb + TabLayout::LL(N, Q);
+  const T* DT = tb + TabLayout::DT(N, Q);
   // 1. value and reference normal derivative at the element's own face points
   //    (orthogonal conforming faces need nothing else and are stored at once)
   for (int w = threadIdx.x; w < ne * NFACE * QF1; w += blockDim.x) {
@@ -451,7 +449,7 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
           const int k = k0 + kk;
           const int qf = mt->slot(el * 2 * DIM + k).qf;
           if (own_rule<Q>(qf, force) || z >= qf) continue;
-          const T* IT = tb + TabLayout::IT(N, qf);
+          const T* IT = tb + TabLayout::IT(N, Q, qf);
           const T* src = F0 + el * PER + k * 4 * QF1 + f * QF1;
           T s = 0;
 #pragma unroll
@@ -469,7 +467,7 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
           const int k = k0 + kk;
           const int qf = mt->slot(el * 2 * DIM + k).qf;
           if (own_rule<Q>(qf, force) || z0 >= qf) continue;
-          const T* IT = tb + TabLayout::IT(N, qf);
+          const T* IT = tb + TabLayout::IT(N, Q, qf);
           const T* src = F0 + el * PER + k * 4 * QF1 + f * QF1 + j1 * Q;
           T s = 0;
 #pragma unroll
@@ -486,7 +484,7 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
           const int k = k0 + kk;
           const int qf = mt->slot(el * 2 * DIM + k).qf;
           if (own_rule<Q>(qf, force) || z0 >= qf || z1 >= qf) continue;
-          const T* IT = tb + TabLayout::IT(N, qf);
+          const T* IT = tb + TabLayout::IT(N, Q, qf);
           const T* src = F0 + el * PER + SC + kk * SL + f * FT + z0;
           T s = 0;
 #pragma unroll
@@ -516,9 +514,9 @@ __device__ __forceinline__ void trace_all_faces(const ApplyArgs<T>& a, const Til
 // rule and written into the other side's block, where its main kernel reads
 // them as the neighbour's trace.  The stored values are read back from global
 // memory, visible to the whole CTA after the barrier that ends the face stages.
-template <typename T, int DIM, int N>
+template <typename T, int DIM, int N, int Q>
 __device__ __forceinline__ void p2p_send(const ApplyArgs<T>& a, const Tile& t, const TileMeta<DIM>* mt, int rhs) {
-  constexpr int Q = N + 1, NFACE = 2 * DIM, FMAX = cpow(kQMax, DIM - 1), NP = cpow(Q, DIM - 1);
+  constexpr int NFACE = 2 * DIM, FMAX = cpow(kQMax, DIM - 1), NP = cpow(Q, DIM - 1);
   const int ne = t.count;
   for (int w = threadIdx.x; w < ne * NFACE * FMAX; w += blockDim.x) {
     const int el = w / (NFACE * FMAX), rem = w - el * NFACE * FMAX;
@@ -561,9 +559,9 @@ __device__ __forceinline__ void p2p_send(const ApplyArgs<T>& a, const Tile& t, c
   }
 }
 
-template <typename T, int DIM, int N, bool P2P>
+template <typename T, int DIM, int N, int Q, bool P2P>
 __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, TileMeta<DIM>* mt, T* sm) {
-  using S = Shape<DIM, N>;
+  using S = Shape<DIM, N, Q>;
   constexpr int PER = S::PER_TRACE;
   const int ne = t.count;
   load_meta<DIM>(a.desc_e, a.desc_s, a.flists, t, mt, nullptr);
@@ -575,7 +573,7 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
   if constexpr (!line_mode<T, DIM>()) {
     // first contraction reads the coefficients straight from global memory
     constexpr int Q = S::Q;
-    const T* BT = tb + TabLayout::BT(N);
+    const T* BT = tb + TabLayout::BT(N, Q);
     T* bA = sm;
     T* bB = sm + S::QV;
     auto gx = [&](int el) { return a.x + rhs * a.ndof + mt->dof(el); };
@@ -600,7 +598,7 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
       sm[el * PER + i] = a.x[rhs * a.ndof + mt->dof(el) + i];
     }
     __syncthreads();
-    U = to_gauss<T, DIM, N>(sm, sm + S::QV, PER, ne);
+    U = to_gauss<T, DIM, N, Q>(sm, sm + S::QV, PER, ne);
   }
   if (a.ug) {
     for (int w = threadIdx.x; w < ne * S::QV; w += blockDim.x) {
@@ -608,23 +606,23 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
       a.ug[rhs * a.nquad + mt->qoff(el) + q] = U[el * PER + q];
     }
   }
-  trace_all_faces<T, DIM, N, P2P>(a, t, mt, rhs, tb, sm, U);
-  if constexpr (P2P) p2p_send<T, DIM, N>(a, t, mt, rhs);
+  trace_all_faces<T, DIM, N, Q, P2P>(a, t, mt, rhs, tb, sm, U);
+  if constexpr (P2P) p2p_send<T, DIM, N, Q>(a, t, mt, rhs);
 }
 
 // ============================================================ main kernel
 // SIP flux of face k of element el at its shared point (z0, z1) (own order):
 // writes s and c_m t (m = 0..DIM-1; only c_a t where the tile is orthogonal) to
 // dst[f * fs + z0 + qf z1].
-template <typename T, int DIM, int N>
+template <typename T, int DIM, int N, int Q>
 __device__ __forceinline__ void face_flux_p2p(const ApplyArgs<T>& a, const TileMeta<DIM>* mt, int rhs, const T* tb,
                                               bool orth, int el, int k, int z0, int z1, T* dst, int fs);
 
-template <typename T, int DIM, int N, bool P2P>
+template <typename T, int DIM, int N, int Q, bool P2P>
 __device__ __forceinline__ void face_flux(const ApplyArgs<T>& a, const TileMeta<DIM>* mt, int rhs, const T* tb,
                                           bool orth, int el, int k, int z0, int z1, T* dst, int fs) {
   if constexpr (P2P) {
-    face_flux_p2p<T, DIM, N>(a, mt, rhs, tb, orth, el, k, z0, z1, dst, fs);
+    face_flux_p2p<T, DIM, N, Q>(a, mt, rhs, tb, orth, el, k, z0, z1, dst, fs);
     return;
   }
   const int si = el * 2 * DIM + k;
@@ -635,7 +633,7 @@ __device__ __forceinline__ void face_flux(const ApplyArgs<T>& a, const TileMeta<
   const int zc = canon(DIM, sl.side, sl.orient, qf, z0, z1);
   const T* tr = a.trace + rhs * a.trace_stride + 4 * mt->troff(si) + zc;
   const bool faff = (sl.flags & kFaceAffine) != 0;
-  const T* GWf = tb + TabLayout::GW(N, qf);
+  const T* GWf = tb + TabLayout::GW(N, Q, qf);
   const T wz = faff ? (DIM == 2 ? GWf[zc] : GWf[zc % qf] * GWf[zc / qf]) : T(0);
   FaceGeo<T> fg{a.fgeo + mt->goff(si), npts, zc, sl.side, DIM, faff, wz};
   const T W = fg.W();
@@ -672,7 +670,7 @@ __device__ __forceinline__ void face_flux(const ApplyArgs<T>& a, const TileMeta<
 // The same flux with point-to-point interpolation: this side's own rule, the
 // other side's values already interpolated to its points by the other side's
 // trace kernel (rows only; the transpose apply is not defined for this variant).
-template <typename T, int DIM, int N>
+template <typename T, int DIM, int N, int Q>
 __device__ __forceinline__ void face_flux_p2p(const ApplyArgs<T>& a, const TileMeta<DIM>* mt, int rhs, const T* tb,
                                               bool orth, int el, int k, int z0, int z1, T* dst, int fs) {
   const int si = el * 2 * DIM + k;
@@ -684,7 +682,7 @@ __device__ __forceinline__ void face_flux_p2p(const ApplyArgs<T>& a, const TileM
   const int oq = face_oq(sl.flags);
   const int npm = face_npts<DIM>(sl.side ? oq : qf);
   const bool faff = (sl.flags & kFaceAffine) != 0;
-  const T* GWf = tb + TabLayout::GW(N, qf);
+  const T* GWf = tb + TabLayout::GW(N, Q, qf);
   const T wz = faff ? (DIM == 2 ? GWf[zc] : GWf[zc % qf] * GWf[zc / qf]) : T(0);
   const FaceGeoP2P<T> fg = face_geo_p2p<T, DIM>(a, sl, mt->goff(si), npts, npm, zc, wz);
   const T* trf = a.trace + rhs * a.trace_stride + 4 * mt->troff(si);
@@ -715,12 +713,12 @@ __device__ __forceinline__ void face_flux_p2p(const ApplyArgs<T>& a, const TileM
 // Flux of faces with a finer shared rule (p-non-conforming), SC slots per
 // round: flux at the shared points, then projection back to the element's own
 // face points (TraceIProduct) into the per-face buffers.
-template <typename T, int DIM, int N, bool P2P>
+template <typename T, int DIM, int N, int Q, bool P2P>
 __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Tile& t, const TileMeta<DIM>* mt,
                                                 const uint16_t* flist, int rhs,
                                                 const T* tb, T* F0, int per, bool orth) {
-  using S = Shape<DIM, N>;
-  constexpr int Q = S::Q, QF1 = S::QF1, FMAX = S::FMAX, FT = S::FT, NFACE = S::NFACE, NF = 1 + DIM;
+  using S = Shape<DIM, N, Q>;
+  constexpr int QF1 = S::QF1, FMAX = S::FMAX, FT = S::FT, NFACE = S::NFACE, NF = 1 + DIM;
   constexpr int SC = NFACE * NF * QF1;
   constexpr int NSC = scratch_slots(DIM);
   constexpr int SL = NF * (FT + FMAX);  // one slot: Ft [NF][FT], Ff [NF][FMAX]
@@ -738,7 +736,7 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
       int j, z;
       fl.fine_at(per_f, w, j, z);
       const int e = fl.fine(j), el = fl_el(e), k = fl_k(e);
-      face_flux<T, DIM, N, P2P>(a, mt, rhs, tb, orth, el, k, z, 0, F0 + el * per + SC + k * SL + NF * FT, FMAX);
+      face_flux<T, DIM, N, Q, P2P>(a, mt, rhs, tb, orth, el, k, z, 0, F0 + el * per + SC + k * SL + NF * FT, FMAX);
     }
     __syncthreads();
     // projection of the fields in use (s and c_a t where the tile is orthogonal)
@@ -748,7 +746,7 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
       const int fi = r2 / Q, r = r2 - fi * Q;
       const int e = fl.fine(j), el = fl_el(e), k = fl_k(e), qf = fl_qf(e);
       const int f = orth && fi == 1 ? 1 + (k >> 1) : fi;
-      const T* II = tb + TabLayout::II(N, qf);
+      const T* II = tb + TabLayout::II(N, Q, qf);
       const T* src = F0 + el * per + SC + k * SL + NF * FT + f * FMAX;
       T s = 0;
       for (int z = 0; z < qf; ++z) s = fma(II[z * Q + r], src[z], s);
@@ -764,7 +762,7 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
         const int k = k0 + kk;
         const int qf = mt->slot(el * 2 * DIM + k).qf;
         if (own_rule<Q>(qf, force) || z0 >= qf || z1 >= qf) continue;
-        face_flux<T, DIM, N, P2P>(a, mt, rhs, tb, orth, el, k, z0, z1, F0 + el * per + SC + kk * SL + NF * FT, FMAX);
+        face_flux<T, DIM, N, Q, P2P>(a, mt, rhs, tb, orth, el, k, z0, z1, F0 + el * per + SC + kk * SL + NF * FT, FMAX);
       }
       __syncthreads();
       if constexpr (DIM == 2) {
@@ -776,7 +774,7 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
           const int k = k0 + kk;
           const int qf = mt->slot(el * 2 * DIM + k).qf;
           if (own_rule<Q>(qf, force) || (orth && f != 0 && f != 1 + (k >> 1))) continue;
-          const T* II = tb + TabLayout::II(N, qf);
+          const T* II = tb + TabLayout::II(N, Q, qf);
           const T* src = F0 + el * per + SC + kk * SL + NF * FT + f * FMAX;
           T s = 0;
           for (int z = 0; z < qf; ++z) s = fma(II[z * Q + r], src[z], s);
@@ -793,7 +791,7 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
           const int k = k0 + kk;
           const int qf = mt->slot(el * 2 * DIM + k).qf;
           if (own_rule<Q>(qf, force) || z1 >= qf || (orth && f != 0 && f != 1 + (k >> 1))) continue;
-          const T* II = tb + TabLayout::II(N, qf);
+          const T* II = tb + TabLayout::II(N, Q, qf);
           const T* src = F0 + el * per + SC + kk * SL + NF * FT + f * FMAX + qf * z1;
           T s = 0;
           for (int z0 = 0; z0 < qf; ++z0) s = fma(II[z0 * Q + r0], src[z0], s);
@@ -809,7 +807,7 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
           const int k = k0 + kk;
           const int qf = mt->slot(el * 2 * DIM + k).qf;
           if (own_rule<Q>(qf, force) || (orth && f != 0 && f != 1 + (k >> 1))) continue;
-          const T* II = tb + TabLayout::II(N, qf);
+          const T* II = tb + TabLayout::II(N, Q, qf);
           const T* src = F0 + el * per + SC + kk * SL + f * FT + r0;
           T s = 0;
           for (int z1 = 0; z1 < qf; ++z1) s = fma(II[z1 * Q + r1], src[z1 * Q], s);
@@ -821,10 +819,10 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
   }
 }
 
-template <typename T, int DIM, int N, bool P2P>
+template <typename T, int DIM, int N, int Q, bool P2P>
 __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, TileMeta<DIM>* mt, T* sm) {
-  using S = Shape<DIM, N>;
-  constexpr int Q = S::Q, QV = S::QV, NV = S::NV, QF1 = S::QF1, NFACE = S::NFACE, PER = S::PER_MAIN;
+  using S = Shape<DIM, N, Q>;
+  constexpr int QV = S::QV, NV = S::NV, QF1 = S::QF1, NFACE = S::NFACE, PER = S::PER_MAIN;
   constexpr int NF = 1 + DIM;
   const int ne = t.count;
   const bool fine = t.flags & kTileFine;
@@ -855,7 +853,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
       G0[el * PER + i] = a.x[rhs * a.ndof + mt->dof(el) + i];
     }
     __syncthreads();
-    const T* BT = tb + TabLayout::BT(N);
+    const T* BT = tb + TabLayout::BT(N, Q);
     if constexpr (DIM == 2) {
       cpt<T, N, N, 1, 0, Q, false>(G0, G1, PER, ne, BT);
       __syncthreads();
@@ -867,11 +865,11 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
       __syncthreads();
       cpt<T, Q, Q, N, 2, Q, false>(G2, U, PER, ne, BT);
     } else {
-      contract<T, N, N, N, 0, Q, tab_B(N), false, false>(G0, G1, PER, ne);
+      contract<T, N, N, N, 0, Q, tab_B(N, Q), false, false>(G0, G1, PER, ne);
       __syncthreads();
-      contract<T, Q, N, N, 1, Q, tab_B(N), false, false>(G1, G2, PER, ne);
+      contract<T, Q, N, N, 1, Q, tab_B(N, Q), false, false>(G1, G2, PER, ne);
       __syncthreads();
-      contract<T, Q, Q, N, 2, Q, tab_B(N), false, false>(G2, U, PER, ne);
+      contract<T, Q, Q, N, 2, Q, tab_B(N, Q), false, false>(G2, U, PER, ne);
     }
     __syncthreads();
   }
@@ -886,7 +884,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   // output-per-thread mode) and the flux of the conforming faces, in one pass:
   //   G_m = kappa (G grad_ref u)_m,  R = lambda w|J| u,  Fq[k] = (s, c_m t)
   {
-    const T* DT = tb + TabLayout::DT(N);
+    const T* DT = tb + TabLayout::DT(N, Q);
     const int nvol = ne * QV;
     // two copies of the pass: the FP32 one over all faces with the others skipped
     // (the shape its compiled code is fastest in), the FP64 one over the tile's
@@ -899,7 +897,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
           const int rem = v - el * NFACE * QF1;
           const int k = rem / QF1, j = rem - k * QF1;
           if (!own_rule<Q>(mt->slot(el * 2 * DIM + k).qf, force)) continue;
-          face_flux<T, DIM, N, P2P>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
+          face_flux<T, DIM, N, Q, P2P>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
           continue;
         }
         const int el = w / QV, q = w - el * QV;
@@ -930,7 +928,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
         if (eaf || a.kappa) {
           T wk = T(1);
           if (eaf) {
-            const T* gw = tb + TabLayout::GW(N, Q);
+            const T* gw = tb + TabLayout::GW(N, Q, Q);
             T wq = gw[q % Q] * gw[(q / Q) % Q];
             if constexpr (DIM == 3) wq *= gw[q / (Q * Q)];
             lwj *= wq;
@@ -974,7 +972,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
             j = rem - k * QF1;
             if (fine && !own_rule<Q>(mt->slot(el * 2 * DIM + k).qf, force)) continue;
           }
-          face_flux<T, DIM, N, P2P>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
+          face_flux<T, DIM, N, Q, P2P>(a, mt, rhs, tb, orth, el, k, j % Q, j / Q, F0 + el * PER + k * NF * QF1, QF1);
           continue;
         }
         const int el = w / QV, q = w - el * QV;
@@ -1005,7 +1003,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
         if (eaf || a.kappa) {
           T wk = T(1);
           if (eaf) {
-            const T* gw = tb + TabLayout::GW(N, Q);
+            const T* gw = tb + TabLayout::GW(N, Q, Q);
             T wq = gw[q % Q] * gw[(q / Q) % Q];
             if constexpr (DIM == 3) wq *= gw[q / (Q * Q)];
             lwj *= wq;
@@ -1030,8 +1028,8 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
     }
   }
   __syncthreads();
-  if (fine) lift_fine_faces<T, DIM, N, P2P>(a, t, mt, flist, rhs, tb, F0, PER, orth);
-  const T* DD = tb + TabLayout::DD(N);
+  if (fine) lift_fine_faces<T, DIM, N, Q, P2P>(a, t, mt, flist, rhs, tb, F0, PER, orth);
+  const T* DD = tb + TabLayout::DD(N, Q);
   if constexpr (kGatherScatter) {
     // ScatrInterp: the face points are volume points of the element's boundary
     // planes, so each face adds s to R and c_m t to G_m there; the one
@@ -1098,7 +1096,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   // H = R + sum_m D_m^T G_m + sum_faces [ l(+-1) P + l'(+-1) c_a t ] (into U);
   // with gathered / scattered traces the faces are already in R and G
   {
-    const T* LL = tb + TabLayout::LL(N);
+    const T* LL = tb + TabLayout::LL(N, Q);
     for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
       const int el = w / QV, q = w - el * QV;
       const int qc[3] = {q % Q, (q / Q) % Q, DIM == 3 ? q / (Q * Q) : 0};
@@ -1137,7 +1135,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
     __syncthreads();
   }
   // y = (B^T x B^T (x B^T)) H; the last contraction writes y in global memory
-  const T* BB = tb + TabLayout::BB(N);
+  const T* BB = tb + TabLayout::BB(N, Q);
   auto gy = [&](int el) { return a.y + rhs * a.ndof + mt->dof(el); };
   T* res = nullptr;
   if constexpr (DIM == 2) {
@@ -1152,11 +1150,11 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
     cpt_io<T, N, N, Q, 2, N, false>([&](int el) { return G1 + el * PER; }, gy, ne, BB);
   } else {
     (void)BB;
-    contract<T, Q, Q, Q, 0, N, tab_B(N), true, false>(U, G0, PER, ne);
+    contract<T, Q, Q, Q, 0, N, tab_B(N, Q), true, false>(U, G0, PER, ne);
     __syncthreads();
-    contract<T, N, Q, Q, 1, N, tab_B(N), true, false>(G0, G1, PER, ne);
+    contract<T, N, Q, Q, 1, N, tab_B(N, Q), true, false>(G0, G1, PER, ne);
     __syncthreads();
-    contract<T, N, N, Q, 2, N, tab_B(N), true, false>(G1, G2, PER, ne);
+    contract<T, N, N, Q, 2, N, tab_B(N, Q), true, false>(G1, G2, PER, ne);
     res = G2;
   }
   if constexpr (line_mode<T, DIM>()) {
@@ -1175,26 +1173,37 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
 // of its tiles (table_block_bytes)][descriptors of its largest tile (meta_bytes)][elements].  A CTA runs a list of tiles of one order (its share
 // of the launch, tiles cta_off[b] .. cta_off[b+1]-1) one after the other, with the
 // order's tables loaded once.
-#define SIP_ORDER_SWITCH(FN) \
-  switch (t.n) {             \
-    case 2: FN(2); break;    \
-    case 3: FN(3); break;    \
-    case 4: FN(4); break;    \
-    case 5: FN(5); break;    \
-    case 6: FN(6); break;    \
-    case 7: FN(7); break;    \
-    case 8: FN(8); break;    \
-    case 9: FN(9); break;    \
-    case 10: FN(10); break;  \
-    case 11: FN(11); break;  \
-    default: break;          \
+// The (N, Q) of the CTA's tiles selects the compile-time specialisation: the
+// standard pairs Q = N + 1, and in the Gauss-Lobatto units the extra pairs
+// of kExtraPairs (elements whose points do not follow their order).
+#define SIP_PAIR_KEY(n, q) ((n) * 16 + (q))
+#define SIP_EXTRA_CASES(FN)                                        \
+  case SIP_PAIR_KEY(2, 4): if constexpr (kGatherScatter) FN(2, 4); break; \
+  case SIP_PAIR_KEY(2, 5): if constexpr (kGatherScatter) FN(2, 5); break; \
+  case SIP_PAIR_KEY(3, 5): if constexpr (kGatherScatter) FN(3, 5); break;
+#define SIP_ORDER_SWITCH(FN)                        \
+  switch (SIP_PAIR_KEY(t.n, t.q)) {                 \
+    case SIP_PAIR_KEY(2, 3): FN(2, 3); break;       \
+    case SIP_PAIR_KEY(3, 4): FN(3, 4); break;       \
+    case SIP_PAIR_KEY(4, 5): FN(4, 5); break;       \
+    case SIP_PAIR_KEY(5, 6): FN(5, 6); break;       \
+    case SIP_PAIR_KEY(6, 7): FN(6, 7); break;       \
+    case SIP_PAIR_KEY(7, 8): FN(7, 8); break;       \
+    case SIP_PAIR_KEY(8, 9): FN(8, 9); break;       \
+    case SIP_PAIR_KEY(9, 10): FN(9, 10); break;     \
+    case SIP_PAIR_KEY(10, 11): FN(10, 11); break;   \
+    case SIP_PAIR_KEY(11, 12): FN(11, 12); break;   \
+    SIP_EXTRA_CASES(FN)                             \
+    default: break;                                 \
   }
+static_assert(kNumExtra == 3 && extra_pair(2, 4) == 0 && extra_pair(2, 5) == 1 && extra_pair(3, 5) == 2,
+              "the extra cases of SIP_ORDER_SWITCH list kExtraPairs");
 
-template <typename T, int DIM, int N, bool MAIN, bool P2P>
+template <typename T, int DIM, int N, int Q, bool MAIN, bool P2P>
 __device__ __forceinline__ void run_tiles(const ApplyArgs<T>& a, int ti0, int ti1, int rhs, unsigned char* smem_raw) {
   // finest face rule and largest tile of the CTA's tiles: the extents of its
   // table block and descriptor block
-  int fmax = N + 1, cmax = 1;
+  int fmax = Q, cmax = 1;
   bool force = false;
   for (int ti = ti0; ti < ti1; ++ti) {
     const Tile t = a.tiles[ti];
@@ -1202,20 +1211,20 @@ __device__ __forceinline__ void run_tiles(const ApplyArgs<T>& a, int ti0, int ti
     cmax = max(cmax, t.count);
     force = force || (t.flags & kTileForce);
   }
-  const int tbytes = table_block_bytes(sizeof(T), N, fmax);
+  const int tbytes = table_block_bytes(sizeof(T), N, Q, fmax);
   T* tb = reinterpret_cast<T*>(smem_raw);
   TileMeta<DIM> meta;
   meta.e_ = reinterpret_cast<ElemDesc*>(smem_raw + tbytes);
   meta.s_ = reinterpret_cast<SlotDesc*>(meta.e_ + cmax);
   TileMeta<DIM>* mt = &meta;
   T* sm = reinterpret_cast<T*>(smem_raw + tbytes + meta_bytes(DIM, cmax));
-  load_tables<T, N>(tb, fmax, force);
+  load_tables<T, N, Q>(tb, fmax, force);
   grid_dep_wait();  // before anything that another kernel writes
   for (int ti = ti0; ti < ti1; ++ti) {
     if (ti > ti0) __syncthreads();  // the previous tile's last stage still reads shared memory
     const Tile t = a.tiles[ti];
-    if constexpr (MAIN) main_tile<T, DIM, N, P2P>(a, t, rhs, tb, mt, sm);
-    else trace_tile<T, DIM, N, P2P>(a, t, rhs, tb, mt, sm);
+    if constexpr (MAIN) main_tile<T, DIM, N, Q, P2P>(a, t, rhs, tb, mt, sm);
+    else trace_tile<T, DIM, N, Q, P2P>(a, t, rhs, tb, mt, sm);
   }
 }
 
@@ -1230,8 +1239,8 @@ __global__ void __launch_bounds__(256) k_trace(ApplyArgs<T> a) {
   grid_dep_launch_next();  // k_main may load its tables meanwhile
   const int ti0 = a.cta_off[blockIdx.x], ti1 = a.cta_off[blockIdx.x + 1];
   if (ti0 >= ti1) return;
-  const Tile t = a.tiles[ti0];  // every tile of the CTA has this order
-#define SIP_TRACE_CASE(NN) run_tiles<T, DIM, NN, false, P2P>(a, ti0, ti1, blockIdx.y, smem_raw)
+  const Tile t = a.tiles[ti0];  // every tile of the CTA has this (N, Q)
+#define SIP_TRACE_CASE(NN, QQ) run_tiles<T, DIM, NN, QQ, false, P2P>(a, ti0, ti1, blockIdx.y, smem_raw)
   SIP_ORDER_SWITCH(SIP_TRACE_CASE)
 #undef SIP_TRACE_CASE
 }
@@ -1251,7 +1260,7 @@ __global__ void __launch_bounds__(SIP_MAIN_LAUNCH_BOUNDS) k_main(ApplyArgs<T> a)
   const int ti0 = a.cta_off[blockIdx.x], ti1 = a.cta_off[blockIdx.x + 1];
   if (ti0 >= ti1) return;
   const Tile t = a.tiles[ti0];
-#define SIP_MAIN_CASE(NN) run_tiles<T, DIM, NN, true, P2P>(a, ti0, ti1, blockIdx.y, smem_raw)
+#define SIP_MAIN_CASE(NN, QQ) run_tiles<T, DIM, NN, QQ, true, P2P>(a, ti0, ti1, blockIdx.y, smem_raw)
   SIP_ORDER_SWITCH(SIP_MAIN_CASE)
 #undef SIP_MAIN_CASE
 }

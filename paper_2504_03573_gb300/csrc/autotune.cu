@@ -49,7 +49,7 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
   // coordinate descent over the orders, each candidate timed on the full apply
   // (all buckets in one launch, as the solver runs it)
   int cur[kNMax + 2] = {};
-  for (int n : orders) cur[n] = apply_epb(p.dim, n, precision, 256);
+  for (int n : orders) cur[n] = apply_epb(p.dim, n, n + 1, precision, 256);
   const bool timing = h->timing;
   h->timing = false;
   auto time_full = [&](const int* epb, int per_sm, bool pers, int threads, float* ms_out, int* per_sm_out) -> int {
@@ -90,8 +90,11 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
   for (int n : orders) {
     if (rc) break;
     const int base = cur[n];
-    const int per = std::max(per_elem_trace(p.dim, n), per_elem_main(p.dim, n)) * es;
-    const int room = (160 * 1024 - table_block_bytes(es, n) - kMetaBytes) / per;
+    int qmax = n + 1;  // the largest point count among the elements of this order
+    for (size_t e = 0; e < p.P.size(); ++e)
+      if (p.P[e] + 1 == n) qmax = std::max(qmax, (int)p.Q[e]);
+    const int per = std::max(per_elem_trace(p.dim, n, qmax), per_elem_main(p.dim, n, qmax)) * es;
+    const int room = (160 * 1024 - table_block_bytes(es, n, qmax) - kMetaBytes) / per;
     std::set<int> cand;
     for (int c : {base / 4, base / 2, 2 * base, 4 * base}) cand.insert(std::max(1, std::min({c, room, kMaxEpb})));
     cand.erase(base);
@@ -152,7 +155,7 @@ extern "C" int sip_get_tiling(const sip_handle* h, int precision, sip_tiling* ou
   std::memset(out, 0, sizeof(*out));
   for (const Tile& t : h->tiles_h[pi]) {
     const int set = h->epb[pi][t.n];
-    out->epb[t.n - 1] = std::min(kMaxEpb, set > 0 ? set : apply_epb(h->plan.dim, t.n, precision, h->threads[pi]));
+    out->epb[t.n - 1] = std::min(kMaxEpb, set > 0 ? set : apply_epb(h->plan.dim, t.n, t.q, precision, h->threads[pi]));
   }
   out->ctas_per_sm = h->ctas_per_sm[pi];
   out->persistent = h->persistent[pi];

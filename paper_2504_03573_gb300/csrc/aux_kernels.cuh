@@ -1,7 +1,7 @@
 // Auxiliary per-element FP64 kernels: kappa gradient, mass inner product, IProduct.
 #pragma once
 
-#include "common.cuh"
+#include "apply_kernels.cuh"
 
 namespace sip {
 
@@ -23,15 +23,15 @@ struct AuxArgs {
   int mode;  // 0: kappa gradient, 1: mass dot partials (one per tile), 2: IProduct
 };
 
-inline int aux_smem_per_element(int dim, int n) {
-  const int q = n + 1;
+inline int aux_smem_per_element(int dim, int n, int q) {
+  (void)n;
   const int qv = dim == 2 ? q * q : q * q * q;
   return 2 * (dim + 1) * qv;
 }
 
 // load N^DIM coefficients of vector v into U (via scratch S) and interpolate to
 // the Gauss points: result in U.
-template <int DIM, int N>
+template <int DIM, int N, int Q>
 __device__ __forceinline__ void load_to_gauss(const AuxArgs& a, const Tile& t, const double* v,
                                               double* U, double* S, int per) {
   constexpr int NV = ipow(N, DIM);
@@ -42,13 +42,12 @@ __device__ __forceinline__ void load_to_gauss(const AuxArgs& a, const Tile& t, c
     dst[el * per + i] = v[a.dof_off[e] + i];
   }
   __syncthreads();
-  if constexpr (DIM == 2) to_gauss<double, 2, N>(U, S, per, t.count);
-  else to_gauss<double, 3, N>(S, U, per, t.count);
+  if constexpr (DIM == 2) to_gauss<double, 2, N, Q>(U, S, per, t.count);
+  else to_gauss<double, 3, N, Q>(S, U, per, t.count);
 }
 
-template <int DIM, int N>
+template <int DIM, int Q>
 __device__ __forceinline__ void gauss_grad(const double* U, double* G0, double* G1, double* G2, int per, int ne) {
-  constexpr int Q = N + 1;
   if constexpr (DIM == 2) {
     contract<double, Q, Q, 1, 0, Q, tab_D(Q), false, false>(U, G0, per, ne);
     contract<double, Q, Q, 1, 1, Q, tab_D(Q), false, false>(U, G1, per, ne);
@@ -72,9 +71,9 @@ __device__ __forceinline__ double vfac(const AuxArgs& a, int e, int q, int comp)
   return w * g[comp];
 }
 
-template <int DIM, int N>
+template <int DIM, int N, int Q>
 __device__ void aux_tile(const AuxArgs& a, const Tile& t, double* sm) {
-  constexpr int Q = N + 1, QV = ipow(Q, DIM), NV = ipow(N, DIM);
+  constexpr int QV = ipow(Q, DIM), NV = ipow(N, DIM);
   constexpr int PER = 2 * (DIM + 1) * QV;
   const int ne = t.count;
   double* Ua = sm;
@@ -82,10 +81,10 @@ __device__ void aux_tile(const AuxArgs& a, const Tile& t, double* sm) {
   double* Ub = sm + (DIM + 1) * QV;
   double* Gb = sm + (DIM + 2) * QV;     // DIM buffers
   if (a.mode == 0) {
-    load_to_gauss<DIM, N>(a, t, a.a, Ua, Ga, PER);
-    gauss_grad<DIM, N>(Ua, Ga, Ga + QV, Ga + 2 * QV, PER, ne);
-    load_to_gauss<DIM, N>(a, t, a.b, Ub, Gb, PER);
-    gauss_grad<DIM, N>(Ub, Gb, Gb + QV, Gb + 2 * QV, PER, ne);
+    load_to_gauss<DIM, N, Q>(a, t, a.a, Ua, Ga, PER);
+    gauss_grad<DIM, Q>(Ua, Ga, Ga + QV, Ga + 2 * QV, PER, ne);
+    load_to_gauss<DIM, N, Q>(a, t, a.b, Ub, Gb, PER);
+    gauss_grad<DIM, Q>(Ub, Gb, Gb + QV, Gb + 2 * QV, PER, ne);
     for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
       const int el = w / QV, q = w - el * QV;
       const int e = a.elist[t.start + el];
@@ -106,8 +105,8 @@ __device__ void aux_tile(const AuxArgs& a, const Tile& t, double* sm) {
       *o = a.accumulate ? *o + v : v;
     }
   } else if (a.mode == 1) {
-    load_to_gauss<DIM, N>(a, t, a.a, Ua, Ga, PER);
-    load_to_gauss<DIM, N>(a, t, a.b, Ub, Gb, PER);
+    load_to_gauss<DIM, N, Q>(a, t, a.a, Ua, Ga, PER);
+    load_to_gauss<DIM, N, Q>(a, t, a.b, Ub, Gb, PER);
     double s = 0.0;
     constexpr int WJ = DIM == 2 ? 3 : 6;
     for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
@@ -137,16 +136,16 @@ __device__ void aux_tile(const AuxArgs& a, const Tile& t, double* sm) {
     double* t2 = Ga + QV;
     double* res;
     if constexpr (DIM == 2) {
-      contract<double, Q, Q, 1, 0, N, tab_B(N), true, false>(Ua, t1, PER, ne);
+      contract<double, Q, Q, 1, 0, N, tab_B(N, Q), true, false>(Ua, t1, PER, ne);
       __syncthreads();
-      contract<double, N, Q, 1, 1, N, tab_B(N), true, false>(t1, t2, PER, ne);
+      contract<double, N, Q, 1, 1, N, tab_B(N, Q), true, false>(t1, t2, PER, ne);
       res = t2;
     } else {
-      contract<double, Q, Q, Q, 0, N, tab_B(N), true, false>(Ua, t1, PER, ne);
+      contract<double, Q, Q, Q, 0, N, tab_B(N, Q), true, false>(Ua, t1, PER, ne);
       __syncthreads();
-      contract<double, N, Q, Q, 1, N, tab_B(N), true, false>(t1, t2, PER, ne);
+      contract<double, N, Q, Q, 1, N, tab_B(N, Q), true, false>(t1, t2, PER, ne);
       __syncthreads();
-      contract<double, N, N, Q, 2, N, tab_B(N), true, false>(t2, t1, PER, ne);
+      contract<double, N, N, Q, 2, N, tab_B(N, Q), true, false>(t2, t1, PER, ne);
       res = t1;
     }
     __syncthreads();
@@ -165,19 +164,9 @@ __global__ void __launch_bounds__(256) k_aux(AuxArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* sm = reinterpret_cast<double*>(smem_raw);
   const Tile t = a.tiles[blockIdx.x];
-  switch (t.n) {
-    case 2: aux_tile<DIM, 2>(a, t, sm); break;
-    case 3: aux_tile<DIM, 3>(a, t, sm); break;
-    case 4: aux_tile<DIM, 4>(a, t, sm); break;
-    case 5: aux_tile<DIM, 5>(a, t, sm); break;
-    case 6: aux_tile<DIM, 6>(a, t, sm); break;
-    case 7: aux_tile<DIM, 7>(a, t, sm); break;
-    case 8: aux_tile<DIM, 8>(a, t, sm); break;
-    case 9: aux_tile<DIM, 9>(a, t, sm); break;
-    case 10: aux_tile<DIM, 10>(a, t, sm); break;
-    case 11: aux_tile<DIM, 11>(a, t, sm); break;
-    default: break;
-  }
+#define SIP_AUX_CASE(NN, QQ) aux_tile<DIM, NN, QQ>(a, t, sm)
+  SIP_ORDER_SWITCH(SIP_AUX_CASE)
+#undef SIP_AUX_CASE
 }
 
 }  // namespace sip

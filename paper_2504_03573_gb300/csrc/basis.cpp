@@ -107,13 +107,14 @@ void point_rule(int rule, int q, std::vector<double>& x, std::vector<double>& w)
 void fill_tables(int rule, std::vector<double>& tab) {
   tab.assign(kTabSize, 0.0);
   std::vector<double> xg, wg, xl, wl, xf, wf;
-  for (int N = kNMin; N <= kNMax; ++N) {
-    const int Q = N + 1;
+  auto fill_b = [&](int N, int Q) {
     gauss_lobatto(N, xl, wl);
     point_rule(rule, Q, xg, wg);
     for (int q = 0; q < Q; ++q)
-      for (int i = 0; i < N; ++i) tab[tab_B(N) + q * N + i] = lagrange(xl, i, xg[q]);
-  }
+      for (int i = 0; i < N; ++i) tab[tab_B(N, Q) + q * N + i] = lagrange(xl, i, xg[q]);
+  };
+  for (int N = kNMin; N <= kNMax; ++N) fill_b(N, N + 1);
+  for (int i = 0; i < kNumExtra; ++i) fill_b(kExtraPairs[i].n, kExtraPairs[i].q);
   for (int Q = kQMin; Q <= kQMax; ++Q) {
     point_rule(rule, Q, xg, wg);
     for (int q = 0; q < Q; ++q)

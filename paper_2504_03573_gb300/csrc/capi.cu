@@ -29,15 +29,14 @@ int cuda_fail(cudaError_t e, const char* where) {
 // Elements per tile: enough work items per CTA to keep its threads busy in every
 // stage (Gauss points in 2D, lines of Gauss points in 3D), within 64 KB of
 // shared memory.
-int apply_epb(int dim, int n, int precision, int threads) {
-  const int q = n + 1;
+int apply_epb(int dim, int n, int q, int precision, int threads) {
   // one Gauss point per work item (2D; FP64 in 3D) or one line of Q points (FP32 in 3D)
   const bool lines = dim == 3 && precision == SIP_FP32;
   const int items = lines ? q * q : (dim == 2 ? q * q : q * q * q);
   int epb = std::max(1, (dim == 3 && !lines ? 3 * threads / 2 : threads) / items);
   const int es = precision == SIP_FP32 ? 4 : 8;
-  const int per = std::max(per_elem_trace(dim, n), per_elem_main(dim, n)) * es;
-  const int room = (64 * 1024 - table_block_bytes(es, n) - kMetaBytes) / per;
+  const int per = std::max(per_elem_trace(dim, n, q), per_elem_main(dim, n, q)) * es;
+  const int room = (64 * 1024 - table_block_bytes(es, n, q) - kMetaBytes) / per;
   return std::max(1, std::min(std::min(epb, room), kMaxEpb));
 }
 
@@ -190,17 +189,17 @@ int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_p
     s.smem_t = s.smem_m = 0;
     for (size_t c = 0; c + 1 < s.cta_off.size(); ++c) {
       if (s.cta_off[c] == s.cta_off[c + 1]) continue;
-      const int n = s.tiles[s.cta_off[c]].n;
-      int fmax = n + 1, cmax = 1;
+      const int n = s.tiles[s.cta_off[c]].n, q = s.tiles[s.cta_off[c]].q;
+      int fmax = q, cmax = 1;
       for (int32_t ti = s.cta_off[c]; ti < s.cta_off[c + 1]; ++ti) {
         fmax = std::max(fmax, s.tiles[ti].flags & kTileQfMask);
         cmax = std::max(cmax, (int)s.tiles[ti].count);
       }
-      const size_t fixed = (size_t)table_block_bytes(es, n, fmax) + meta_bytes(p.dim, cmax);
+      const size_t fixed = (size_t)table_block_bytes(es, n, q, fmax) + meta_bytes(p.dim, cmax);
       for (int32_t ti = s.cta_off[c]; ti < s.cta_off[c + 1]; ++ti) {
         const Tile& t = s.tiles[ti];
-        s.smem_t = std::max(s.smem_t, fixed + (size_t)t.count * per_elem_trace(p.dim, t.n) * es);
-        s.smem_m = std::max(s.smem_m, fixed + (size_t)t.count * per_elem_main(p.dim, t.n) * es +
+        s.smem_t = std::max(s.smem_t, fixed + (size_t)t.count * per_elem_trace(p.dim, t.n, t.q) * es);
+        s.smem_m = std::max(s.smem_m, fixed + (size_t)t.count * per_elem_main(p.dim, t.n, t.q) * es +
                                           (precision == SIP_FP64 ? kFaceListBytes : 0));
       }
     }
@@ -390,6 +389,7 @@ void sip_options_default(sip_options* o) {
   o->face_scheme = SIP_FACES_SHARED;
   o->quad_rule = SIP_RULE_GAUSS;
   o->force_interp = 0;
+  o->qorders = nullptr;
 }
 
 struct sip_plan {

@@ -148,21 +148,20 @@ __device__ __forceinline__ void contract(const T* __restrict__ in, T* __restrict
 
 // GLL coefficients -> Gauss values.  in: buffers bA (holding N^DIM coefficients),
 // scratch bB; returns pointer (bA or bB) holding Q^DIM values.
-template <typename T, int DIM, int N>
+template <typename T, int DIM, int N, int Q>
 __device__ __forceinline__ T* to_gauss(T* bA, T* bB, int stride, int ne) {
-  constexpr int Q = N + 1;
   if constexpr (DIM == 2) {
-    contract<T, N, N, 1, 0, Q, tab_B(N), false, false>(bA, bB, stride, ne);
+    contract<T, N, N, 1, 0, Q, tab_B(N, Q), false, false>(bA, bB, stride, ne);
     __syncthreads();
-    contract<T, Q, N, 1, 1, Q, tab_B(N), false, false>(bB, bA, stride, ne);
+    contract<T, Q, N, 1, 1, Q, tab_B(N, Q), false, false>(bB, bA, stride, ne);
     __syncthreads();
     return bA;
   } else {
-    contract<T, N, N, N, 0, Q, tab_B(N), false, false>(bA, bB, stride, ne);
+    contract<T, N, N, N, 0, Q, tab_B(N, Q), false, false>(bA, bB, stride, ne);
     __syncthreads();
-    contract<T, Q, N, N, 1, Q, tab_B(N), false, false>(bB, bA, stride, ne);
+    contract<T, Q, N, N, 1, Q, tab_B(N, Q), false, false>(bB, bA, stride, ne);
     __syncthreads();
-    contract<T, Q, Q, N, 2, Q, tab_B(N), false, false>(bA, bB, stride, ne);
+    contract<T, Q, Q, N, 2, Q, tab_B(N, Q), false, false>(bA, bB, stride, ne);
     __syncthreads();
     return bB;
   }

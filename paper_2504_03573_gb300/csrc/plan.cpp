@@ -186,10 +186,22 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
     }
   }
   p.P.assign(orders, orders + E);
+  // volume points per direction: P + 2, or the caller's per-element counts
+  p.Q.resize(E);
+  for (int64_t e = 0; e < E; ++e) {
+    const int q = opt.qorders ? opt.qorders[e] : p.P[e] + 2;
+    if (!pair_supported(opt.quad_rule, p.P[e] + 1, q)) {
+      err = "element " + std::to_string(e) + ": " + std::to_string(q) + " points per direction for order " +
+            std::to_string(p.P[e]) + " is not supported with this rule (P + 2 always; with Gauss-Lobatto points "
+            "also (P, Q) = (1, 4), (1, 5), (2, 5))";
+      return SIP_ERR_ARG;
+    }
+    p.Q[e] = q;
+  }
   p.dof_off.assign(E + 1, 0);
   p.quad_off.assign(E + 1, 0);
   for (int64_t e = 0; e < E; ++e) {
-    int64_t n = p.P[e] + 1, q = p.P[e] + 2;
+    int64_t n = p.P[e] + 1, q = p.Q[e];
     p.dof_off[e + 1] = p.dof_off[e] + (dim == 2 ? n * n : n * n * n);
     p.quad_off[e + 1] = p.quad_off[e] + (dim == 2 ? q * q : q * q * q);
   }
@@ -214,7 +226,7 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
   p.affine.assign(E, 0);
   int vrc = parallel_chunks(E, [&](int64_t e0, int64_t e1, std::string& verr) -> int {
   for (int64_t e = e0; e < e1; ++e) {
-    const int Q = p.P[e] + 2;
+    const int Q = p.Q[e];
     const std::vector<double>& xg = rules.x[Q];
     const std::vector<double>& wg = rules.w[Q];
     const double* v = &ev[(size_t)e * nc * dim];
@@ -325,8 +337,8 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
   for (int64_t f = 0; f < F; ++f) {
     const Pair& pr = f < p.n_int ? inter[f] : bnd[f - p.n_int];
     p.f_em[f] = pr.em; p.f_km[f] = pr.km; p.f_ep[f] = pr.ep; p.f_kp[f] = pr.kp;
-    const int qm = p.P[pr.em] + 2;
-    const int qp = pr.ep >= 0 ? p.P[pr.ep] + 2 : qm;
+    const int qm = p.Q[pr.em];
+    const int qp = pr.ep >= 0 ? p.Q[pr.ep] : qm;
     const int qf = std::max(qm, qp);
     p.f_qf[f] = qf;
     if (pr.ep >= 0 && p.P[pr.ep] != p.P[pr.em]) ++p.n_nonconf;
@@ -473,7 +485,7 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
     const double area = eval_face(f, qf, sg, sg + npts, ep >= 0 ? sg + (1 + dim) * npts : nullptr);
     bool ok = area > 0.0;
     if (own && ok) {
-      const int qm = p.P[em] + 2, qp = p.P[ep] + 2;
+      const int qm = p.Q[em], qp = p.Q[ep];
       const int npm = dim == 2 ? qm : qm * qm, npp = dim == 2 ? qp : qp * qp;
       ok = eval_face(f, qm, fg, fg + npm, nullptr) > 0.0;
       double* fp = fg + (1 + dim) * npm;
@@ -525,7 +537,7 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
       const int64_t nq = p.quad_off[e + 1] - p.quad_off[e];
       const double* src = &p.vgeo[p.vgoff[e]];
       if (p.affine[e]) {
-        const std::vector<double>& wq = rules.w[p.P[e] + 2];
+        const std::vector<double>& wq = rules.w[p.Q[e]];
         double w0 = 1.0;
         for (int k = 0; k < dim; ++k) w0 *= wq[0];
         for (int c = 0; c < nG; ++c) vg[vnew[e] + c] = src[c * nq] / w0;
@@ -552,7 +564,7 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
       if (faff[f] && p2p && p.f_ep[f] >= 0) {
         // own rules: [W-, c-] at Q- points, [W+, c+] at Q+ points -> the same
         // constants as a shared face (W without the weight, c-, c+)
-        const int qm = p.P[p.f_em[f]] + 2, qp = p.P[p.f_ep[f]] + 2;
+        const int qm = p.Q[p.f_em[f]], qp = p.Q[p.f_ep[f]];
         const int npm = dim == 2 ? qm : qm * qm, npp = dim == 2 ? qp : qp * qp;
         const std::vector<double>& wq = rules.w[qm];
         const double wz = dim == 2 ? wq[0] : wq[0] * wq[0];
@@ -581,8 +593,9 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
   // ---- elements sorted by order (the paper's element groups)
   p.elist.resize(E);
   std::iota(p.elist.begin(), p.elist.end(), 0);
-  std::stable_sort(p.elist.begin(), p.elist.end(),
-                   [&](int32_t a, int32_t b) { return p.P[a] < p.P[b]; });
+  std::stable_sort(p.elist.begin(), p.elist.end(), [&](int32_t a, int32_t b) {
+    return p.P[a] != p.P[b] ? p.P[a] < p.P[b] : p.Q[a] < p.Q[b];
+  });
   p.desc_e.resize(E);
   p.desc_s.resize((size_t)E * nf);
   for (int64_t i = 0; i < E; ++i) {
@@ -600,7 +613,7 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
 // of the apply and the cost that the CTA schedule balances.
 void element_flops(const Plan& p, int64_t e, double& ft, double& fm) {
   const int d = p.dim;
-  const double N = p.P[e] + 1, Q = N + 1;
+  const double N = p.P[e] + 1, Q = p.Q[e];
   const double QV = d == 2 ? Q * Q : Q * Q * Q;
   const double QF1 = d == 2 ? Q : Q * Q;
   // one sum-factorised interpolation GLL -> Gauss
@@ -641,9 +654,10 @@ void element_flops(const Plan& p, int64_t e, double& ft, double& fm) {
 
 namespace {
 
-// tile of elist[s0, s1) (order n - 1) with its face list appended to fl
-Tile make_tile(const Plan& p, int n, int64_t s0, int64_t s1, std::vector<uint16_t>& fl) {
-  int qfm = n + 1;
+// tile of elist[s0, s1) (n nodes and q points per direction) with its face list
+// appended to fl
+Tile make_tile(const Plan& p, int n, int q, int64_t s0, int64_t s1, std::vector<uint16_t>& fl) {
+  int qfm = q;
   bool orth = true;
   const bool force = p.opt.force_interp != 0;
   std::vector<uint16_t> conf, fine;
@@ -653,7 +667,7 @@ Tile make_tile(const Plan& p, int n, int64_t s0, int64_t s1, std::vector<uint16_
       qfm = std::max(qfm, (int)sl.qf);
       orth = orth && (sl.flags & kFaceOrth);
       const uint16_t e = (uint16_t)((s - s0) | (f << 5) | (sl.qf << 8));
-      (sl.qf == n + 1 && !force ? conf : fine).push_back(e);
+      (sl.qf == q && !force ? conf : fine).push_back(e);
     }
   std::stable_sort(fine.begin(), fine.end(), [](uint16_t a, uint16_t b) { return fl_qf(a) < fl_qf(b); });
   std::vector<std::pair<int, int>> groups;  // (qf, count)
@@ -671,8 +685,8 @@ Tile make_tile(const Plan& p, int n, int64_t s0, int64_t s1, std::vector<uint16_
   }
   fl.insert(fl.end(), conf.begin(), conf.end());
   fl.insert(fl.end(), fine.begin(), fine.end());
-  const int flags = qfm | (qfm > n + 1 || force ? kTileFine : 0) | (orth ? kTileOrth : 0) | (force ? kTileForce : 0);
-  return Tile{n, (int32_t)s0, (int32_t)(s1 - s0), flags, off};
+  const int flags = qfm | (qfm > q || force ? kTileFine : 0) | (orth ? kTileOrth : 0) | (force ? kTileForce : 0);
+  return Tile{n, q, (int32_t)s0, (int32_t)(s1 - s0), flags, off};
 }
 
 }  // namespace
@@ -702,11 +716,12 @@ void build_tiles(const Plan& p, int precision, const int* epb_override, int thre
     C += ce[i];
   }
   for (int64_t i = 0; i < E;) {
-    const int n = p.P[p.elist[i]] + 1;
+    // a run of elements with the same (N, Q)
+    const int n = p.P[p.elist[i]] + 1, q = p.Q[p.elist[i]];
     int64_t j = i;
     double Cn = 0.0;
-    while (j < E && p.P[p.elist[j]] + 1 == n) Cn += ce[j++];
-    int epb = epb_override && epb_override[n] > 0 ? epb_override[n] : apply_epb(p.dim, n, precision, threads);
+    while (j < E && p.P[p.elist[j]] + 1 == n && p.Q[p.elist[j]] == q) Cn += ce[j++];
+    int epb = epb_override && epb_override[n] > 0 ? epb_override[n] : apply_epb(p.dim, n, q, precision, threads);
     epb = std::max(1, std::min(epb, kMaxEpb));
     const int64_t cnt = j - i;
     const int64_t share = nctas > 0 ? std::max<int64_t>(1, std::llround(nctas * Cn / C)) : 0;
@@ -717,7 +732,8 @@ void build_tiles(const Plan& p, int precision, const int* epb_override, int thre
     for (int64_t c = 0; c < kc; ++c) {
       const int64_t r0 = i + (cnt * c) / kc, r1 = i + (cnt * (c + 1)) / kc;
       const int64_t m = r1 - r0, nt = (m + epb - 1) / epb;
-      for (int64_t k = 0; k < nt; ++k) tiles.push_back(make_tile(p, n, r0 + (m * k) / nt, r0 + (m * (k + 1)) / nt, flists));
+      for (int64_t k = 0; k < nt; ++k)
+        tiles.push_back(make_tile(p, n, q, r0 + (m * k) / nt, r0 + (m * (k + 1)) / nt, flists));
       cta_off.push_back((int32_t)tiles.size());
     }
     i = j;

@@ -25,14 +25,40 @@ constexpr int kQMax = kNMax + 1;          // 12; also the largest face rule
 //   L_Q   [4][Q]  rows l_r(-1), l_r(+1), l_r'(-1), l_r'(+1) of the rule's Lagrange basis
 //   I_Q,F [F][Q]  I[z][r]  = l^R_Q,r (xi^R_F,z), F in Q..kQMax (face rule interpolation;
 //                 F = Q is the identity, used when interpolation is forced on every face)
-// with Q = N + 1.
+// B for Q = N + 1 (the standard (P+2)-point rules) and for the extra (N, Q) pairs
+// below; D, L and I for every Q.
 // ---------------------------------------------------------------------------
-constexpr int tab_B(int N) {
+
+// Elements whose points do not follow their order (Q != N + 1): the pairs the
+// Gauss-Lobatto kernels are also built for.  They carry the transition layer of
+// Sec. 3.3 (the coefficients of one order, the points of a higher one, e.g.
+// P2Q5 between P4Q5 and P2Q3 in the paper's counts) and Table 2's P3Q5.
+struct NQ { int n, q; };
+constexpr NQ kExtraPairs[] = {{2, 4}, {2, 5}, {3, 5}};
+constexpr int kNumExtra = (int)(sizeof(kExtraPairs) / sizeof(kExtraPairs[0]));
+constexpr int extra_pair(int n, int q) {
+  for (int i = 0; i < kNumExtra; ++i)
+    if (kExtraPairs[i].n == n && kExtraPairs[i].q == q) return i;
+  return -1;
+}
+// an (N, Q) pair the kernels of a rule are built for
+constexpr bool pair_supported(int rule, int n, int q) {
+  return (q == n + 1 && n >= kNMin && n <= kNMax) || (rule == SIP_RULE_GLL && extra_pair(n, q) >= 0);
+}
+
+constexpr int tab_B(int N, int Q) {
   int off = 0;
-  for (int n = kNMin; n < N; ++n) off += (n + 1) * n;
+  if (Q == N + 1) {
+    for (int n = kNMin; n < N; ++n) off += (n + 1) * n;
+    return off;
+  }
+  for (int n = kNMin; n <= kNMax; ++n) off += (n + 1) * n;
+  for (int i = 0; i < kNumExtra && !(kExtraPairs[i].n == N && kExtraPairs[i].q == Q); ++i)
+    off += kExtraPairs[i].n * kExtraPairs[i].q;
   return off;
 }
-constexpr int kTabBEnd = tab_B(kNMax + 1);
+constexpr int tab_B(int N) { return tab_B(N, N + 1); }
+constexpr int kTabBEnd = tab_B(0, 0);   // past the last extra pair
 constexpr int tab_D(int Q) {
   int off = kTabBEnd;
   for (int q = kQMin; q < Q; ++q) off += q * q;
@@ -60,8 +86,8 @@ constexpr int kTabSize = tab_I(kQMax + 1, kQMax + 2);
 // Shared-memory layout of the apply kernels (host computes launch sizes, device
 // indexes with the same constexpr functions).
 //
-// Per-CTA table block for one order (N, Q = N + 1), laid out so that a warp whose
-// lanes compute consecutive outputs reads consecutive addresses:
+// Per-CTA table block for one (N, Q), laid out so that a warp whose lanes compute
+// consecutive outputs reads consecutive addresses:
 //   BT [N][Q]  B[q][i] at i*Q + q      forward interpolation nodes -> rule points
 //   BB [Q][N]  B[q][i] at q*N + i      transposed interpolation
 //   DT [Q][Q]  D[q][r] at r*Q + q      collocation derivative
@@ -73,25 +99,25 @@ constexpr int kTabSize = tab_I(kQMax + 1, kQMax + 2);
 // tiles: the element buffers follow at table_block_bytes(bytes, n, fmax).
 // ---------------------------------------------------------------------------
 struct TabLayout {
-  static constexpr int BT(int) { return 0; }
-  static constexpr int BB(int n) { return n * (n + 1); }
-  static constexpr int DT(int n) { return 2 * n * (n + 1); }
-  static constexpr int DD(int n) { return DT(n) + (n + 1) * (n + 1); }
-  static constexpr int LL(int n) { return DD(n) + (n + 1) * (n + 1); }
+  static constexpr int BT(int, int) { return 0; }
+  static constexpr int BB(int n, int q) { return n * q; }
+  static constexpr int DT(int n, int q) { return 2 * n * q; }
+  static constexpr int DD(int n, int q) { return DT(n, q) + q * q; }
+  static constexpr int LL(int n, int q) { return DD(n, q) + q * q; }
   // weights of the F-point rules, F = Q .. kQMax (affine geometry)
-  static constexpr int GW(int n, int f) {
-    int o = LL(n) + 4 * (n + 1);
-    for (int g = n + 1; g < f; ++g) o += g;
+  static constexpr int GW(int n, int q, int f) {
+    int o = LL(n, q) + 4 * q;
+    for (int g = q; g < f; ++g) o += g;
     return o;
   }
-  static constexpr int IT(int n, int f) {
-    int o = GW(n, kQMax + 1);
-    for (int g = n + 1; g < f; ++g) o += 2 * g * (n + 1);
+  static constexpr int IT(int n, int q, int f) {
+    int o = GW(n, q, kQMax + 1);
+    for (int g = q; g < f; ++g) o += 2 * g * q;
     return o;
   }
-  static constexpr int II(int n, int f) { return IT(n, f) + f * (n + 1); }
+  static constexpr int II(int n, int q, int f) { return IT(n, q, f) + f * q; }
   // entries up to and including the interpolation to the fmax-point rule
-  static constexpr int size(int n, int fmax) { return IT(n, fmax + 1); }
+  static constexpr int size(int n, int q, int fmax) { return IT(n, q, fmax + 1); }
 };
 
 constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * cpow(b, e - 1); }
@@ -102,16 +128,17 @@ constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * cpow(b, e - 1); }
 // [slots][fields][FT + kQMax^(dim-1)] (FT = kQMax Q in 3D, 0 in 2D): one slot per
 // face in 2D (all processed together), one slot in 3D (one face at a time)
 constexpr int scratch_slots(int dim) { return dim == 2 ? 4 : 1; }
-constexpr int face_buf(int dim, int n, int fields) {
-  return 2 * dim * fields * cpow(n + 1, dim - 1) +
-         scratch_slots(dim) * fields * ((dim == 3 ? kQMax * (n + 1) : 0) + cpow(kQMax, dim - 1));
+constexpr int face_buf(int dim, int q, int fields) {
+  return 2 * dim * fields * cpow(q, dim - 1) +
+         scratch_slots(dim) * fields * ((dim == 3 ? kQMax * q : 0) + cpow(kQMax, dim - 1));
 }
-constexpr int per_elem_trace(int dim, int n) { return 2 * cpow(n + 1, dim) + face_buf(dim, n, 4); }
-constexpr int per_elem_main(int dim, int n) { return (2 + dim) * cpow(n + 1, dim) + face_buf(dim, n, 1 + dim); }
+// (the volume buffers hold Q^dim values; N <= Q, so the N^dim coefficients fit)
+constexpr int per_elem_trace(int dim, int n, int q) { return (void)n, 2 * cpow(q, dim) + face_buf(dim, q, 4); }
+constexpr int per_elem_main(int dim, int n, int q) { return (void)n, (2 + dim) * cpow(q, dim) + face_buf(dim, q, 1 + dim); }
 // bytes of the CTA's table block (padded to 16) that precedes the element buffers,
 // for tiles whose finest face rule is fmax (at most kQMax)
-constexpr int table_block_bytes(int bytes_per, int n, int fmax = kQMax) {
-  return ((TabLayout::size(n, fmax) * bytes_per + 15) / 16) * 16;
+constexpr int table_block_bytes(int bytes_per, int n, int q, int fmax = kQMax) {
+  return ((TabLayout::size(n, q, fmax) * bytes_per + 15) / 16) * 16;
 }
 
 // ---------------------------------------------------------------------------
@@ -147,6 +174,7 @@ constexpr int kMaxEpb = 32;        // elements per tile, at most
 
 struct Tile {
   int32_t n;       // nodes per direction (P + 1) of every element of the tile
+  int32_t q;       // volume points per direction of every element of the tile
   int32_t start;   // first index into the order-sorted element list
   int32_t count;   // elements in the tile
   int32_t flags;   // kTileQfMask | kTileFine | kTileOrth | kTileForce
@@ -196,6 +224,7 @@ struct Plan {
   int64_t E = 0, ndof = 0, nquad = 0;
   sip_options opt{};
   std::vector<int32_t> P;
+  std::vector<int32_t> Q;       // volume points per direction of each element
   std::vector<int64_t> dof_off, quad_off;
   std::vector<int8_t> affine;
   // volume geometry: per element nG comps x Q^dim points, comp-major:
@@ -243,7 +272,7 @@ void fill_tables(int rule, std::vector<double>& tab);
 // elements per tile for the apply kernels (host choice), per-element flops, and
 // the tiles with the CTA that runs each (tiles cta_off[b] .. cta_off[b+1]-1, one
 // order per CTA)
-int apply_epb(int dim, int n, int precision, int threads);
+int apply_epb(int dim, int n, int q, int precision, int threads);
 void element_flops(const Plan& p, int64_t e, double& ft, double& fm);
 void build_tiles(const Plan& p, int precision, const int* epb_override, int threads, int nctas, bool persistent,
                  std::vector<Tile>& tiles, std::vector<int32_t>& cta_off, std::vector<uint16_t>& flists);

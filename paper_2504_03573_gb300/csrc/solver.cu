@@ -703,7 +703,7 @@ int solve_impl(sip_handle* h, int mode, const double* b, double* x_out, int nrhs
 size_t aux_smem(sip_handle* h) {
   size_t m = 0;
   for (const Tile& t : h->tiles_h[0]) {
-    m = std::max(m, (size_t)t.count * aux_smem_per_element(h->plan.dim, t.n) * sizeof(double));
+    m = std::max(m, (size_t)t.count * aux_smem_per_element(h->plan.dim, t.n, t.q) * sizeof(double));
   }
   return m + kRedThreads * sizeof(double);
 }

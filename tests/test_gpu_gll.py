@@ -174,3 +174,57 @@ def test_orders_9_and_10_against_oracle_rows(pkg):
     assert rel(gpu_apply(op2, x2), A2 @ x2) <= TOL64
     assert rel(gpu_apply(op2, x2, transpose=True), A2.T @ x2) <= TOL64
     assert rel(gpu_apply(op2, x2, "f32"), A2 @ x2) <= TOL32
+
+
+def _column_mesh(n, spec):
+    """n x n quads of the unit square; column c (along x) gets (degree, points)
+    spec[c] (the paper's counts are coefficients: degree = count - 1)."""
+    mm = si.structured_mesh(2, n, order=1)
+    col = (mm.vert[mm.elem_vert].mean(axis=1)[:, 0] * n).astype(int)
+    mm.orders = np.array([spec[c][0] for c in col], dtype=np.int32)
+    return mm, np.array([spec[c][1] for c in col], dtype=np.int32)
+
+
+def test_transition_layer_on_gpu(pkg):
+    """Sec. 3.3's transition layer with the point-to-point variant: a P4Q5
+    element (4 coefficients, 5 GLL points) next to P2Q3 ones is not
+    symmetric; a layer of P2Q5 elements (the lower order's coefficients, the
+    higher order's points) between them makes both interfaces exact and the
+    operator symmetric.  GPU against the oracle's assembly with the same
+    per-element point counts, and the symmetry measured through the GPU apply."""
+    high, trans, low = (3, 5), (1, 5), (1, 3)
+    res = {}
+    for name, n, spec in (("direct", 2, [high, low]), ("layered", 3, [high, trans, low])):
+        m, q = _column_mesh(n, spec)
+        orc = SipOracle(m, face_scheme="p2p", rule="gll", qorders=q)
+        A = orc.assemble()
+        op = pkg.SipOperator.from_mesh(m, opts=pkg.options(quad_rule=pkg.SIP_RULE_GLL, face_scheme=pkg.SIP_FACES_P2P,
+                                                           qorders=q))
+        x = si.random_vector(orc.ndof, 8)
+        assert rel(gpu_apply(op, x), A @ x) <= TOL64
+        assert rel(gpu_apply(op, x, "f32"), A @ x) <= TOL32
+        res[name] = _asym(op, orc.ndof, pkg)
+        # the shared-rule operator with the same point counts
+        S = SipOracle(m, rule="gll", qorders=q).assemble()
+        ops = pkg.SipOperator.from_mesh(m, opts=pkg.options(quad_rule=pkg.SIP_RULE_GLL, qorders=q))
+        assert rel(gpu_apply(ops, x), S @ x) <= TOL64
+        assert rel(gpu_apply(ops, x, transpose=True), S.T @ x) <= TOL64
+    assert res["direct"] >= 1e-4, res
+    assert res["layered"] <= 1e-13, res
+
+
+def test_table2_p3q5_on_gpu(pkg):
+    """Table 2's P3Q5-P5Q6 (degree 2 on 5 GLL points, degree 4 on 6): the
+    lower side's own rule is exact, so the point-to-point operator is
+    symmetric; GPU against the oracle."""
+    m = _half_mesh(3, 2, 2, 4)
+    left = m.vert[m.elem_vert].mean(axis=1)[:, 0] < 0.5
+    q = np.where(left, 5, 6).astype(np.int32)
+    orc = SipOracle(m, rule="gll", face_scheme="p2p", qorders=q)
+    A = orc.assemble()
+    op = pkg.SipOperator.from_mesh(m, opts=pkg.options(quad_rule=pkg.SIP_RULE_GLL, face_scheme=pkg.SIP_FACES_P2P,
+                                                       qorders=q))
+    x = si.random_vector(orc.ndof, 9)
+    assert rel(gpu_apply(op, x), A @ x) <= TOL64
+    assert _asym(op, orc.ndof, pkg) <= 1e-13
+

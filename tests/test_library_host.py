@@ -200,3 +200,21 @@ int main(void) {
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.split() == ["25", "1", "6", "1"]
+
+
+def test_qorders_option(pkg):
+    """Per-element point counts (sip_options.qorders): the plan takes the
+    supported (P, Q) pairs, sizes the volume-point arrays by them and rejects
+    the others (the extra pairs only with Gauss-Lobatto points)."""
+    m = si.structured_mesh(2, 3, order=1)
+    col = (m.vert[m.elem_vert].mean(axis=1)[:, 0] * 3).astype(int)
+    m.orders = np.array([(3, 1, 1)[c] for c in col], dtype=np.int32)
+    q = np.array([(5, 5, 3)[c] for c in col], dtype=np.int32)
+    info = pkg.plan_info(2, m.vert, m.elem_vert, m.orders, pkg.options(quad_rule=pkg.SIP_RULE_GLL, qorders=q))
+    assert info["nquad"] == int(np.sum(q.astype(np.int64) ** 2))
+    bad = q.copy()
+    bad[0] = 7
+    for opts in (pkg.options(quad_rule=pkg.SIP_RULE_GLL, qorders=bad), pkg.options(qorders=q)):
+        with pytest.raises(pkg.SipError) as e:
+            pkg.plan_info(2, m.vert, m.elem_vert, m.orders, opts)
+        assert e.value.code == 1
