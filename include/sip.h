@@ -318,7 +318,8 @@ int  sip_work_model(const sip_handle* h, int precision, sip_work* out);
  * Autotuner: coordinate descent over the orders present, timing the whole
  * apply (best of three batches of reps launches) for a few candidate tile sizes
  * of one order at a time, then over the threads per CTA and the CTAs per SM in
- * both modes; installs the fastest for this precision.  Set-up call: allocates temporaries and
+ * the three modes (one tile per CTA, persistent, single launch); installs the
+ * fastest for this precision.  Set-up call: allocates temporaries and
  * synchronises the stream.  The paper picks a kernel configuration per order
  * (Sec. 5.1); this chooses it by measurement on the current GPU. */
 int  sip_autotune(sip_handle* h, int precision, int reps, void* stream);
@@ -331,7 +332,11 @@ typedef struct sip_tiling {
     int32_t ctas_per_sm;            /* resident CTAs per SM balanced for (set: 0 = as many as
                                        fit, at most the tiles per SM that epb gives; larger
                                        values are capped at the occupancy) */
-    int32_t persistent;             /* 1: each CTA runs several tiles */
+    int32_t persistent;             /* 1: each CTA runs several tiles; 2: also the whole apply in ONE
+                                       cooperative launch (all CTAs resident: trace phase, grid-wide
+                                       barrier, main phase; the barrier's waits are bounded and a wait
+                                       that gives up is reported by the solver as SIP_ERR_CUDA), used
+                                       while CTAs x nrhs fit on the device, else the two kernels */
     int32_t threads;                /* threads per CTA: 32, 64, 128 or 256 (set: 0 = 256) */
     int64_t ntiles, nctas;          /* get only: tiles and CTAs per right-hand side */
 } sip_tiling;

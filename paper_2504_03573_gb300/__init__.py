@@ -278,12 +278,13 @@ class SipOperator:
         t = _lib.sip_tiling()
         check(lib.sip_get_tiling(self._h, precision, C.byref(t)))
         return {"epb_by_order": list(t.epb), "ntiles": t.ntiles, "nctas": t.nctas, "ctas_per_sm": t.ctas_per_sm,
-                "persistent": bool(t.persistent), "threads": t.threads}
+                "persistent": int(t.persistent), "threads": t.threads}
 
     def set_tiling(self, precision=SIP_FP64, epb_by_order=None, ctas_per_sm=0, persistent=False, threads=256):
         """Install elements per tile by order (None or 0 entries: default), the
         CTAs per SM the schedule is balanced for (0: automatic), whether CTAs run
-        several tiles each, and the threads per CTA (32, 64, 128 or 256)."""
+        several tiles each (persistent = 1; 2: the whole apply in one cooperative
+        launch), and the threads per CTA (32, 64, 128 or 256)."""
         t = _lib.sip_tiling()
         if epb_by_order is not None:
             if len(epb_by_order) != _lib.SIP_MAX_ORDER + 1:
@@ -291,7 +292,7 @@ class SipOperator:
             for i, v in enumerate(epb_by_order):
                 t.epb[i] = int(v)
         t.ctas_per_sm = int(ctas_per_sm)
-        t.persistent = int(bool(persistent))
+        t.persistent = int(persistent)  # 0, 1 (persistent CTAs) or 2 (also one launch per apply)
         t.threads = int(threads)
         check(lib.sip_set_tiling(self._h, precision, C.byref(t)))
         return self.tiling(precision)

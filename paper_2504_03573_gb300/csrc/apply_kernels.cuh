@@ -638,8 +638,10 @@ __device__ __forceinline__ void face_flux(const ApplyArgs<T>& a, const TileMeta<
   FaceGeo<T> fg{a.fgeo + mt->goff(si), npts, zc, sl.side, DIM, faff, wz};
   const T W = fg.W();
   const T tau = (T)mt->tau(si);
-  const T uo = tr[(int64_t)(2 * sl.side) * npts];
-  const T go_ = tr[(int64_t)(2 * sl.side + 1) * npts];
+  // traces come from other CTAs (in the single-launch apply, of the same
+  // kernel): read them at L2
+  const T uo = __ldcg(tr + (int64_t)(2 * sl.side) * npts);
+  const T go_ = __ldcg(tr + (int64_t)(2 * sl.side + 1) * npts);
   T s, tt;
   if (sl.flags & kFaceBnd) {
     // Nitsche: -(grad v.n, u) - (v, grad u.n) + tau (v, u)
@@ -647,8 +649,8 @@ __device__ __forceinline__ void face_flux(const ApplyArgs<T>& a, const TileMeta<
     else { s = W * tau * uo - W * go_; tt = -(W * uo); }
   } else {
     const int oth = 1 - sl.side;
-    const T un = tr[(int64_t)(2 * oth) * npts];
-    const T gn = tr[(int64_t)(2 * oth + 1) * npts];
+    const T un = __ldcg(tr + (int64_t)(2 * oth) * npts);
+    const T gn = __ldcg(tr + (int64_t)(2 * oth + 1) * npts);
     if (!a.transpose) {
       // rows of the per-point flux: s = W (tau [u] - {du/dn}), t = -W [u] / 2
       const T jmp = uo - un;
@@ -689,16 +691,16 @@ __device__ __forceinline__ void face_flux_p2p(const ApplyArgs<T>& a, const TileM
   const T* tr = trf + p2p_own_block(sl.side, npm) + zc;
   const T W = fg.W();
   const T tau = (T)mt->tau(si);
-  const T uo = tr[0];
-  const T go_ = tr[npts];
+  const T uo = __ldcg(tr);
+  const T go_ = __ldcg(tr + npts);
   T s, tt;
   if (sl.flags & kFaceBnd) {
     s = W * (tau * uo - go_);
     tt = -W * uo;
   } else {
     const T* trn = oq == qf ? trf + p2p_own_block(1 - sl.side, npm) + zc : tr + 2 * npts;
-    const T un = trn[0];
-    const T gn = trn[npts];
+    const T un = __ldcg(trn);
+    const T gn = __ldcg(trn + npts);
     const T jmp = uo - un;
     const T avg = T(0.5) * (go_ - gn);
     s = W * (tau * jmp - avg);
@@ -843,7 +845,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   if (a.ug) {
     for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
       const int el = w / QV, q = w - el * QV;
-      U[el * PER + q] = a.ug[rhs * a.nquad + mt->qoff(el) + q];
+      U[el * PER + q] = __ldcg(a.ug + rhs * a.nquad + mt->qoff(el) + q);
     }
     __syncthreads();
   } else {
@@ -1199,7 +1201,40 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
 static_assert(kNumExtra == 3 && extra_pair(2, 4) == 0 && extra_pair(2, 5) == 1 && extra_pair(3, 5) == 2,
               "the extra cases of SIP_ORDER_SWITCH list kExtraPairs");
 
-template <typename T, int DIM, int N, int Q, bool MAIN, bool P2P>
+// Grid-wide barrier of the single-launch apply: every CTA of the cooperative
+// launch (all resident at once) arrives once; the last one to arrive opens the
+// next generation.  A wait gives up after a bounded number of polls (about a
+// second), sets the status word and lets the CTA go on, so the kernel always
+// ends; the solver reports a set status as an error.
+__device__ __forceinline__ void grid_barrier(unsigned int* gbar) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = gbar + 1;
+    const unsigned int gen = *vgen;
+    __threadfence();
+    const unsigned int total = gridDim.x * gridDim.y;
+    if (atomicAdd(gbar, 1u) + 1u == total) {
+      gbar[0] = 0u;
+      __threadfence();
+      atomicAdd(gbar + 1, 1u);
+    } else {
+      unsigned int polls = 0;
+      while (*vgen == gen) {
+        if (++polls > (1u << 24)) {
+          atomicExch(gbar + 2, 1u);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// MODE: 0 the trace phase, 1 the main phase, 2 both in one launch with a grid
+// barrier between them (the tables are loaded once)
+template <typename T, int DIM, int N, int Q, int MODE, bool P2P>
 __device__ __forceinline__ void run_tiles(const ApplyArgs<T>& a, int ti0, int ti1, int rhs, unsigned char* smem_raw) {
   // finest face rule and largest tile of the CTA's tiles: the extents of its
   // table block and descriptor block
@@ -1220,11 +1255,18 @@ __device__ __forceinline__ void run_tiles(const ApplyArgs<T>& a, int ti0, int ti
   T* sm = reinterpret_cast<T*>(smem_raw + tbytes + meta_bytes(DIM, cmax));
   load_tables<T, N, Q>(tb, fmax, force);
   grid_dep_wait();  // before anything that another kernel writes
-  for (int ti = ti0; ti < ti1; ++ti) {
-    if (ti > ti0) __syncthreads();  // the previous tile's last stage still reads shared memory
-    const Tile t = a.tiles[ti];
-    if constexpr (MAIN) main_tile<T, DIM, N, Q, P2P>(a, t, rhs, tb, mt, sm);
-    else trace_tile<T, DIM, N, Q, P2P>(a, t, rhs, tb, mt, sm);
+  if constexpr (MODE != 1) {
+    for (int ti = ti0; ti < ti1; ++ti) {
+      if (ti > ti0) __syncthreads();  // the previous tile's last stage still reads shared memory
+      trace_tile<T, DIM, N, Q, P2P>(a, a.tiles[ti], rhs, tb, mt, sm);
+    }
+  }
+  if constexpr (MODE == 2) grid_barrier(a.gbar);  // every trace is written (and visible)
+  if constexpr (MODE != 0) {
+    for (int ti = ti0; ti < ti1; ++ti) {
+      if (ti > ti0 || MODE == 2) __syncthreads();
+      main_tile<T, DIM, N, Q, P2P>(a, a.tiles[ti], rhs, tb, mt, sm);
+    }
   }
 }
 
@@ -1240,7 +1282,7 @@ __global__ void __launch_bounds__(256) k_trace(ApplyArgs<T> a) {
   const int ti0 = a.cta_off[blockIdx.x], ti1 = a.cta_off[blockIdx.x + 1];
   if (ti0 >= ti1) return;
   const Tile t = a.tiles[ti0];  // every tile of the CTA has this (N, Q)
-#define SIP_TRACE_CASE(NN, QQ) run_tiles<T, DIM, NN, QQ, false, P2P>(a, ti0, ti1, blockIdx.y, smem_raw)
+#define SIP_TRACE_CASE(NN, QQ) run_tiles<T, DIM, NN, QQ, 0, P2P>(a, ti0, ti1, blockIdx.y, smem_raw)
   SIP_ORDER_SWITCH(SIP_TRACE_CASE)
 #undef SIP_TRACE_CASE
 }
@@ -1260,9 +1302,29 @@ __global__ void __launch_bounds__(SIP_MAIN_LAUNCH_BOUNDS) k_main(ApplyArgs<T> a)
   const int ti0 = a.cta_off[blockIdx.x], ti1 = a.cta_off[blockIdx.x + 1];
   if (ti0 >= ti1) return;
   const Tile t = a.tiles[ti0];
-#define SIP_MAIN_CASE(NN, QQ) run_tiles<T, DIM, NN, QQ, true, P2P>(a, ti0, ti1, blockIdx.y, smem_raw)
+#define SIP_MAIN_CASE(NN, QQ) run_tiles<T, DIM, NN, QQ, 1, P2P>(a, ti0, ti1, blockIdx.y, smem_raw)
   SIP_ORDER_SWITCH(SIP_MAIN_CASE)
 #undef SIP_MAIN_CASE
+}
+
+// The whole apply in one cooperative launch of persistent CTAs: trace phase,
+// grid barrier, main phase.  Every CTA of a persistent schedule has tiles; one
+// without would still take part in the barrier.
+template <typename T, int DIM, bool P2P, int RULE>
+__global__ void __launch_bounds__(SIP_MAIN_LAUNCH_BOUNDS) k_apply(ApplyArgs<T> a) {
+  static_assert(RULE == kTuRule, "kernel instantiated in a unit of another rule");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ti0 = a.cta_off[blockIdx.x], ti1 = a.cta_off[blockIdx.x + 1];
+  if (ti0 >= ti1) {
+    grid_barrier(a.gbar);
+    return;
+  }
+  const Tile t = a.tiles[ti0];
+  bool ran = false;
+#define SIP_APPLY_CASE(NN, QQ) (run_tiles<T, DIM, NN, QQ, 2, P2P>(a, ti0, ti1, blockIdx.y, smem_raw), ran = true)
+  SIP_ORDER_SWITCH(SIP_APPLY_CASE)
+#undef SIP_APPLY_CASE
+  if (!ran) grid_barrier(a.gbar);  // (no such tile is built) keep the barrier whole
 }
 
 }  // namespace sip

@@ -25,7 +25,8 @@
   cudaError_t prepare_##SUFFIX() {                                                                 \
     cudaError_t e = cudaSuccess;                                                                  \
     for (auto fn : {k_trace<TYPE, DIM, false, kTuRule>, k_trace<TYPE, DIM, true, kTuRule>,          \
-                    k_main<TYPE, DIM, false, kTuRule>, k_main<TYPE, DIM, true, kTuRule>})                                                     \
+                    k_main<TYPE, DIM, false, kTuRule>, k_main<TYPE, DIM, true, kTuRule>,            \
+                    k_apply<TYPE, DIM, false, kTuRule>, k_apply<TYPE, DIM, true, kTuRule>})        \
       if (e == cudaSuccess)                                                                       \
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);    \
     return e;                                                                                     \
@@ -40,11 +41,36 @@
     *blocks = bt < bm ? bt : bm;                                                                  \
     return e;                                                                                     \
   }                                                                                               \
+  /* resident CTAs per SM of the single-launch kernel (both phases' shared memory) */             \
+  cudaError_t occupancy_fused_##SUFFIX(int threads, size_t smem, int* blocks) {                   \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_apply<TYPE, DIM, false, kTuRule>, \
+                                                         threads, smem);                          \
+  }                                                                                               \
   cudaError_t launch_apply_##SUFFIX(const ApplyArgs<TYPE>& a, int nctas, int nrhs, int threads,   \
                                     size_t smem_trace, size_t smem_main, cudaStream_t s,          \
-                                    cudaEvent_t ev0, cudaEvent_t ev1, cudaEvent_t ev2) {          \
+                                    cudaEvent_t ev0, cudaEvent_t ev1, cudaEvent_t ev2, bool fused) { \
     if (nctas == 0) return cudaSuccess;                                                           \
     dim3 grid(nctas, nrhs);                                                                       \
+    if (fused) {                                                                                  \
+      /* one cooperative launch: every CTA resident, so the grid barrier completes */            \
+      if (ev0) cudaEventRecord(ev0, s);                                                           \
+      if (ev1) cudaEventRecord(ev1, s);                                                           \
+      cudaLaunchConfig_t cfg = {};                                                                \
+      cfg.gridDim = grid;                                                                         \
+      cfg.blockDim = dim3(threads);                                                               \
+      cfg.dynamicSmemBytes = smem_trace > smem_main ? smem_trace : smem_main;                     \
+      cfg.stream = s;                                                                             \
+      cudaLaunchAttribute attr[1];                                                                \
+      attr[0].id = cudaLaunchAttributeCooperative;                                                \
+      attr[0].val.cooperative = 1;                                                                \
+      cfg.attrs = attr;                                                                           \
+      cfg.numAttrs = 1;                                                                           \
+      cudaError_t e = cudaLaunchKernelEx(&cfg, a.p2p_I ? k_apply<TYPE, DIM, true, kTuRule>        \
+                                                       : k_apply<TYPE, DIM, false, kTuRule>, a);  \
+      if (e != cudaSuccess) return e;                                                             \
+      if (ev2) cudaEventRecord(ev2, s);                                                           \
+      return cudaGetLastError();                                                                  \
+    }                                                                                             \
     /* programmatic dependent launch, except when events time each kernel */                      \
     const bool pdl = ev0 == nullptr;                                                              \
     if (ev0) cudaEventRecord(ev0, s);                                                             \

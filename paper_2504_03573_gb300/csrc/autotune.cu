@@ -52,9 +52,9 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
   for (int n : orders) cur[n] = apply_epb(p.dim, n, n + 1, precision, 256);
   const bool timing = h->timing;
   h->timing = false;
-  auto time_full = [&](const int* epb, int per_sm, bool pers, int threads, float* ms_out, int* per_sm_out) -> int {
+  auto time_full = [&](const int* epb, int per_sm, int mode, int threads, float* ms_out, int* per_sm_out) -> int {
     Schedule sc;
-    int r2 = make_schedule(h, precision, epb, per_sm, pers, threads, sc);
+    int r2 = make_schedule(h, precision, epb, per_sm, mode, threads, sc);
     if (r2 == SIP_ERR_ARG) { *ms_out = 1e30f; return SIP_OK; }  // tile too large for shared memory
     if (r2) return r2;
     if (per_sm_out) *per_sm_out = sc.per_sm;
@@ -62,8 +62,8 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
     cudaError_t ee = upload_schedule(sc, d);
     if (ee != cudaSuccess) return cuda_fail(ee, "autotune tiles");
     auto run = [&]() {
-      return apply_tiles(h, precision, d.tiles, d.cta, d.flist, sc.nctas(), sc.threads, sc.smem_t, sc.smem_m, x, y, 1,
-                         s, 0, nullptr);
+      return apply_tiles(h, precision, d.tiles, d.cta, d.flist, sc.nctas(), sc.threads, sc.smem_t, sc.smem_m,
+                         sc.fused_cap, x, y, 1, s, 0, nullptr);
     };
     for (int w = 0; w < 2 && r2 == SIP_OK; ++w) r2 = run();
     // best of three batches of reps launches
@@ -84,8 +84,8 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
   };
   float cur_ms = 1e30f;
   int cur_per_sm = 0, auto_per_sm = 0, cur_threads = 256;
-  bool cur_pers = false;
-  rc = time_full(cur, 0, false, 256, &cur_ms, &auto_per_sm);
+  int cur_mode = 0;
+  rc = time_full(cur, 0, 0, 256, &cur_ms, &auto_per_sm);
   // 1. elements per tile, one order at a time (256 threads, default grid)
   for (int n : orders) {
     if (rc) break;
@@ -103,7 +103,7 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
       std::memcpy(trial, cur, sizeof(trial));
       trial[n] = c;
       float ms = 0.0f;
-      rc = time_full(trial, 0, false, 256, &ms, nullptr);
+      rc = time_full(trial, 0, 0, 256, &ms, nullptr);
       if (rc) break;
       if (ms < 0.97f * cur_ms) {  // keep a change only for a clear gain
         cur_ms = ms;
@@ -112,24 +112,25 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
     }
   }
   // 2. threads per CTA (tiles scaled with them), then the resident CTAs per SM
-  //    the schedule is balanced for, with one tile per CTA or persistent CTAs
+  //    the schedule is balanced for, with one tile per CTA, persistent CTAs, or
+  //    persistent CTAs running the whole apply in one cooperative launch
   int best_epb[kNMax + 2];
   std::memcpy(best_epb, cur, sizeof(cur));
   for (int threads : {256, 128, 64, 32}) {
     int scaled[kNMax + 2] = {};
     for (int n : orders) scaled[n] = std::max(1, cur[n] * threads / 256);
-    for (int pers = 0; pers < 2 && rc == SIP_OK; ++pers)
+    for (int pers = 0; pers < 3 && rc == SIP_OK; ++pers)
       for (int ps = 0; ps <= 32 && rc == SIP_OK; ++ps) {
         if (ps == 0 && (pers || threads == 256)) continue;  // the default grid was timed above
         if (ps > 0 && threads == 256 && !pers && ps == auto_per_sm) continue;
         float ms = 0.0f;
         int got = 0;
-        rc = time_full(scaled, ps, pers != 0, threads, &ms, &got);
+        rc = time_full(scaled, ps, pers, threads, &ms, &got);
         if (rc || (ps > 0 && got != ps)) break;  // beyond the occupancy
         if (ms < 0.97f * cur_ms) {
           cur_ms = ms;
           cur_per_sm = ps;
-          cur_pers = pers != 0;
+          cur_mode = pers;
           cur_threads = threads;
           std::memcpy(best_epb, scaled, sizeof(scaled));
         }
@@ -142,7 +143,7 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
   cudaFree(x);
   cudaFree(y);
   if (rc) return rc;
-  rc = set_tiles(h, precision, best_epb, cur_per_sm, cur_pers, cur_threads);
+  rc = set_tiles(h, precision, best_epb, cur_per_sm, cur_mode, cur_threads);
   if (rc) return rc;
   std::memcpy(h->epb[pi], best_epb, sizeof(best_epb));
   return SIP_OK;
@@ -158,7 +159,7 @@ extern "C" int sip_get_tiling(const sip_handle* h, int precision, sip_tiling* ou
     out->epb[t.n - 1] = std::min(kMaxEpb, set > 0 ? set : apply_epb(h->plan.dim, t.n, t.q, precision, h->threads[pi]));
   }
   out->ctas_per_sm = h->ctas_per_sm[pi];
-  out->persistent = h->persistent[pi];
+  out->persistent = h->fused_cap[pi] > 0 ? 2 : h->persistent[pi];
   out->threads = h->threads[pi];
   out->ntiles = (int64_t)h->tiles_h[pi].size();
   out->nctas = (int64_t)h->cta_h[pi].size() - 1;
@@ -169,17 +170,16 @@ extern "C" int sip_set_tiling(sip_handle* h, int precision, const sip_tiling* t)
   if (!h) return fail(SIP_ERR_ARG, "null handle");
   if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
   int e[kNMax + 2] = {};
-  int per_sm = 0, threads = 256;
-  bool pers = false;
+  int per_sm = 0, threads = 256, pers = 0;
   if (t) {
     for (int P = 0; P <= kMaxOrder; ++P) {
       if (t->epb[P] < 0 || t->epb[P] > kMaxEpb) return fail(SIP_ERR_ARG, "elements per tile must be in 0.." + std::to_string(kMaxEpb));
       e[P + 1] = t->epb[P];
     }
     if (t->ctas_per_sm < 0) return fail(SIP_ERR_ARG, "ctas_per_sm must be >= 0");
-    if (t->persistent != 0 && t->persistent != 1) return fail(SIP_ERR_ARG, "persistent must be 0 or 1");
+    if (t->persistent < 0 || t->persistent > 2) return fail(SIP_ERR_ARG, "persistent must be 0, 1 or 2");
     per_sm = t->ctas_per_sm;
-    pers = t->persistent != 0;
+    pers = t->persistent;
     threads = t->threads == 0 ? 256 : t->threads;
   }
   const int pi = precision == SIP_FP32 ? 1 : 0;

@@ -46,8 +46,9 @@ int apply_epb(int dim, int n, int q, int precision, int threads) {
   cudaError_t upload_tables_##SUFFIX(const double*, const float*, const int*, const double*, const float*); \
   cudaError_t prepare_##SUFFIX();                                                                      \
   cudaError_t occupancy_##SUFFIX(int, size_t, size_t, int*);                                           \
+  cudaError_t occupancy_fused_##SUFFIX(int, size_t, int*);                                             \
   cudaError_t launch_apply_##SUFFIX(const ApplyArgs<TYPE>&, int, int, int, size_t, size_t, cudaStream_t, \
-                                    cudaEvent_t, cudaEvent_t, cudaEvent_t);
+                                    cudaEvent_t, cudaEvent_t, cudaEvent_t, bool);
 SIP_DECLARE_APPLY_TU(2d_f64, double)
 SIP_DECLARE_APPLY_TU(2d_f32, float)
 SIP_DECLARE_APPLY_TU(3d_f64, double)
@@ -71,25 +72,31 @@ static const UploadFn kUpload[2][2][2] = {{{upload_tables_2d_f64, upload_tables_
                                            {upload_tables_gll_3d_f64, upload_tables_gll_3d_f32}}};
 static const PrepareFn kPrepare[2][2][2] = {{{prepare_2d_f64, prepare_2d_f32}, {prepare_3d_f64, prepare_3d_f32}},
                                             {{prepare_gll_2d_f64, prepare_gll_2d_f32}, {prepare_gll_3d_f64, prepare_gll_3d_f32}}};
+using OccupancyFusedFn = cudaError_t (*)(int, size_t, int*);
+static const OccupancyFusedFn kOccupancyFused[2][2][2] = {
+    {{occupancy_fused_2d_f64, occupancy_fused_2d_f32}, {occupancy_fused_3d_f64, occupancy_fused_3d_f32}},
+    {{occupancy_fused_gll_2d_f64, occupancy_fused_gll_2d_f32}, {occupancy_fused_gll_3d_f64, occupancy_fused_gll_3d_f32}}};
 static const OccupancyFn kOccupancy[2][2][2] = {
     {{occupancy_2d_f64, occupancy_2d_f32}, {occupancy_3d_f64, occupancy_3d_f32}},
     {{occupancy_gll_2d_f64, occupancy_gll_2d_f32}, {occupancy_gll_3d_f64, occupancy_gll_3d_f32}}};
 
 static cudaError_t launch_apply(int rule, int dim, const ApplyArgs<double>& a, int nctas, int nrhs, int threads,
-                                size_t st, size_t sm, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, cudaEvent_t e2) {
+                                size_t st, size_t sm, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, cudaEvent_t e2,
+                                bool fused) {
   if (rule == SIP_RULE_GLL)
-    return dim == 2 ? launch_apply_gll_2d_f64(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2)
-                    : launch_apply_gll_3d_f64(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2);
-  return dim == 2 ? launch_apply_2d_f64(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2)
-                  : launch_apply_3d_f64(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2);
+    return dim == 2 ? launch_apply_gll_2d_f64(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2, fused)
+                    : launch_apply_gll_3d_f64(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2, fused);
+  return dim == 2 ? launch_apply_2d_f64(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2, fused)
+                  : launch_apply_3d_f64(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2, fused);
 }
 static cudaError_t launch_apply(int rule, int dim, const ApplyArgs<float>& a, int nctas, int nrhs, int threads,
-                                size_t st, size_t sm, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, cudaEvent_t e2) {
+                                size_t st, size_t sm, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, cudaEvent_t e2,
+                                bool fused) {
   if (rule == SIP_RULE_GLL)
-    return dim == 2 ? launch_apply_gll_2d_f32(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2)
-                    : launch_apply_gll_3d_f32(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2);
-  return dim == 2 ? launch_apply_2d_f32(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2)
-                  : launch_apply_3d_f32(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2);
+    return dim == 2 ? launch_apply_gll_2d_f32(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2, fused)
+                    : launch_apply_gll_3d_f32(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2, fused);
+  return dim == 2 ? launch_apply_2d_f32(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2, fused)
+                  : launch_apply_3d_f32(a, nctas, nrhs, threads, st, sm, s, e0, e1, e2, fused);
 }
 
 namespace {
@@ -179,8 +186,10 @@ size_t apply_scratch_bytes(const sip_handle* h, int precision, int nrhs, size_t*
   return precision == SIP_FP64 ? tr + (size_t)nrhs * (size_t)h->plan.nquad * es : tr;
 }
 
-int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_per_sm, bool persistent, int threads,
+int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_per_sm, int mode, int threads,
                   Schedule& s) {
+  if (mode < 0 || mode > 2) return fail(SIP_ERR_ARG, "schedule mode must be 0, 1 or 2");
+  const bool persistent = mode >= 1, fused = mode == 2;
   const Plan& p = h->plan;
   const int es = precision == SIP_FP32 ? 4 : 8;
   // per CTA: its table block (up to the finest face rule of its tiles, as the
@@ -218,7 +227,11 @@ int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_p
   if (ntile == 0) return SIP_OK;
   int occ = 0, nsm = 0;
   cudaError_t e;
-  e = kOccupancy[p.opt.quad_rule][p.dim - 2][precision == SIP_FP64 ? 0 : 1](threads, s.smem_t, s.smem_m, &occ);
+  const int pr = precision == SIP_FP64 ? 0 : 1;
+  if (fused)  // the single launch holds both phases' shared memory
+    e = kOccupancyFused[p.opt.quad_rule][p.dim - 2][pr](threads, std::max(s.smem_t, s.smem_m), &occ);
+  else
+    e = kOccupancy[p.opt.quad_rule][p.dim - 2][pr](threads, s.smem_t, s.smem_m, &occ);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy");
   occ = std::max(1, occ);
@@ -229,6 +242,21 @@ int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_p
   build_tiles(p, precision, epb, threads, nsm * per_sm, persistent, s.tiles, s.cta_off, s.flists);
   size_smem();
   s.per_sm = per_sm;
+  s.fused_cap = 0;
+  if (fused) {
+    int of = 0;
+    e = kOccupancyFused[p.opt.quad_rule][p.dim - 2][pr](threads, std::max(s.smem_t, s.smem_m), &of);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+    s.fused_cap = std::max(1, of) * nsm;
+    // the per-order shares are rounded, so the CTA count can exceed the target
+    // by a few: aim lower until every CTA fits at once
+    for (int target = nsm * per_sm; s.nctas() > s.fused_cap && target > 1;) {
+      target = std::max(1, target - (s.nctas() - s.fused_cap));
+      build_tiles(p, precision, epb, threads, target, true, s.tiles, s.cta_off, s.flists);
+      size_smem();
+    }
+    if (s.nctas() > s.fused_cap) return fail(SIP_ERR_ARG, "single-launch schedule larger than the resident CTAs");
+  }
   return SIP_OK;
 }
 
@@ -259,10 +287,10 @@ void free_schedule(DevSchedule& d) {
 // (Re)build the schedule of one precision (epb_by_n[n] > 0 overrides the default
 // elements per tile for order n - 1; ctas_per_sm > 0 fixes the resident CTAs per
 // SM it is balanced for), upload it and size the shared memory.
-int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm, bool persistent, int threads) {
+int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm, int mode, int threads) {
   const int pi = precision == SIP_FP32 ? 1 : 0;
   Schedule sc;
-  int rc = make_schedule(h, precision, epb_by_n, ctas_per_sm, persistent, threads, sc);
+  int rc = make_schedule(h, precision, epb_by_n, ctas_per_sm, mode, threads, sc);
   if (rc) return rc;
   DevSchedule d;
   cudaError_t e = upload_schedule(sc, d);
@@ -280,6 +308,7 @@ int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm
   h->cta_h[pi] = std::move(sc.cta_off);
   h->ctas_per_sm[pi] = sc.per_sm;
   h->persistent[pi] = sc.persistent ? 1 : 0;
+  h->fused_cap[pi] = sc.fused_cap;
   h->threads[pi] = sc.threads;
   h->smem_trace[pi] = sc.smem_t;
   h->smem_main[pi] = sc.smem_m;
@@ -319,12 +348,16 @@ ApplyArgs<T> make_args(sip_handle* h, const T* x, T* y, T* trace, T* ug, int tra
   a.lambda = (T)h->lambda;
   a.transpose = transpose;
   a.p2p_I = h->p2p_interp<T>();
+  a.gbar = h->gbar;
   return a;
 }
 
 int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t* cta_d, const uint16_t* flist_d,
-                int nctas, int threads, size_t smem_t, size_t smem_m, const void* x, void* y, int nrhs, cudaStream_t s,
-                int transpose, void* scratch_override) {
+                int nctas, int threads, size_t smem_t, size_t smem_m, int fused_cap, const void* x, void* y, int nrhs,
+                cudaStream_t s, int transpose, void* scratch_override) {
+  // one cooperative launch where the schedule allows it and every CTA of all
+  // right-hand sides fits on the device at once; otherwise the two kernels
+  const bool fused = fused_cap > 0 && (int64_t)nctas * nrhs <= fused_cap;
   size_t ug_off = 0;
   apply_scratch_bytes(h, precision, nrhs, &ug_off);
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
@@ -337,14 +370,14 @@ int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t
     a.tiles = tiles_d;
     a.cta_off = cta_d;
     a.flists = flist_d;
-    e = launch_apply(h->plan.opt.quad_rule, h->plan.dim, a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2);
+    e = launch_apply(h->plan.opt.quad_rule, h->plan.dim, a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2, fused);
   } else {
     float* tr = scratch_override ? (float*)scratch_override : (float*)h->trace_d;
     auto a = make_args<float>(h, (const float*)x, (float*)y, tr, nullptr, transpose);
     a.tiles = tiles_d;
     a.cta_off = cta_d;
     a.flists = flist_d;
-    e = launch_apply(h->plan.opt.quad_rule, h->plan.dim, a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2);
+    e = launch_apply(h->plan.opt.quad_rule, h->plan.dim, a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2, fused);
   }
   if (e != cudaSuccess) return cuda_fail(e, "apply launch");
   h->timed_pending = h->timing;
@@ -364,7 +397,8 @@ int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cu
   }
   const int pi = precision == SIP_FP32 ? 1 : 0;
   return apply_tiles(h, precision, h->tiles_d[pi], h->cta_d[pi], h->flist_d[pi], (int)h->cta_h[pi].size() - 1,
-                     h->threads[pi], h->smem_trace[pi], h->smem_main[pi], x, y, nrhs, s, transpose, scratch_override);
+                     h->threads[pi], h->smem_trace[pi], h->smem_main[pi], h->fused_cap[pi], x, y, nrhs, s, transpose,
+                     scratch_override);
 }
 
 }  // namespace sip
@@ -513,6 +547,8 @@ int sip_create(const sip_mesh* mesh, const int32_t* orders, double lambda, const
     UP(h->p2p_I_f, If);
   }
 #undef UP
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->gbar, 4 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(h->gbar, 0, 4 * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->gd.kappa, std::max<size_t>(16, p.nquad * sizeof(double)));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->gf.kappa, std::max<size_t>(16, p.nquad * sizeof(float)));
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
@@ -522,7 +558,7 @@ int sip_create(const sip_mesh* mesh, const int32_t* orders, double lambda, const
     return rc;
   }
   for (int prec : {SIP_FP64, SIP_FP32}) {
-    rc = set_tiles(h, prec, nullptr, 0, false, 256);
+    rc = set_tiles(h, prec, nullptr, 0, 0, 256);
     if (rc) { sip_destroy(h); return rc; }
   }
   rc = handle_grow_trace(h, 1);

@@ -45,6 +45,9 @@ struct ApplyArgs {
   // f-point to the t-point rule at p2p_I + (f (kQMax+1) + t) kQMax^2, entry
   // [z][r] = l^G_{f,r}(xi^G_{t,z}) at z kQMax + r; nullptr with a shared rule
   const T* p2p_I;
+  // single-launch apply (k_apply): grid barrier words {arrived, generation,
+  // status}; the status word is set when a wait gives up
+  unsigned int* gbar;
 };
 
 constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }

@@ -84,6 +84,9 @@ struct sip_handle {
   int epb[2][sip::kNMax + 2] = {};                // elements per tile per order in use (0: default)
   int ctas_per_sm[2] = {0, 0};                    // resident CTAs per SM the schedule is balanced for
   int persistent[2] = {0, 0};                     // CTAs run several tiles each
+  int fused_cap[2] = {0, 0};                      // > 0: single cooperative launch per apply while
+                                                  // CTAs x nrhs <= fused_cap (resident at once)
+  unsigned int* gbar = nullptr;                   // grid barrier words of the single-launch apply
   int threads[2] = {256, 256};                    // threads per CTA
   double* xq = nullptr;
   // point-to-point interpolation matrices between Gauss rules (SIP_FACES_P2P only)
@@ -155,13 +158,15 @@ struct Schedule {
   size_t smem_t = 0, smem_m = 0;
   int per_sm = 0;
   bool persistent = false;
+  int fused_cap = 0;  // > 0: one cooperative launch per apply (persistent CTAs), up to this many CTAs
   int threads = 256;
   int nctas() const { return (int)cta_off.size() - 1; }
 };
 // epb: elements per tile by order (nullptr or 0 entries: default); ctas_per_sm <= 0:
-// as many as fit, capped at the number of default-sized tiles per SM; persistent:
-// per_sm x SMs CTAs with several tiles each (build_tiles)
-int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_per_sm, bool persistent, int threads,
+// as many as fit, capped at the number of default-sized tiles per SM; mode 1
+// (persistent): per_sm x SMs CTAs with several tiles each (build_tiles); mode 2:
+// persistent CTAs all resident at once, the apply one cooperative launch
+int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_per_sm, int mode, int threads,
                   Schedule& s);
 // device copy of a schedule
 struct DevSchedule {
@@ -179,8 +184,8 @@ int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cu
               int transpose, void* scratch_override);
 size_t apply_scratch_bytes(const sip_handle* h, int precision, int nrhs, size_t* ug_offset);
 int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t* cta_d, const uint16_t* flist_d,
-                int nctas, int threads, size_t smem_t, size_t smem_m, const void* x, void* y, int nrhs, cudaStream_t s,
-                int transpose, void* scratch_override);
-int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm, bool persistent, int threads);
+                int nctas, int threads, size_t smem_t, size_t smem_m, int fused_cap, const void* x, void* y, int nrhs,
+                cudaStream_t s, int transpose, void* scratch_override);
+int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm, int mode, int threads);
 int handle_grow_trace(sip_handle* h, int nrhs);
 }  // namespace sip

@@ -207,7 +207,7 @@ void sip_handle::release() {
   ck.clear();
   if (solve_stream) cudaStreamDestroy(solve_stream);
   cudaFree(dof_off); cudaFree(quad_off); cudaFree(vgoff); cudaFree(f_troff); cudaFree(f_goff);
-  cudaFree(desc_e); cudaFree(desc_s);
+  cudaFree(desc_e); cudaFree(desc_s); cudaFree(gbar);
   cudaFree(slots); cudaFree(elist); cudaFree(eaff); cudaFree(tiles_d[0]); cudaFree(tiles_d[1]); cudaFree(cta_d[0]); cudaFree(cta_d[1]); cudaFree(flist_d[0]); cudaFree(flist_d[1]); cudaFree(xq);
   cudaFree(gd.vgeo); cudaFree(gd.fgeo); cudaFree(gd.tau); cudaFree(gd.kappa);
   cudaFree(gf.vgeo); cudaFree(gf.fgeo); cudaFree(gf.tau); cudaFree(gf.kappa);
@@ -337,9 +337,14 @@ int run_iters(sip_handle* h, CgWork& W, int nrhs, int prec, int transpose, int i
 int read_scal(sip_handle* h, CgWork& W, int nrhs, cudaStream_t s, int* status) {
   cudaMemcpyAsync(h->scal_host, W.scal, sizeof(double) * kScal * nrhs, cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(h->scal_host + kScal * 1023, W.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  // status word of the single-launch apply's grid barrier
+  cudaMemcpyAsync(h->scal_host + kScal * 1023 + 1, h->gbar + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "CG scalars");
   std::memcpy(status, h->scal_host + kScal * 1023, sizeof(int));
+  unsigned int gb = 0;
+  std::memcpy(&gb, h->scal_host + kScal * 1023 + 1, sizeof(unsigned int));
+  if (gb) return fail(SIP_ERR_CUDA, "a grid-barrier wait of the single-launch apply gave up");
   return SIP_OK;
 }
 

@@ -219,7 +219,8 @@ def test_tilings_give_identical_results(pkg, name):
         big = 32 if m.dim == 2 else 4
         for epb, per_sm, pers, thr in (([1] * P1, 0, False, 256), ([big] * P1, 0, False, 256), ([big] * P1, 1, True, 256),
                                        (None, 1, False, 128), (None, 3, True, 64), ([2] * P1, 8, True, 128),
-                                       ([2] * P1, 8, False, 64)):
+                                       ([2] * P1, 8, False, 64), (None, 0, 2, 256), ([2] * P1, 2, 2, 128),
+                                       (None, 1, 2, 32)):
             info = op.set_tiling(prec, epb, per_sm, pers, thr)
             assert info["persistent"] == pers and info["threads"] == thr
             assert 1 <= info["nctas"] <= len(m.orders) and info["ctas_per_sm"] >= 1
@@ -227,12 +228,60 @@ def test_tilings_give_identical_results(pkg, name):
                 assert info["ntiles"] == len(m.orders)
             if not pers:
                 assert info["nctas"] == info["ntiles"]
+            if pers == 2:   # one cooperative launch per apply: trace phase, grid barrier, main phase
+                op.set_timing(True)
+                assert torch.equal(op.apply(xt), ref)
+                tr_ms, main_ms = op.last_kernel_ms()
+                assert tr_ms < 0.02 and main_ms > 0.0   # no separate trace kernel
+                op.set_timing(False)
             ntiles.add(info["ntiles"])
             assert torch.equal(op.apply(xt), ref), (epb, per_sm, pers, thr, info)
         if not small:
             assert len(ntiles) >= 3
         op.set_tiling(prec)  # back to the defaults
         assert torch.equal(op.apply(xt), ref)
+
+
+def test_single_launch_apply(pkg):
+    """The whole apply as one cooperative launch (schedule mode 2): the same
+    bits as the two-kernel apply for several right-hand sides, the transpose,
+    the point-to-point variant and Gauss-Lobatto points, the CG solve on top of
+    it, and the two-kernel fallback when the CTAs of all right-hand sides do not
+    fit on the device at once."""
+    import torch
+    P1 = pkg._lib.SIP_MAX_ORDER + 1
+    m = MESHES["3d_rot_jitter_p1to5"]
+    for kw in ({}, {"face_scheme": pkg.SIP_FACES_P2P}, {"quad_rule": pkg.SIP_RULE_GLL}):
+        op = pkg.SipOperator.from_mesh(m, opts=pkg.options(**kw) if kw else None)
+        X = torch.tensor(si.random_rhs_batch(3, op.ndof, 11), device="cuda")
+        for prec, dt in ((pkg.SIP_FP64, torch.float64), (pkg.SIP_FP32, torch.float32)):
+            Xp = X.to(dt)
+            ref = op.apply(Xp)
+            reft = None if kw.get("face_scheme") else op.apply(Xp, transpose=True)
+            info = op.set_tiling(prec, None, 0, 2, 256)
+            assert info["persistent"] == 2
+            assert torch.equal(op.apply(Xp), ref)
+            if reft is not None:
+                assert torch.equal(op.apply(Xp, transpose=True), reft)
+            op.set_tiling(prec)
+    # CG on the single-launch apply gives the default solve's bits
+    op = pkg.SipOperator.from_mesh(m)
+    b = torch.tensor(si.random_vector(op.ndof, 12), device="cuda")
+    x0, _ = op.cg_solve(b, mode=0, rtol=1e-10)
+    x1r, _ = op.cg_solve(b, mode=1, rtol=1e-10)
+    op.set_tiling(pkg.SIP_FP64, [1] * P1, 0, 2, 256)
+    op.set_tiling(pkg.SIP_FP32, [1] * P1, 0, 2, 256)
+    x1, st = op.cg_solve(b, mode=0, rtol=1e-10)
+    assert torch.equal(x0, x1) and st["converged"] == 1
+    x2r, _ = op.cg_solve(b, mode=1, rtol=1e-10)
+    assert torch.equal(x1r, x2r)
+    # more right-hand sides than fit at once: the two kernels run instead
+    nctas = op.tiling(pkg.SIP_FP64)["nctas"]
+    nr = 152 * 64 // nctas + 2
+    Xb = torch.tensor(si.random_rhs_batch(nr, op.ndof, 13), device="cuda")
+    Yb = op.apply(Xb)
+    op.set_tiling(pkg.SIP_FP64)
+    assert torch.equal(op.apply(Xb), Yb)
 
 
 def test_set_tiling_rejects_bad_values(pkg):
