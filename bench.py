@@ -48,9 +48,10 @@ METRIC = "SIP apply GDoF/s (FP64 vs FP32-refined) and CG time to 1e-10 residual"
 NRHS = {"c4_3d_24cube_jitter_p2to7": 32}
 
 # DRAM bytes (read + write) per launch of the FP64 main kernel, from one ncu
-# capture of that workload with the current kernels; None where no capture of
-# the current kernels exists
-NCU_MAIN_TRAFFIC: dict[str, float] = {}
+# capture of that workload with the current kernels and the schedule the
+# autotuner picks for it (shared-rule faces, Gauss points); workloads without
+# such a capture report null
+NCU_MAIN_TRAFFIC: dict[str, float] = {"c2_2d_64x64_jitter_p2to6": 11151104.0}
 
 
 def peaks():

@@ -336,7 +336,8 @@ typedef struct sip_tiling {
                                        cooperative launch (all CTAs resident: trace phase, grid-wide
                                        barrier, main phase; the barrier's waits are bounded and a wait
                                        that gives up is reported by the solver as SIP_ERR_CUDA), used
-                                       while CTAs x nrhs fit on the device, else the two kernels */
+                                       while CTAs x nrhs fit on the device (and the device accepts the
+                                       cooperative launch), else the two kernels */
     int32_t threads;                /* threads per CTA: 32, 64, 128 or 256 (set: 0 = 256) */
     int64_t ntiles, nctas;          /* get only: tiles and CTAs per right-hand side */
 } sip_tiling;

@@ -67,9 +67,15 @@
       cfg.numAttrs = 1;                                                                           \
       cudaError_t e = cudaLaunchKernelEx(&cfg, a.p2p_I ? k_apply<TYPE, DIM, true, kTuRule>        \
                                                        : k_apply<TYPE, DIM, false, kTuRule>, a);  \
-      if (e != cudaSuccess) return e;                                                             \
-      if (ev2) cudaEventRecord(ev2, s);                                                           \
-      return cudaGetLastError();                                                                  \
+      if (e == cudaErrorCooperativeLaunchTooLarge) {                                              \
+        /* the device will not hold every CTA at once: run the two kernels */                     \
+        cudaGetLastError();                                                                       \
+        ++g_fused_fallbacks;                                                                      \
+      } else {                                                                                    \
+        if (e != cudaSuccess) return e;                                                           \
+        if (ev2) cudaEventRecord(ev2, s);                                                         \
+        return cudaGetLastError();                                                                \
+      }                                                                                           \
     }                                                                                             \
     /* programmatic dependent launch, except when events time each kernel */                      \
     const bool pdl = ev0 == nullptr;                                                              \

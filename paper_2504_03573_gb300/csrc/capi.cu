@@ -15,6 +15,7 @@
 namespace sip {
 
 thread_local std::string g_err;
+thread_local int g_fused_fallbacks = 0;
 
 int fail(int code, const std::string& msg) {
   g_err = msg;

@@ -52,6 +52,10 @@ struct ApplyArgs {
 
 constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 
+// single-launch applies that the device refused as too large for one
+// cooperative launch and that ran as the two kernels instead (this thread)
+extern thread_local int g_fused_fallbacks;
+
 // The point rule of this translation unit's tables and kernels (volume and face
 // points, P + 2 per direction): Gauss-Legendre unless the unit defines
 // SIP_TU_RULE before including this header.  With Gauss-Lobatto-Legendre points
