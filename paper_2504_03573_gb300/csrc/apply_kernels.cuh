@@ -1,5 +1,8 @@
 // Matrix-free SIP Helmholtz apply, y = A x, on quad (DIM = 2) and hex
-// (DIM = 3) elements with per-element order.  Two kernels per apply:
+// (DIM = 3) elements with per-element order.  Two phases per apply, run as two
+// kernels chained by programmatic dependent launch, or as one cooperative
+// kernel (k_apply) with a grid-wide barrier between them (written below for
+// Gauss points; the Gauss-Lobatto variant follows further down):
 //
 //  k_trace  (TracePhysEval, Sec. 3.2):  per element, interpolate the nodal
 //           coefficients to the volume Gauss points (BwdTrans, sum
@@ -25,10 +28,10 @@
 // independent items (FP32 in 3D: one line of Q outputs per work item, with the
 // matrices as constant-bank operands).  The 1D matrices live in shared memory
 // in layouts where the lanes of a warp (consecutive outputs) read consecutive
-// addresses.  Elements are grouped in tiles of equal order (the paper's element
-// groups); a CTA runs one or more tiles of one order per right-hand side
-// (grid.y); a switch on the order selects the compile-time specialisation
-// (Sec. 5.1, "separate kernels for different orders").
+// addresses.  Elements are grouped in tiles of equal order and point count (the
+// paper's element groups); a CTA runs one or more tiles of one (N, Q) per
+// right-hand side (grid.y); a switch on (N, Q) selects the compile-time
+// specialisation (Sec. 5.1, "separate kernels for different orders").
 //
 // Point rules: Gauss-Legendre (TracePhysEval / TraceIProduct, Sec. 3.2) or, in
 // the translation units built with SIP_TU_RULE = SIP_RULE_GLL, Gauss-Lobatto-
