@@ -366,10 +366,11 @@ int  sip_last_kernel_ms(sip_handle* h, float* trace_ms, float* main_ms);
  * The paper has no counterpart; this is an interface variant, not part of the
  * method.
  * - Needs the apply's scratch to fit: nrhs * (4 * trace_points + nquad)
- *   doubles in SIP_FP64, nrhs * 4 * trace_points floats in SIP_FP32 (plus
- *   256-byte alignment), at most SIP_STATIC_TRACE_BYTES (trace_points and
- *   nquad from sip_get_plan_info); larger requests return SIP_ERR_ARG without
- *   launching anything.
+ *   doubles in SIP_FP64; in SIP_FP32 nrhs * (4 * trace_points + nquad) floats
+ *   on quads and nrhs * 4 * trace_points floats on hexes (plus 256-byte
+ *   alignment), at most SIP_STATIC_TRACE_BYTES (trace_points and nquad from
+ *   sip_get_plan_info); larger requests return SIP_ERR_ARG without launching
+ *   anything.
  * - The first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
  *   before any stream capture.

@@ -606,7 +606,7 @@ __device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb,
   if (a.ug) {
     for (int w = threadIdx.x; w < ne * S::QV; w += blockDim.x) {
       const int el = w / S::QV, q = w - el * S::QV;
-      a.ug[rhs * a.nquad + mt->qoff(el) + q] = U[el * PER + q];
+      a.ug[rhs * a.nquad + t.qbase + (int64_t)el * S::QV + q] = U[el * PER + q];
     }
   }
   trace_all_faces<T, DIM, N, Q, P2P>(a, t, mt, rhs, tb, sm, U);
@@ -844,14 +844,15 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   // the face list follows the element buffers (kFaceListBytes, FP64 only)
   uint16_t* flist = dense_faces<T>() ? reinterpret_cast<uint16_t*>(sm + ne * PER) : nullptr;
   load_meta<DIM>(a.desc_e, a.desc_s, a.flists, t, mt, flist);
-  __syncthreads();
   if (a.ug) {
-    for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) {
-      const int el = w / QV, q = w - el * QV;
-      U[el * PER + q] = __ldcg(a.ug + rhs * a.nquad + mt->qoff(el) + q);
-    }
+    // the trace phase stored the tile's volume-point values contiguously (the
+    // tile's own range of the hand-off buffer), so they load in the same stage as
+    // the descriptors, with no lookup
+    const T* ug = a.ug + rhs * a.nquad + t.qbase;
+    for (int w = threadIdx.x; w < ne * QV; w += blockDim.x) U[(w / QV) * PER + w % QV] = __ldcg(ug + w);
     __syncthreads();
   } else {
+    __syncthreads();
     // recompute the Gauss values: 2D G0 -> G1 -> U, 3D G0 -> G1 -> G2 -> U
     for (int w = threadIdx.x; w < ne * NV; w += blockDim.x) {
       const int el = w / NV, i = w - el * NV;

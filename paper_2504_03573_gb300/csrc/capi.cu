@@ -178,13 +178,21 @@ int handle_grow_trace(sip_handle* h, int nrhs) {
   return SIP_OK;
 }
 
-// Scratch of one apply: trace buffer [nrhs][4 trace_points], then (FP64 only)
-// the Gauss-point buffer [nrhs][nquad], 256-byte aligned.
+// Whether the main phase takes the volume-point values from the trace phase
+// (the hand-off buffer) instead of recomputing them: always in FP64, where the
+// recomputation costs FP64 flops, and in FP32 on quads, where it costs two
+// barrier-separated stages of kernels that wait on latency; FP32 hexes
+// recompute (more values per element, and throughput-bound stages).
+bool uses_handoff(const sip_handle* h, int precision) { return precision == SIP_FP64 || h->plan.dim == 2; }
+
+// Scratch of one apply: trace buffer [nrhs][4 trace_points], then (where the
+// main phase takes them over) the volume-point values [nrhs][nquad], 256-byte
+// aligned.
 size_t apply_scratch_bytes(const sip_handle* h, int precision, int nrhs, size_t* ug_offset) {
   const size_t es = precision == SIP_FP64 ? sizeof(double) : sizeof(float);
   const size_t tr = ((size_t)nrhs * 4 * (size_t)h->plan.trace_points * es + 255) / 256 * 256;
   if (ug_offset) *ug_offset = tr;
-  return precision == SIP_FP64 ? tr + (size_t)nrhs * (size_t)h->plan.nquad * es : tr;
+  return uses_handoff(h, precision) ? tr + (size_t)nrhs * (size_t)h->plan.nquad * es : tr;
 }
 
 int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_per_sm, int mode, int threads,
@@ -374,7 +382,9 @@ int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t
     e = launch_apply(h->plan.opt.quad_rule, h->plan.dim, a, nctas, nrhs, threads, smem_t, smem_m, s, e0, e1, e2, fused);
   } else {
     float* tr = scratch_override ? (float*)scratch_override : (float*)h->trace_d;
-    auto a = make_args<float>(h, (const float*)x, (float*)y, tr, nullptr, transpose);
+    float* ug = !uses_handoff(h, precision) ? nullptr
+                : scratch_override ? (float*)((char*)scratch_override + ug_off) : (float*)h->ug_d;
+    auto a = make_args<float>(h, (const float*)x, (float*)y, tr, ug, transpose);
     a.tiles = tiles_d;
     a.cta_off = cta_d;
     a.flists = flist_d;

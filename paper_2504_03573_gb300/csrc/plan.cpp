@@ -598,6 +598,8 @@ int build_plan(const sip_mesh* mesh, const int32_t* orders, const sip_options* o
   });
   p.desc_e.resize(E);
   p.desc_s.resize((size_t)E * nf);
+  p.qpos.assign(E + 1, 0);
+  for (int64_t i = 0; i < E; ++i) p.qpos[i + 1] = p.qpos[i] + (p.quad_off[p.elist[i] + 1] - p.quad_off[p.elist[i]]);
   for (int64_t i = 0; i < E; ++i) {
     const int32_t e = p.elist[i];
     p.desc_e[i] = ElemDesc{p.dof_off[e], p.vgoff[e], p.quad_off[e], e, (int32_t)p.affine[e]};
@@ -686,7 +688,7 @@ Tile make_tile(const Plan& p, int n, int q, int64_t s0, int64_t s1, std::vector<
   fl.insert(fl.end(), conf.begin(), conf.end());
   fl.insert(fl.end(), fine.begin(), fine.end());
   const int flags = qfm | (qfm > q || force ? kTileFine : 0) | (orth ? kTileOrth : 0) | (force ? kTileForce : 0);
-  return Tile{n, q, (int32_t)s0, (int32_t)(s1 - s0), flags, off};
+  return Tile{n, q, (int32_t)s0, (int32_t)(s1 - s0), flags, off, p.qpos[s0]};
 }
 
 }  // namespace

@@ -179,7 +179,10 @@ struct Tile {
   int32_t count;   // elements in the tile
   int32_t flags;   // kTileQfMask | kTileFine | kTileOrth | kTileForce
   int32_t flist;   // offset of the tile's face list (16-bit words)
+  int64_t qbase;   // first volume point of the tile in the element-list order of the
+                   // volume-point hand-off buffer (ug): the tile's points are contiguous there
 };
+static_assert(sizeof(Tile) == 32, "tile layout");
 
 // Face list of a tile, so that face stages run over dense work items:
 // [nconf, nfine, ngroups, (qf, count) x ngroups, nconf conforming entries
@@ -254,6 +257,8 @@ struct Plan {
   // descriptors in elist order: [E] and [E][2 dim]
   std::vector<ElemDesc> desc_e;
   std::vector<SlotDesc> desc_s;
+  // volume points before each position of the element list ([E+1], prefix sums of Q^dim)
+  std::vector<int64_t> qpos;
   int64_t orient_hist[8] = {0};
 };
 
