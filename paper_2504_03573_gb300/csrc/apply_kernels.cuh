@@ -82,32 +82,37 @@ struct Shape {
 // Copy this order's 1D tables from __constant__ into the CTA's table block: the
 // face-rule interpolations up to the finest rule fmax of the CTA's tiles (from
 // the identity F = Q on when interpolation is forced), the weights up to fmax.
+// The source is the rule's tables in global memory (gtab: the __constant__
+// layout; gw: [kQMax+1][kQMax] weights): consecutive threads read consecutive
+// entries, one coalesced round, where the constant bank would serialise the
+// warp's 32 different addresses.
 template <typename T, int N, int Q>
-__device__ __forceinline__ void load_tables(T* tb, int fmax, bool force) {
+__device__ __forceinline__ void load_tables(T* tb, int fmax, bool force, const T* __restrict__ gtab,
+                                            const T* __restrict__ gw) {
   for (int w = threadIdx.x; w < N * Q; w += blockDim.x) {
     const int q = w / N, i = w - q * N;  // B[q][i]
-    const T v = ctab<T>(tab_B(N, Q) + w);
+    const T v = gtab[tab_B(N, Q) + w];
     tb[TabLayout::BT(N, Q) + i * Q + q] = v;
     tb[TabLayout::BB(N, Q) + q * N + i] = v;
   }
   for (int w = threadIdx.x; w < Q * Q; w += blockDim.x) {
     const int q = w / Q, r = w - q * Q;  // D[q][r]
-    const T v = ctab<T>(tab_D(Q) + w);
+    const T v = gtab[tab_D(Q) + w];
     tb[TabLayout::DT(N, Q) + r * Q + q] = v;
     tb[TabLayout::DD(N, Q) + q * Q + r] = v;
   }
-  for (int w = threadIdx.x; w < 4 * Q; w += blockDim.x) tb[TabLayout::LL(N, Q) + w] = ctab<T>(tab_L(Q) + w);
+  for (int w = threadIdx.x; w < 4 * Q; w += blockDim.x) tb[TabLayout::LL(N, Q) + w] = gtab[tab_L(Q) + w];
   for (int f = force ? Q : Q + 1; f <= fmax; ++f) {
-    const int io = c_ioff[Q][f];
+    const int io = c_ioff[Q][f];  // the same for every thread: a broadcast
     for (int w = threadIdx.x; w < f * Q; w += blockDim.x) {
       const int z = w / Q, r = w - z * Q;  // I[z][r]
-      const T v = ctab<T>(io + w);
+      const T v = gtab[io + w];
       tb[TabLayout::IT(N, Q, f) + r * f + z] = v;
       tb[TabLayout::II(N, Q, f) + z * Q + r] = v;
     }
   }
   for (int f = Q; f <= fmax; ++f)
-    for (int z = threadIdx.x; z < f; z += blockDim.x) tb[TabLayout::GW(N, Q, f) + z] = cgw<T>(f, z);
+    for (int z = threadIdx.x; z < f; z += blockDim.x) tb[TabLayout::GW(N, Q, f) + z] = gw[f * kQMax + z];
   __syncthreads();
 }
 
@@ -1257,7 +1262,7 @@ __device__ __forceinline__ void run_tiles(const ApplyArgs<T>& a, int ti0, int ti
   meta.s_ = reinterpret_cast<SlotDesc*>(meta.e_ + cmax);
   TileMeta<DIM>* mt = &meta;
   T* sm = reinterpret_cast<T*>(smem_raw + tbytes + meta_bytes(DIM, cmax));
-  load_tables<T, N, Q>(tb, fmax, force);
+  load_tables<T, N, Q>(tb, fmax, force, a.gtab, a.ggw);
   grid_dep_wait();  // before anything that another kernel writes
   if constexpr (MODE != 1) {
     for (int ti = ti0; ti < ti1; ++ti) {

@@ -104,6 +104,16 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 bool g_tables_uploaded[kMaxDevices] = {false};
+// per device and rule: the tables and weights in global memory, the source of
+// the kernels' per-CTA table copies (coalesced reads); allocated once, kept for
+// the process
+struct GlobalTables {
+  double* tab_d = nullptr;
+  float* tab_f = nullptr;
+  double* gw_d = nullptr;
+  float* gw_f = nullptr;
+};
+GlobalTables g_tables[kMaxDevices][2];
 
 template <typename T>
 cudaError_t upload(T** dst, const void* src, size_t bytes) {
@@ -142,6 +152,13 @@ int ensure_tables(int dev) {
       for (int pr = 0; pr < 2; ++pr)
         if ((e = kUpload[rule][d][pr](tab.data(), tabf.data(), &ioff[0][0], &gwd[0][0], &gwf[0][0])) != cudaSuccess)
           return cuda_fail(e, "tables");
+    GlobalTables& gt = g_tables[dev][rule];
+    const size_t ngw = (size_t)(kQMax + 1) * kQMax;
+    if ((e = upload(&gt.tab_d, tab.data(), tab.size() * sizeof(double))) != cudaSuccess ||
+        (e = upload(&gt.tab_f, tabf.data(), tabf.size() * sizeof(float))) != cudaSuccess ||
+        (e = upload(&gt.gw_d, &gwd[0][0], ngw * sizeof(double))) != cudaSuccess ||
+        (e = upload(&gt.gw_f, &gwf[0][0], ngw * sizeof(float))) != cudaSuccess)
+      return cuda_fail(e, "tables");
   }
   // dynamic shared-memory limits, set once per device (never during a stream capture)
   for (int rule = 0; rule < 2; ++rule)
@@ -358,6 +375,13 @@ ApplyArgs<T> make_args(sip_handle* h, const T* x, T* y, T* trace, T* ug, int tra
   a.transpose = transpose;
   a.p2p_I = h->p2p_interp<T>();
   a.gbar = h->gbar;
+  if constexpr (std::is_same<T, double>::value) {
+    a.gtab = h->gtab_d;
+    a.ggw = h->ggw_d;
+  } else {
+    a.gtab = h->gtab_f;
+    a.ggw = h->ggw_f;
+  }
   return a;
 }
 
@@ -515,6 +539,13 @@ int sip_create(const sip_mesh* mesh, const int32_t* orders, double lambda, const
   cudaGetDevice(&h->device);
   rc = ensure_tables(h->device);
   if (rc) { delete h; return rc; }
+  {
+    const GlobalTables& gt = g_tables[h->device][h->plan.opt.quad_rule];
+    h->gtab_d = gt.tab_d;
+    h->gtab_f = gt.tab_f;
+    h->ggw_d = gt.gw_d;
+    h->ggw_f = gt.gw_f;
+  }
   const Plan& p = h->plan;
   cudaError_t e = cudaSuccess;
 #define UP(dst, vec) \

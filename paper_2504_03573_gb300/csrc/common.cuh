@@ -48,6 +48,9 @@ struct ApplyArgs {
   // single-launch apply (k_apply): grid barrier words {arrived, generation,
   // status}; the status word is set when a wait gives up
   unsigned int* gbar;
+  // the rule's 1D tables and weights in global memory (source of the per-CTA copy)
+  const T* gtab;
+  const T* ggw;
 };
 
 constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }

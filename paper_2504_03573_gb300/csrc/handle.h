@@ -87,6 +87,11 @@ struct sip_handle {
   int fused_cap[2] = {0, 0};                      // > 0: single cooperative launch per apply while
                                                   // CTAs x nrhs <= fused_cap (resident at once)
   unsigned int* gbar = nullptr;                   // grid barrier words of the single-launch apply
+  // the rule's tables and weights in global memory (per device, kept for the process)
+  const double* gtab_d = nullptr;
+  const float* gtab_f = nullptr;
+  const double* ggw_d = nullptr;
+  const float* ggw_f = nullptr;
   int threads[2] = {256, 256};                    // threads per CTA
   double* xq = nullptr;
   // point-to-point interpolation matrices between Gauss rules (SIP_FACES_P2P only)
