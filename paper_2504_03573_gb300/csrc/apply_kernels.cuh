@@ -568,12 +568,15 @@ __device__ __forceinline__ void p2p_send(const ApplyArgs<T>& a, const Tile& t, c
 }
 
 template <typename T, int DIM, int N, int Q, bool P2P>
-__device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, TileMeta<DIM>* mt, T* sm) {
+__device__ void trace_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, TileMeta<DIM>* mt, T* sm,
+                           bool meta_loaded) {
   using S = Shape<DIM, N, Q>;
   constexpr int PER = S::PER_TRACE;
   const int ne = t.count;
-  load_meta<DIM>(a.desc_e, a.desc_s, a.flists, t, mt, nullptr);
-  __syncthreads();
+  if (!meta_loaded) {
+    load_meta<DIM>(a.desc_e, a.desc_s, a.flists, t, mt, nullptr);
+    __syncthreads();
+  }
   // one output per thread (2D, and FP64 in 3D: more parallel work for the narrow
   // FP64 pipe) or one line per thread with the matrices as constant-bank operands
   // (FP32 in 3D: fewer instructions per FMA)
@@ -830,7 +833,8 @@ __device__ __forceinline__ void lift_fine_faces(const ApplyArgs<T>& a, const Til
 }
 
 template <typename T, int DIM, int N, int Q, bool P2P>
-__device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, TileMeta<DIM>* mt, T* sm) {
+__device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, TileMeta<DIM>* mt, T* sm,
+                          bool meta_loaded) {
   using S = Shape<DIM, N, Q>;
   constexpr int QV = S::QV, NV = S::NV, QF1 = S::QF1, NFACE = S::NFACE, PER = S::PER_MAIN;
   constexpr int NF = 1 + DIM;
@@ -848,7 +852,7 @@ __device__ void main_tile(const ApplyArgs<T>& a, const Tile& t, int rhs, T* tb, 
   T* const F0 = sm + (2 + DIM) * QV;
   // the face list follows the element buffers (kFaceListBytes, FP64 only)
   uint16_t* flist = dense_faces<T>() ? reinterpret_cast<uint16_t*>(sm + ne * PER) : nullptr;
-  load_meta<DIM>(a.desc_e, a.desc_s, a.flists, t, mt, flist);
+  if (!meta_loaded) load_meta<DIM>(a.desc_e, a.desc_s, a.flists, t, mt, flist);
   if (a.ug) {
     // the trace phase stored the tile's volume-point values contiguously (the
     // tile's own range of the hand-off buffer), so they load in the same stage as
@@ -1262,19 +1266,30 @@ __device__ __forceinline__ void run_tiles(const ApplyArgs<T>& a, int ti0, int ti
   meta.s_ = reinterpret_cast<SlotDesc*>(meta.e_ + cmax);
   TileMeta<DIM>* mt = &meta;
   T* sm = reinterpret_cast<T*>(smem_raw + tbytes + meta_bytes(DIM, cmax));
+  // the first tile's descriptors (and, for the main phase, its face list) are
+  // static data: copy them before the wait too, so that their latency overlaps
+  // the previous kernel's tail (load_tables ends with the barrier that makes them
+  // visible)
+  {
+    const Tile t0 = a.tiles[ti0];
+    uint16_t* fl0 = MODE == 1 && dense_faces<T>()
+                        ? reinterpret_cast<uint16_t*>(sm + t0.count * Shape<DIM, N, Q>::PER_MAIN)
+                        : nullptr;
+    load_meta<DIM>(a.desc_e, a.desc_s, a.flists, t0, mt, fl0);
+  }
   load_tables<T, N, Q>(tb, fmax, force, a.gtab, a.ggw);
   grid_dep_wait();  // before anything that another kernel writes
   if constexpr (MODE != 1) {
     for (int ti = ti0; ti < ti1; ++ti) {
       if (ti > ti0) __syncthreads();  // the previous tile's last stage still reads shared memory
-      trace_tile<T, DIM, N, Q, P2P>(a, a.tiles[ti], rhs, tb, mt, sm);
+      trace_tile<T, DIM, N, Q, P2P>(a, a.tiles[ti], rhs, tb, mt, sm, ti == ti0);
     }
   }
   if constexpr (MODE == 2) grid_barrier(a.gbar);  // every trace is written (and visible)
   if constexpr (MODE != 0) {
     for (int ti = ti0; ti < ti1; ++ti) {
       if (ti > ti0 || MODE == 2) __syncthreads();
-      main_tile<T, DIM, N, Q, P2P>(a, a.tiles[ti], rhs, tb, mt, sm);
+      main_tile<T, DIM, N, Q, P2P>(a, a.tiles[ti], rhs, tb, mt, sm, MODE == 1 && ti == ti0);
     }
   }
 }
