@@ -51,8 +51,8 @@ NRHS = {"c4_3d_24cube_jitter_p2to7": 32}
 # capture of that workload with the current kernels and the schedule the
 # autotuner picks for it (shared-rule faces, Gauss points); workloads without
 # such a capture report null
-NCU_MAIN_TRAFFIC: dict[str, float] = {"c2_2d_64x64_jitter_p2to6": 11151104.0,
-                                        "c3_3d_32cube_p4": 185606656.0 + 23636224.0}
+NCU_MAIN_TRAFFIC: dict[str, float] = {"c2_2d_64x64_jitter_p2to6": 11170048.0,
+                                        "c3_3d_32cube_p4": 186371584.0 + 24141312.0}
 
 
 def peaks():
