@@ -339,8 +339,18 @@ typedef struct sip_tiling {
                                        while CTAs x nrhs fit on the device (and the device accepts the
                                        cooperative launch), else the two kernels */
     int32_t threads;                /* threads per CTA: 32, 64, 128 or 256 (set: 0 = 256) */
+    int32_t cta_layout;             /* block order of the CTAs (set: 0 = SIP_CTAS_SEQUENTIAL):
+                                       SIP_CTAS_SEQUENTIAL: block b runs the b-th CTA of the
+                                       order-sorted list; SIP_CTAS_SM_MAJOR: blocks b, b + S,
+                                       b + 2S, ... (S = the SM count), which the hardware places
+                                       on one SM in its first wave, run consecutive CTAs of that
+                                       list, so that an SM runs mostly one (N, Q) specialisation.
+                                       Either way the results are bit-identical. */
     int64_t ntiles, nctas;          /* get only: tiles and CTAs per right-hand side */
 } sip_tiling;
+
+#define SIP_CTAS_SM_MAJOR   1
+#define SIP_CTAS_SEQUENTIAL 2
 
 /* Current schedule of one precision. */
 int  sip_get_tiling(const sip_handle* h, int precision, sip_tiling* out);

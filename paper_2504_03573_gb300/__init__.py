@@ -15,11 +15,12 @@ import numpy as np
 
 from . import _lib
 from ._lib import (SIP_CG_FP32_REFINED, SIP_CG_FP64, SIP_FACES_P2P, SIP_FACES_SHARED, SIP_FP32, SIP_FP64,
-                   SIP_RULE_GAUSS, SIP_RULE_GLL, SipError, check, lib,
+                   SIP_CTAS_SEQUENTIAL, SIP_CTAS_SM_MAJOR, SIP_RULE_GAUSS, SIP_RULE_GLL, SipError, check, lib,
                    sip_mesh, sip_options, sip_plan_info, sip_stats, sip_work)
 
 __all__ = ["SipOperator", "plan_info", "options", "fp_peak", "SipError", "SIP_FP64", "SIP_FP32", "SIP_CG_FP64",
            "SIP_CG_FP32_REFINED", "SIP_FACES_SHARED", "SIP_FACES_P2P", "SIP_RULE_GAUSS", "SIP_RULE_GLL",
+           "SIP_CTAS_SM_MAJOR", "SIP_CTAS_SEQUENTIAL",
            "SipApplyFn", "SipSolveFn", "lib"]
 
 
@@ -278,13 +279,15 @@ class SipOperator:
         t = _lib.sip_tiling()
         check(lib.sip_get_tiling(self._h, precision, C.byref(t)))
         return {"epb_by_order": list(t.epb), "ntiles": t.ntiles, "nctas": t.nctas, "ctas_per_sm": t.ctas_per_sm,
-                "persistent": int(t.persistent), "threads": t.threads}
+                "persistent": int(t.persistent), "threads": t.threads, "cta_layout": t.cta_layout}
 
-    def set_tiling(self, precision=SIP_FP64, epb_by_order=None, ctas_per_sm=0, persistent=False, threads=256):
+    def set_tiling(self, precision=SIP_FP64, epb_by_order=None, ctas_per_sm=0, persistent=False, threads=256,
+                   cta_layout=0):
         """Install elements per tile by order (None or 0 entries: default), the
         CTAs per SM the schedule is balanced for (0: automatic), whether CTAs run
         several tiles each (persistent = 1; 2: the whole apply in one cooperative
-        launch), and the threads per CTA (32, 64, 128 or 256)."""
+        launch), the threads per CTA (32, 64, 128 or 256) and the block order of
+        the CTAs (SIP_CTAS_SEQUENTIAL, the default, or SIP_CTAS_SM_MAJOR)."""
         t = _lib.sip_tiling()
         if epb_by_order is not None:
             if len(epb_by_order) != _lib.SIP_MAX_ORDER + 1:
@@ -294,6 +297,7 @@ class SipOperator:
         t.ctas_per_sm = int(ctas_per_sm)
         t.persistent = int(persistent)  # 0, 1 (persistent CTAs) or 2 (also one launch per apply)
         t.threads = int(threads)
+        t.cta_layout = int(cta_layout)
         check(lib.sip_set_tiling(self._h, precision, C.byref(t)))
         return self.tiling(precision)
 

@@ -27,6 +27,8 @@ SIP_FACES_P2P = 1
 SIP_RULE_GAUSS = 0
 SIP_RULE_GLL = 1
 SIP_MAX_ORDER = 10
+SIP_CTAS_SM_MAJOR = 1
+SIP_CTAS_SEQUENTIAL = 2
 SIP_STATIC_TRACE_BYTES = 16 << 20
 
 ERROR_NAMES = {1: "SIP_ERR_ARG", 2: "SIP_ERR_MESH", 3: "SIP_ERR_CUDA", 4: "SIP_ERR_OOM",
@@ -79,7 +81,7 @@ class sip_plan_info(C.Structure):
 
 class sip_tiling(C.Structure):
     _fields_ = [("epb", C.c_int32 * (SIP_MAX_ORDER + 1)), ("ctas_per_sm", C.c_int32), ("persistent", C.c_int32),
-                ("threads", C.c_int32), ("ntiles", C.c_int64), ("nctas", C.c_int64)]
+                ("threads", C.c_int32), ("cta_layout", C.c_int32), ("ntiles", C.c_int64), ("nctas", C.c_int64)]
 
 
 class sip_checkpoint_info(C.Structure):

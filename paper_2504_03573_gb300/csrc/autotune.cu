@@ -54,9 +54,10 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
   for (int n : orders) cur[n] = apply_epb(p.dim, n, n + 1, precision, 256);
   const bool timing = h->timing;
   h->timing = false;
-  auto time_full = [&](const int* epb, int per_sm, int mode, int threads, float* ms_out, int* per_sm_out) -> int {
+  auto time_full = [&](const int* epb, int per_sm, int mode, int threads, int layout, float* ms_out,
+                       int* per_sm_out) -> int {
     Schedule sc;
-    int r2 = make_schedule(h, precision, epb, per_sm, mode, threads, sc);
+    int r2 = make_schedule(h, precision, epb, per_sm, mode, threads, layout, sc);
     if (r2 == SIP_ERR_ARG) { *ms_out = 1e30f; return SIP_OK; }  // tile too large for shared memory
     if (r2) return r2;
     if (per_sm_out) *per_sm_out = sc.per_sm;
@@ -92,13 +93,13 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
   };
   float cur_ms = 1e30f;
   int cur_per_sm = 0, auto_per_sm = 0, cur_threads = 256;
-  int cur_mode = 0;
-  rc = time_full(cur, 0, 0, 256, &cur_ms, &auto_per_sm);
+  int cur_mode = 0, cur_layout = SIP_CTAS_SEQUENTIAL;
+  rc = time_full(cur, 0, 0, 256, cur_layout, &cur_ms, &auto_per_sm);
   // short applies: enough launches per timed batch (>= 2 ms) that the batch
   // times decide between candidates rather than the timer's noise
   if (rc == SIP_OK && cur_ms < 2.0f && cur_ms > 0.0f) {
     reps = std::min(400, (int)std::ceil(reps * 2.0f / cur_ms));
-    rc = time_full(cur, 0, 0, 256, &cur_ms, &auto_per_sm);
+    rc = time_full(cur, 0, 0, 256, cur_layout, &cur_ms, &auto_per_sm);
   }
   // 1. elements per tile, one order at a time (256 threads, default grid)
   for (int n : orders) {
@@ -117,7 +118,7 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
       std::memcpy(trial, cur, sizeof(trial));
       trial[n] = c;
       float ms = 0.0f;
-      rc = time_full(trial, 0, 0, 256, &ms, nullptr);
+      rc = time_full(trial, 0, 0, 256, cur_layout, &ms, nullptr);
       if (rc) break;
       if (ms < 0.97f * cur_ms) {  // keep a change only for a clear gain
         cur_ms = ms;
@@ -139,7 +140,7 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
         if (ps > 0 && threads == 256 && !pers && ps == auto_per_sm) continue;
         float ms = 0.0f;
         int got = 0;
-        rc = time_full(scaled, ps, pers, threads, &ms, &got);
+        rc = time_full(scaled, ps, pers, threads, cur_layout, &ms, &got);
         if (rc || (ps > 0 && got != ps)) break;  // beyond the occupancy
         if (ms < 0.97f * cur_ms) {
           cur_ms = ms;
@@ -151,13 +152,23 @@ extern "C" int sip_autotune(sip_handle* h, int precision, int reps, void* stream
       }
     if (rc) break;
   }
+  // 3. the other block order of the CTAs, with the best of the above
+  if (rc == SIP_OK) {
+    float ms = 0.0f;
+    int got = 0;
+    rc = time_full(best_epb, cur_per_sm, cur_mode, cur_threads, SIP_CTAS_SM_MAJOR, &ms, &got);
+    if (rc == SIP_OK && ms < 0.97f * cur_ms) {
+      cur_ms = ms;
+      cur_layout = SIP_CTAS_SM_MAJOR;
+    }
+  }
   h->timing = timing;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaFree(x);
   cudaFree(y);
   if (rc) return rc;
-  rc = set_tiles(h, precision, best_epb, cur_per_sm, cur_mode, cur_threads);
+  rc = set_tiles(h, precision, best_epb, cur_per_sm, cur_mode, cur_threads, cur_layout);
   if (rc) return rc;
   std::memcpy(h->epb[pi], best_epb, sizeof(best_epb));
   return SIP_OK;
@@ -175,6 +186,7 @@ extern "C" int sip_get_tiling(const sip_handle* h, int precision, sip_tiling* ou
   out->ctas_per_sm = h->ctas_per_sm[pi];
   out->persistent = h->fused_cap[pi] > 0 ? 2 : h->persistent[pi];
   out->threads = h->threads[pi];
+  out->cta_layout = h->cta_layout[pi];
   out->ntiles = (int64_t)h->tiles_h[pi].size();
   out->nctas = (int64_t)h->cta_h[pi].size() - 1;
   return SIP_OK;
@@ -184,7 +196,7 @@ extern "C" int sip_set_tiling(sip_handle* h, int precision, const sip_tiling* t)
   if (!h) return fail(SIP_ERR_ARG, "null handle");
   if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
   int e[kNMax + 2] = {};
-  int per_sm = 0, threads = 256, pers = 0;
+  int per_sm = 0, threads = 256, pers = 0, layout = SIP_CTAS_SEQUENTIAL;
   if (t) {
     for (int P = 0; P <= kMaxOrder; ++P) {
       if (t->epb[P] < 0 || t->epb[P] > kMaxEpb) return fail(SIP_ERR_ARG, "elements per tile must be in 0.." + std::to_string(kMaxEpb));
@@ -195,9 +207,10 @@ extern "C" int sip_set_tiling(sip_handle* h, int precision, const sip_tiling* t)
     per_sm = t->ctas_per_sm;
     pers = t->persistent;
     threads = t->threads == 0 ? 256 : t->threads;
+    layout = t->cta_layout == 0 ? SIP_CTAS_SEQUENTIAL : t->cta_layout;
   }
   const int pi = precision == SIP_FP32 ? 1 : 0;
-  int rc = set_tiles(h, precision, e, per_sm, pers, threads);
+  int rc = set_tiles(h, precision, e, per_sm, pers, threads, layout);
   if (rc) return rc;
   std::memcpy(h->epb[pi], e, sizeof(e));
   return SIP_OK;

@@ -93,6 +93,7 @@ struct sip_handle {
   const double* ggw_d = nullptr;
   const float* ggw_f = nullptr;
   int threads[2] = {256, 256};                    // threads per CTA
+  int cta_layout[2] = {SIP_CTAS_SEQUENTIAL, SIP_CTAS_SEQUENTIAL};  // block order of the CTAs
   double* xq = nullptr;
   // point-to-point interpolation matrices between Gauss rules (SIP_FACES_P2P only)
   double* p2p_I_d = nullptr;
@@ -165,14 +166,16 @@ struct Schedule {
   bool persistent = false;
   int fused_cap = 0;  // > 0: one cooperative launch per apply (persistent CTAs), up to this many CTAs
   int threads = 256;
+  int layout = SIP_CTAS_SEQUENTIAL;
   int nctas() const { return (int)cta_off.size() - 1; }
 };
 // epb: elements per tile by order (nullptr or 0 entries: default); ctas_per_sm <= 0:
 // as many as fit, capped at the number of default-sized tiles per SM; mode 1
 // (persistent): per_sm x SMs CTAs with several tiles each (build_tiles); mode 2:
-// persistent CTAs all resident at once, the apply one cooperative launch
+// persistent CTAs all resident at once, the apply one cooperative launch;
+// layout: SIP_CTAS_SM_MAJOR or SIP_CTAS_SEQUENTIAL (the block order of the CTAs)
 int make_schedule(const sip_handle* h, int precision, const int* epb, int ctas_per_sm, int mode, int threads,
-                  Schedule& s);
+                  int layout, Schedule& s);
 // device copy of a schedule
 struct DevSchedule {
   Tile* tiles = nullptr;
@@ -191,6 +194,7 @@ size_t apply_scratch_bytes(const sip_handle* h, int precision, int nrhs, size_t*
 int apply_tiles(sip_handle* h, int precision, const Tile* tiles_d, const int32_t* cta_d, const uint16_t* flist_d,
                 int nctas, int threads, size_t smem_t, size_t smem_m, int fused_cap, const void* x, void* y, int nrhs,
                 cudaStream_t s, int transpose, void* scratch_override);
-int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm, int mode, int threads);
+int set_tiles(sip_handle* h, int precision, const int* epb_by_n, int ctas_per_sm, int mode, int threads,
+              int layout);
 int handle_grow_trace(sip_handle* h, int nrhs);
 }  // namespace sip

@@ -217,12 +217,16 @@ def test_tilings_give_identical_results(pkg, name):
             assert rel(ref.double().cpu().numpy(), A @ x) <= tol
         ntiles = set()
         big = 32 if m.dim == 2 else 4
-        for epb, per_sm, pers, thr in (([1] * P1, 0, False, 256), ([big] * P1, 0, False, 256), ([big] * P1, 1, True, 256),
-                                       (None, 1, False, 128), (None, 3, True, 64), ([2] * P1, 8, True, 128),
-                                       ([2] * P1, 8, False, 64), (None, 0, 2, 256), ([2] * P1, 2, 2, 128),
-                                       (None, 1, 2, 32)):
-            info = op.set_tiling(prec, epb, per_sm, pers, thr)
+        smm = pkg.SIP_CTAS_SM_MAJOR   # the non-default block order
+        for epb, per_sm, pers, thr, lay in (([1] * P1, 0, False, 256, 0), ([1] * P1, 0, False, 256, smm),
+                                            ([big] * P1, 0, False, 256, 0), ([big] * P1, 1, True, 256, smm),
+                                            (None, 1, False, 128, 0), (None, 3, True, 64, 0),
+                                            ([2] * P1, 8, True, 128, smm), ([2] * P1, 8, False, 64, 0),
+                                            (None, 0, 2, 256, 0), (None, 0, 2, 256, smm), ([2] * P1, 2, 2, 128, 0),
+                                            (None, 1, 2, 32, 0)):
+            info = op.set_tiling(prec, epb, per_sm, pers, thr, lay)
             assert info["persistent"] == pers and info["threads"] == thr
+            assert info["cta_layout"] == (lay or pkg.SIP_CTAS_SEQUENTIAL)
             assert 1 <= info["nctas"] <= len(m.orders) and info["ctas_per_sm"] >= 1
             if epb is not None and epb[0] == 1:
                 assert info["ntiles"] == len(m.orders)
@@ -235,7 +239,7 @@ def test_tilings_give_identical_results(pkg, name):
                 assert tr_ms < 0.02 and main_ms > 0.0   # no separate trace kernel
                 op.set_timing(False)
             ntiles.add(info["ntiles"])
-            assert torch.equal(op.apply(xt), ref), (epb, per_sm, pers, thr, info)
+            assert torch.equal(op.apply(xt), ref), (epb, per_sm, pers, thr, lay, info)
         if not small:
             assert len(ntiles) >= 3
         op.set_tiling(prec)  # back to the defaults
@@ -295,6 +299,8 @@ def test_set_tiling_rejects_bad_values(pkg):
         op.set_tiling(pkg.SIP_FP64, None, -1)
     with pytest.raises(pkg.SipError):
         op.set_tiling(pkg.SIP_FP64, None, 0, False, 96)
+    with pytest.raises(pkg.SipError):
+        op.set_tiling(pkg.SIP_FP64, None, 0, False, 256, 3)
     with pytest.raises(ValueError):
         op.set_tiling(pkg.SIP_FP64, [1, 2], 0)
     assert op.tiling(pkg.SIP_FP64) == before

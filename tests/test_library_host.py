@@ -202,6 +202,37 @@ int main(void) {
     assert r.stdout.split() == ["25", "1", "6", "1"]
 
 
+def test_binding_structs_match_the_header(pkg, tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets of
+    its C declaration in include/sip.h (compiled and printed by gcc)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [getattr(pkg._lib, n) for n in ("sip_mesh", "sip_options", "sip_stats", "sip_plan_info",
+                                               "sip_tiling", "sip_checkpoint_info", "sip_work")]
+    lines = []
+    for st in structs:
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (st.__name__, st.__name__))
+        for f in st._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (st.__name__, f[0], st.__name__, f[0]))
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"sip.h\"\nint main(void) {\n"
+                   + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(HERE, "..", "include")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", inc, str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, check=True)
+    got = {tuple(line.split()[:2]): int(line.split()[2]) for line in r.stdout.splitlines()}
+    for st in structs:
+        assert got[(st.__name__, "size")] == C.sizeof(st), st.__name__
+        for f in st._fields_:
+            assert got[(st.__name__, f[0])] == getattr(st, f[0]).offset, (st.__name__, f[0])
+
+
 def test_qorders_option(pkg):
     """Per-element point counts (sip_options.qorders): the plan takes the
     supported (P, Q) pairs, sizes the volume-point arrays by them and rejects
