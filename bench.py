@@ -433,8 +433,9 @@ def run_gb300(args):
                       "kernel": "main", "kernel_ms": main32_ms},
               "peak_src": "HBM: MEASURED_PEAKS.json; FP32: sip_fp_peak, of measured"}
 
-    # ---- end to end through the C ABI with host buffers: sip_apply_host copies x
-    # in, applies and copies y out, all inside the timed region
+    # ---- end to end through the C ABI with host buffers: sip_apply_host moves x in,
+    # applies and moves y out (pinned buffers: the kernels read x and write y in place
+    # over the host link), all inside the timed region
     xh = torch.tensor(xhost).pin_memory()
     yh = torch.empty(xh.shape, dtype=torch.float64).pin_memory()
     for _ in range(args.warmup):

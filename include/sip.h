@@ -197,14 +197,15 @@ int  sip_set_kappa(sip_handle* h, const double* kappa_dev, void* stream);
  * x and y must not overlap.  nrhs >= 1. */
 int  sip_apply(sip_handle* h, int precision, const void* x_dev, void* y_dev, int nrhs, void* stream);
 
-/* y = A x with x and y in HOST memory: copies x [nrhs][ndof] to device
- * buffers owned by the handle, applies as sip_apply on `stream`, copies y back
- * and returns once y is complete (synchronises the stream).  The end-to-end
- * form of the apply for callers that hold their vectors on the host; pinned
- * host buffers (cudaHostAlloc / cudaHostRegister) make both copies DMA
- * transfers, pageable ones are staged by the driver.  The device buffers grow
- * to the largest nrhs used and are freed with the handle.  Errors as
- * sip_apply, plus SIP_ERR_OOM for the buffers. */
+/* y = A x with x and y in HOST memory [nrhs][ndof]: applies as sip_apply on
+ * `stream` and returns once y is complete (synchronises the stream).  The
+ * end-to-end form of the apply for callers that hold their vectors on the
+ * host.  A vector in page-locked memory mapped into the device's address
+ * space (cudaHostAlloc, cudaHostRegister; the whole vector in one allocation)
+ * is read or written in place by the kernels over the host link; a pageable one
+ * is copied through a device buffer owned by the handle (grown to the largest
+ * nrhs used, freed with the handle).  Errors as sip_apply, plus SIP_ERR_OOM for
+ * the buffers. */
 int  sip_apply_host(sip_handle* h, int precision, const void* x_host, void* y_host, int nrhs, void* stream);
 
 /* y = A^T x with the roles of trial side (trace evaluation) and test side

@@ -173,9 +173,9 @@ class SipOperator:
         return y
 
     def apply_host(self, x, precision=None, out=None):
-        """y = A x for CPU tensors (pinned or pageable), through sip_apply_host:
-        the library copies x in, applies and copies y out, and returns when y is
-        complete."""
+        """y = A x for CPU tensors through sip_apply_host, returning when y is
+        complete: pinned tensors are read / written in place by the kernels,
+        pageable ones are copied through device buffers."""
         torch = _torch()
         if precision is None:
             precision = SIP_FP32 if x.dtype == torch.float32 else SIP_FP64

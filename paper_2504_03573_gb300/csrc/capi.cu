@@ -478,6 +478,31 @@ int apply_any(sip_handle* h, int precision, const void* x, void* y, int nrhs, cu
 
 using namespace sip;
 
+namespace {
+
+// The address under which the current device reaches the host range [p, p +
+// bytes) directly, or nullptr: page-locked memory mapped into the device's
+// address space (cudaHostAlloc, cudaHostRegister), the whole range inside one
+// such allocation.  Pageable memory gives nullptr.
+void* mapped_host_range(const void* p, size_t bytes) {
+  cudaPointerAttributes a0{}, a1{};
+  if (cudaPointerGetAttributes(&a0, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a0.type != cudaMemoryTypeHost || a0.devicePointer == nullptr) return nullptr;
+  const void* last = static_cast<const char*>(p) + (bytes - 1);
+  if (cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a1.type != cudaMemoryTypeHost || a1.devicePointer != static_cast<char*>(a0.devicePointer) + (bytes - 1))
+    return nullptr;
+  return a0.devicePointer;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* sip_last_error(void) { return g_err.c_str(); }
@@ -696,7 +721,12 @@ int sip_apply_host(sip_handle* h, int precision, const void* x, void* y, int nrh
   if (precision != SIP_FP64 && precision != SIP_FP32) return fail(SIP_ERR_ARG, "precision");
   const size_t bytes = (size_t)nrhs * (size_t)h->plan.ndof * (precision == SIP_FP64 ? sizeof(double) : sizeof(float));
   cudaStream_t s = (cudaStream_t)stream;
-  if (bytes > h->io_cap) {
+  // page-locked, mapped vectors are read and written in place by the kernels
+  // (over the host link, no staging copy); others go through the handle's
+  // device buffers
+  const void* x_map = mapped_host_range(x, bytes);
+  void* y_map = mapped_host_range(y, bytes);
+  if ((!x_map || !y_map) && bytes > h->io_cap) {
     cudaStreamSynchronize(s);  // earlier calls may still use the old buffers
     cudaFree(h->io_x);
     cudaFree(h->io_y);
@@ -711,11 +741,14 @@ int sip_apply_host(sip_handle* h, int precision, const void* x, void* y, int nrh
     }
     h->io_cap = bytes;
   }
-  cudaError_t e = cudaMemcpyAsync(h->io_x, x, bytes, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(e, "sip_apply_host copy in");
-  int rc = apply_any(h, precision, h->io_x, h->io_y, nrhs, s, 0, nullptr);
+  cudaError_t e = cudaSuccess;
+  if (!x_map) {
+    e = cudaMemcpyAsync(h->io_x, x, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sip_apply_host copy in");
+  }
+  int rc = apply_any(h, precision, x_map ? x_map : h->io_x, y_map ? y_map : h->io_y, nrhs, s, 0, nullptr);
   if (rc) return rc;
-  e = cudaMemcpyAsync(y, h->io_y, bytes, cudaMemcpyDeviceToHost, s);
+  if (!y_map) e = cudaMemcpyAsync(y, h->io_y, bytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? SIP_OK : cuda_fail(e, "sip_apply_host copy out");
 }

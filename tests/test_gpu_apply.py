@@ -156,18 +156,29 @@ def test_symmetry_c2_via_gpu(pkg):
 
 
 def test_apply_host_matches_device(pkg):
-    """sip_apply_host (host vectors in and out, copies inside the call) gives the
-    same bits as sip_apply on device copies, pinned or pageable, FP64 and FP32,
-    one and several right-hand sides."""
+    """sip_apply_host (host vectors in and out) gives the same bits as sip_apply
+    on device copies, FP64 and FP32, one and several right-hand sides, with x and
+    y each pinned (read / written in place by the kernels) or pageable (staged
+    through device buffers), on hexes and on quads."""
     import torch
-    m = MESHES["3d_rot_jitter_p1to5"]
-    op = pkg.SipOperator.from_mesh(m)
-    X = torch.tensor(si.random_rhs_batch(3, op.ndof, 11))
-    Yd = op.apply(X.cuda()).cpu()
-    assert torch.equal(op.apply_host(X.pin_memory()), Yd)
-    assert torch.equal(op.apply_host(X[0].clone()), Yd[0])
-    X32 = X.float()
-    assert torch.equal(op.apply_host(X32), op.apply(X32.cuda()).cpu())
+    for name in ("3d_rot_jitter_p1to5", "2d_rot_jitter_p1to8"):
+        op = pkg.SipOperator.from_mesh(MESHES[name])
+        X = torch.tensor(si.random_rhs_batch(3, op.ndof, 11))
+        Yd = op.apply(X.cuda()).cpu()
+        for x_pin in (False, True):
+            for y_pin in (False, True):
+                xh = X.pin_memory() if x_pin else X.clone()
+                yh = torch.empty_like(X).pin_memory() if y_pin else torch.empty_like(X)
+                yh.fill_(float("nan"))
+                assert torch.equal(op.apply_host(xh, out=yh), Yd), (name, x_pin, y_pin)
+                # twice in a row into the same buffers
+                assert torch.equal(op.apply_host(xh, out=yh), Yd), (name, x_pin, y_pin)
+        assert torch.equal(op.apply_host(X[0].clone()), Yd[0])
+        assert torch.equal(op.apply_host(X[1].clone().pin_memory()), Yd[1])
+        X32 = X.float()
+        Y32 = op.apply(X32.cuda()).cpu()
+        assert torch.equal(op.apply_host(X32), Y32)
+        assert torch.equal(op.apply_host(X32.pin_memory(), out=torch.empty_like(X32).pin_memory()), Y32)
     with pytest.raises(pkg.SipError):
         op.apply_host(X.cuda())
 
